@@ -1,0 +1,358 @@
+"""Plain FP64 CPU oracle of the FFT-Galerkin (GaNi) homogenization hot path.
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, obviously correct
+restatement of what the GPU path computes.  Only the test suite, the smoke
+check and the benchmark's CPU-baseline / reference arm may import it; the
+product path (the C-ABI library and its Python binding) never does, and
+shares no code, table or helper with it.
+
+Every function follows one passage of Vondrejc, Zeman & Marek, "An FFT-based
+Galerkin method for homogenization of periodic media" (arXiv:1311.0089):
+
+  * Sec. 2 (Eq. FT_def)        frequencies xi(k) = (k_a / Y_a)_a
+  * Sec. 4.1 (Eq. A4)          odd grids, Z_N^d = {-N_a/2 <= m_a < N_a/2}
+  * Sec. 4.1 (Eq. DFT_def)     forward DFT carries 1/|N|, inverse unnormalised
+  * Sec. 3 (Eq. Gamma_hat)     Gamma_hat(k) = xi (x) xi / (A0 xi . xi), 0 at k=0
+  * Sec. 5.1 (Eq. FFT_matrices) Gamma_N = F^-1 Gamma_hat F,  G_N = Gamma_N A0
+  * Sec. 5.1                   scalar product (u,v) = 1/|N| sum_k u^k . v^k
+  * Sec. 5.2 (Eq. LSD, final_system)  [I + Gamma_N(A_N - A0)] e = E and
+                               G_N A_N e~ = -G_N A_N E for A0 = lambda I
+  * Sec. 5.3 (Lemma on CG)     CG on the non-symmetric G_N A_N from e~_0 in E_N
+  * Sec. 5.3                   Moulinec-Suquet fixed point (Neumann series)
+  * Sec. 3 (Eq. forms_def1)    energy a(e,e) -> homogenized matrix A_H
+                               (A_H itself is not defined in the paper; the
+                               energy reading is stated in the project notes)
+
+Array conventions: a field is float64 of shape (d, *N) (component first,
+spatial C order, first index slowest); a coefficient field is (d, d, *N).
+The FFT is numpy's (a library primitive used as one step); `dft_naive`
+writes the definition out as a dense sum and pins it on small grids.
+"""
+from __future__ import annotations
+
+import itertools
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+__all__ = [
+    "check_grid", "freq_index", "xi_axes", "dft", "idft", "dft_naive",
+    "idft_naive", "gamma_hat", "apply_gamma", "apply_G", "apply_A", "apply_K",
+    "inner", "ZERO_RHS", "cg", "homogenized_energy", "homogenized_flux", "solve_AH",
+    "dense_gamma_matrix", "solve_lsd_dense", "moulinec_suquet",
+]
+
+
+# ---------------------------------------------------------------------------
+# grid and frequencies (Sec. 4.1, Eq. A4; Sec. 2, Eq. FT_def)
+# ---------------------------------------------------------------------------
+def check_grid(N: Sequence[int]) -> Tuple[int, ...]:
+    """Assumption (A4): every N_a is odd (Sec. 4.1)."""
+    N = tuple(int(n) for n in N)
+    if len(N) < 1 or any(n < 1 or n % 2 == 0 for n in N):
+        raise ValueError(f"grid {N} violates (A4): every N_a must be odd")
+    return N
+
+
+def freq_index(n: int) -> np.ndarray:
+    """Integer frequency m of storage bin j on an odd axis of length n.
+
+    The grid Z_N = {-n/2 <= m < n/2} (Sec. 4.1) is stored 0-based; bin j holds
+    m = j for j <= (n-1)/2 and m = j - n otherwise.  Since the DFT kernel
+    omega^{km} (Eq. DFT_def) depends on k*m mod n only, this storage changes
+    nothing in the transform itself; it fixes which xi multiplies each bin.
+    """
+    j = np.arange(n)
+    return np.where(j <= (n - 1) // 2, j, j - n)
+
+
+def xi_axes(N: Sequence[int], Y: Optional[Sequence[float]] = None) -> List[np.ndarray]:
+    """xi_a(k) = k_a / Y_a per axis (Sec. 2, definition below Eq. FT_def)."""
+    N = check_grid(N)
+    if Y is None:
+        Y = [1.0] * len(N)
+    return [freq_index(n).astype(np.float64) / float(y) for n, y in zip(N, Y)]
+
+
+def _xi_field(N, Y) -> np.ndarray:
+    """The vector xi(k) on the whole grid, shape (d, *N)."""
+    axes = xi_axes(N, Y)
+    return np.stack(np.meshgrid(*axes, indexing="ij"))
+
+
+# ---------------------------------------------------------------------------
+# discrete Fourier transform (Sec. 4.1, Eq. DFT_def)
+# ---------------------------------------------------------------------------
+def dft(u: np.ndarray, d: Optional[int] = None) -> np.ndarray:
+    """Forward DFT over the trailing d axes, normalised by 1/|N| (Eq. DFT_def)."""
+    d = u.ndim if d is None else d
+    axes = tuple(range(u.ndim - d, u.ndim))
+    M = int(np.prod(u.shape[u.ndim - d:]))
+    return np.fft.fftn(u, axes=axes) / M
+
+
+def idft(U: np.ndarray, d: Optional[int] = None) -> np.ndarray:
+    """Inverse DFT over the trailing d axes, unnormalised (Eq. DFT_def)."""
+    d = U.ndim if d is None else d
+    axes = tuple(range(U.ndim - d, U.ndim))
+    M = int(np.prod(U.shape[U.ndim - d:]))
+    return np.fft.ifftn(U, axes=axes) * M
+
+
+def _dft_matrix(N: Sequence[int], sign: int) -> np.ndarray:
+    """Dense matrix omega_N^{sign k m} over all multi-indices (Eq. DFT_def)."""
+    N = tuple(N)
+    ks = np.array(list(itertools.product(*[range(n) for n in N])), dtype=np.int64)
+    phase = np.zeros((ks.shape[0], ks.shape[0]))
+    for a, n in enumerate(N):
+        phase += np.outer(ks[:, a], ks[:, a]) / n
+    return np.exp(sign * 2j * np.pi * phase)
+
+
+def dft_naive(u: np.ndarray, N: Sequence[int]) -> np.ndarray:
+    """The forward DFT written out as the dense sum of Eq. DFT_def (small |N|).
+
+    u has shape (..., *N); returns (1/|N|) sum_m u(x_m) omega^{-k m}."""
+    N = tuple(N)
+    M = int(np.prod(N))
+    W = _dft_matrix(N, -1)
+    lead = u.shape[: u.ndim - len(N)]
+    flat = u.reshape(lead + (M,))
+    return (flat @ W.T / M).reshape(lead + N)
+
+
+def idft_naive(U: np.ndarray, N: Sequence[int]) -> np.ndarray:
+    """Inverse of Eq. DFT_def as a dense sum: sum_m U(m) omega^{k m}."""
+    N = tuple(N)
+    M = int(np.prod(N))
+    W = _dft_matrix(N, +1)
+    lead = U.shape[: U.ndim - len(N)]
+    flat = U.reshape(lead + (M,))
+    return (flat @ W.T).reshape(lead + N)
+
+
+# ---------------------------------------------------------------------------
+# Green operator and projection (Sec. 3 Eq. Gamma_hat; Sec. 5.1 Eq. FFT_matrices)
+# ---------------------------------------------------------------------------
+def gamma_hat(N: Sequence[int], Y=None, A0: Optional[np.ndarray] = None) -> np.ndarray:
+    """Gamma_hat(k) = xi(k) (x) xi(k) / (A0 xi(k) . xi(k)), zero at k = 0.
+
+    Eq. Gamma_hat (Sec. 3) evaluated on Z_N^d (Sec. 5.1).  Returns (d, d, *N)."""
+    N = check_grid(N)
+    d = len(N)
+    A0 = np.eye(d) if A0 is None else np.asarray(A0, dtype=np.float64)
+    xi = _xi_field(N, Y)
+    denom = np.einsum("ab,a...,b...->...", A0, xi, xi)
+    G = np.einsum("a...,b...->ab...", xi, xi)
+    zero = denom == 0.0
+    denom = np.where(zero, 1.0, denom)
+    G = G / denom
+    G[(slice(None), slice(None)) + np.nonzero(zero)] = 0.0
+    return G
+
+
+def apply_gamma(u: np.ndarray, N, Y=None, A0=None) -> np.ndarray:
+    """Gamma_N u = F^-1 Gamma_hat F u (Eq. FFT_matrices); u is (d, *N) real."""
+    N = check_grid(N)
+    d = len(N)
+    Gh = gamma_hat(N, Y, A0)
+    uh = dft(u, d)
+    vh = np.einsum("ab...,b...->a...", Gh, uh)
+    return idft(vh, d).real
+
+
+def apply_G(u: np.ndarray, N, Y=None, A0=None) -> np.ndarray:
+    """G_N u = Gamma_N A0 u (Eq. FFT_matrices)."""
+    N = check_grid(N)
+    d = len(N)
+    A0m = np.eye(d) if A0 is None else np.asarray(A0, dtype=np.float64)
+    return apply_gamma(np.einsum("ab,b...->a...", A0m, u), N, Y, A0)
+
+
+def apply_A(A: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """A_N u: the block-diagonal coefficient matrix of Sec. 5.1 acting pointwise."""
+    return np.einsum("ab...,b...->a...", A, u)
+
+
+def apply_K(A: np.ndarray, u: np.ndarray, N, Y=None) -> np.ndarray:
+    """K u = G_N A_N u with A0 = I, the system matrix of Eq. final_system."""
+    return apply_G(apply_A(A, u), N, Y, None)
+
+
+def inner(u: np.ndarray, v: np.ndarray) -> float:
+    """(u, v) = 1/|N| sum_k u^k . v^k, the scalar product of Sec. 5.1."""
+    M = u[0].size
+    return float(np.sum(u * v)) / M
+
+
+# ---------------------------------------------------------------------------
+# conjugate gradients on Eq. final_system (Sec. 5.3)
+# ---------------------------------------------------------------------------
+ZERO_RHS = 1e-13   # ||b|| / ||A_N E|| below this is roundoff of an exact zero
+
+def cg(A: np.ndarray, E: np.ndarray, N, Y=None, tol: float = 1e-10,
+       maxiter: int = 10000, x0: Optional[np.ndarray] = None) -> Dict:
+    """Solve G_N A_N x = -G_N A_N E by conjugate gradients (Sec. 5.3 Lemma).
+
+    The paper proves that plain CG works on this non-symmetric system from
+    any start in E_N.  The steps are the textbook Hestenes-Stiefel recursion:
+      b = -K E;  r_0 = b - K x_0;  p_0 = r_0;
+      q = K p;  alpha = (r,r)/(p,q);  x += alpha p;  r -= alpha q;
+      beta = (r,r)_new/(r,r)_old;  p = r + beta p.
+    Stop when ||r_i|| / ||b|| <= tol (relative recursive residual; the paper
+    gives no criterion).  The sign of r follows Eq. final_system (r = b - K x),
+    reading the printed r_0 = G A (e~_0 + E) as its negative.
+
+    A right-hand side that vanishes in exact arithmetic (G kills constants,
+    Lemma FD_projection (iv)) is roundoff in floating point; since G is an
+    orthogonal projection, ||b|| <= ||A_N E||, and b is taken as zero when
+    ||b|| <= ZERO_RHS * ||A_N E||.  Then x = x_0 and no iteration is made.
+    """
+    N = check_grid(N)
+    d = len(N)
+    Evec = np.asarray(E, dtype=np.float64).reshape((d,) + (1,) * d) * np.ones((d,) + N)
+    b = -apply_K(A, Evec, N, Y)
+    x = np.zeros((d,) + N) if x0 is None else np.array(x0, dtype=np.float64)
+    r = b - apply_K(A, x, N, Y) if x0 is not None else b.copy()
+    p = r.copy()
+    rr = inner(r, r)
+    bnorm = np.sqrt(inner(b, b))
+    AE = apply_A(A, Evec)
+    if bnorm <= ZERO_RHS * np.sqrt(inner(AE, AE)):
+        bnorm = 0.0
+    hist = [np.sqrt(rr) / bnorm if bnorm > 0 else 0.0]
+    it = 0
+    if bnorm == 0.0 or hist[0] <= tol:
+        return {"x": x, "iters": 0, "rel_res": hist[0], "hist": hist,
+                "true_rel_res": 0.0 if bnorm == 0 else hist[0], "b": b}
+    while it < maxiter:
+        q = apply_K(A, p, N, Y)
+        alpha = rr / inner(p, q)
+        x = x + alpha * p
+        r = r - alpha * q
+        it += 1
+        rr_new = inner(r, r)
+        hist.append(np.sqrt(rr_new) / bnorm)
+        if hist[-1] <= tol:
+            break
+        beta = rr_new / rr
+        p = r + beta * p
+        rr = rr_new
+    true_r = b - apply_K(A, x, N, Y)
+    return {"x": x, "iters": it, "rel_res": hist[-1], "hist": hist,
+            "true_rel_res": np.sqrt(inner(true_r, true_r)) / bnorm, "b": b}
+
+
+# ---------------------------------------------------------------------------
+# homogenized matrix (energy of the macroscopic loads, Eq. forms_def1)
+# ---------------------------------------------------------------------------
+def homogenized_energy(A: np.ndarray, e: Sequence[np.ndarray]) -> np.ndarray:
+    """A_H[i][j] = (A_N e_j, e_i) with e_j = E_j + e~_j (energy form)."""
+    d = len(e)
+    AH = np.zeros((d, d))
+    for i in range(d):
+        for j in range(d):
+            AH[i, j] = inner(apply_A(A, e[j]), e[i])
+    return AH
+
+
+def homogenized_flux(A: np.ndarray, e: Sequence[np.ndarray]) -> np.ndarray:
+    """A_H[i][j] = <A_N e_j>_i, the mean flux of load j (equal to the energy
+    form at convergence by Galerkin orthogonality, Eq. GaNiD with v = e~_i)."""
+    d = len(e)
+    AH = np.zeros((d, d))
+    for j in range(d):
+        flux = apply_A(A, e[j])
+        for i in range(d):
+            AH[i, j] = float(np.mean(flux[i]))
+    return AH
+
+
+def solve_AH(A: np.ndarray, N, Y=None, tol: float = 1e-10, maxiter: int = 10000,
+             loads: Optional[Sequence[int]] = None) -> Dict:
+    """Solve the cell problem for E = e_1..e_d and assemble A_H (Sec. 5.2-5.3)."""
+    N = check_grid(N)
+    d = len(N)
+    loads = list(range(d)) if loads is None else list(loads)
+    res = {"iters": [], "rel_res": [], "true_rel_res": [], "x": []}
+    es = []
+    for j in range(d):
+        E = np.zeros(d)
+        E[j] = 1.0
+        out = cg(A, E, N, Y, tol, maxiter)
+        res["iters"].append(out["iters"])
+        res["rel_res"].append(out["rel_res"])
+        res["true_rel_res"].append(out["true_rel_res"])
+        res["x"].append(out["x"])
+        es.append(E.reshape((d,) + (1,) * d) + out["x"])
+    res["AH"] = homogenized_energy(A, es)
+    res["AH_flux"] = homogenized_flux(A, es)
+    return res
+
+
+# ---------------------------------------------------------------------------
+# dense discrete Lippmann-Schwinger solve (Sec. 5.2, Eq. LSD) for tiny grids
+# ---------------------------------------------------------------------------
+def dense_gamma_matrix(N, Y=None, A0=None) -> np.ndarray:
+    """Gamma_N = F^-1 Gamma_hat F as a dense real (d|N|) x (d|N|) matrix.
+
+    Built from the dense DFT matrices of Eq. FFT_matrices (not from an FFT),
+    with index order (component, flat grid index)."""
+    N = check_grid(N)
+    d = len(N)
+    M = int(np.prod(N))
+    F = _dft_matrix(N, -1) / M
+    Fi = _dft_matrix(N, +1)
+    Gh = gamma_hat(N, Y, A0).reshape(d, d, M)
+    out = np.zeros((d * M, d * M), dtype=np.complex128)
+    for a in range(d):
+        for b in range(d):
+            out[a * M:(a + 1) * M, b * M:(b + 1) * M] = Fi @ (Gh[a, b][:, None] * F)
+    return out.real
+
+
+def solve_lsd_dense(A: np.ndarray, E: np.ndarray, N, Y=None, lam: float = 1.0) -> np.ndarray:
+    """Solve [I + Gamma_N (A_N - lam I)] e = E by LU (Eq. LSD); returns e (d, *N)."""
+    N = check_grid(N)
+    d = len(N)
+    M = int(np.prod(N))
+    Gam = dense_gamma_matrix(N, Y, lam * np.eye(d))
+    Ad = np.zeros((d * M, d * M))
+    Af = A.reshape(d, d, M)
+    idx = np.arange(M)
+    for a in range(d):
+        for b in range(d):
+            Ad[a * M + idx, b * M + idx] = Af[a, b]
+    Ad -= lam * np.eye(d * M)
+    sysm = np.eye(d * M) + Gam @ Ad
+    rhs = np.repeat(np.asarray(E, dtype=np.float64), M)
+    e = np.linalg.solve(sysm, rhs)
+    return e.reshape((d,) + N)
+
+
+# ---------------------------------------------------------------------------
+# Moulinec-Suquet fixed point (Sec. 5.3, Neumann series for Eq. LSD)
+# ---------------------------------------------------------------------------
+def moulinec_suquet(A: np.ndarray, E: np.ndarray, N, Y=None, lam: float = 1.0,
+                    tol: float = 1e-10, maxiter: int = 100000) -> Dict:
+    """e_i = -Gamma_N (A_N - lam I) e_{i-1} + E, from e_0 = E (Sec. 5.3).
+
+    Stops when ||e_i - e_{i-1}|| / ||E|| <= tol (the paper gives no criterion).
+    """
+    N = check_grid(N)
+    d = len(N)
+    A0 = lam * np.eye(d)
+    Evec = np.asarray(E, dtype=np.float64).reshape((d,) + (1,) * d) * np.ones((d,) + N)
+    e = Evec.copy()
+    Enorm = np.sqrt(inner(Evec, Evec))
+    it = 0
+    step = np.inf
+    while it < maxiter:
+        tau = apply_A(A, e) - np.einsum("ab,b...->a...", A0, e)
+        e_new = Evec - apply_gamma(tau, N, Y, A0)
+        step = np.sqrt(inner(e_new - e, e_new - e)) / Enorm
+        e = e_new
+        it += 1
+        if step <= tol:
+            break
+    return {"e": e, "iters": it, "step": step}

@@ -1,0 +1,54 @@
+"""Writes the stored expected values under tests/golden/ from the CPU oracle.
+
+Calls only `oracle` and `workloads` (never the CUDA library).  Each fixture
+records its inputs, the oracle settings and the passage it follows.
+Run:  python tests/golden/make_golden.py
+"""
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import oracle as O  # noqa: E402
+import workloads as W  # noqa: E402
+
+
+def square_inclusion():
+    ms = W.square_inclusion_15()
+    res = O.solve_AH(ms.full_field(), ms.N, tol=1e-12)
+    return {
+        "citation": "Sec. 5.2 Eq. final_system solved by CG (Sec. 5.3 Lemma); A_H by the "
+                    "energy form of Eq. forms_def1; 15x15 grid, central 7x7 inclusion "
+                    "(0-based voxels 4..10) of 10*I in 1*I, A0 = I, loads e1, e2",
+        "N": list(ms.N),
+        "tol": 1e-12,
+        "AH": res["AH"].tolist(),
+        "iters": res["iters"],
+    }
+
+
+def laminate():
+    # closed form: harmonic mean across the layers, arithmetic mean along them
+    a = [1.0, 3.0, 10.0, 30.0, 100.0, 30.0, 10.0, 3.0, 1.0]
+    harm = len(a) / sum(1.0 / v for v in a)
+    arith = sum(a) / len(a)
+    return {
+        "citation": "exact GaNi solution of a laminate A(x) = a(x_1) I on a 9x7 grid: "
+                    "e~ = (harm/a - 1, 0) is curl-free, zero-mean and makes A e constant "
+                    "(Sec. 5.2 Eq. GaNiD)",
+        "N": [9, 7],
+        "layers_axis0": a,
+        "AH": [[harm, 0.0], [0.0, arith]],
+    }
+
+
+if __name__ == "__main__":
+    for name, fn in (("square_inclusion_15.json", square_inclusion),
+                     ("laminate_9x7.json", laminate)):
+        with open(os.path.join(HERE, name), "w") as f:
+            json.dump(fn(), f, indent=1)
+        print("wrote", name)
