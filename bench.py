@@ -1,0 +1,430 @@
+#!/usr/bin/env python
+"""Benchmark of the FFT-Galerkin homogenization solve on GB300.
+
+One step = one complete homogenized-matrix solve of the 729 x 729 two-phase
+workload (40 seeded circles, radii U[10,30], phases 1*I and 100*I, loads
+E = e1, e2): FP64 right-hand side, FP32 CG with FP64 dot products, FP64
+residual recomputation (iterative refinement) and FP64 A_H, stopping at a
+relative residual of 1e-5, which puts A_H within 1e-6 of the FP64 oracle.
+The plain FP64 GPU solve of the same problem at the same tolerance is timed
+beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per GPU, launched by torchrun): the
+path has no data exchange between GPUs.  --impl reference times the CPU
+oracle (the plain FP64 numpy restatement of the paper's algorithm) on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CG voxel-iterations/sec and A_H solves/sec (p50/p99 latency) vs plain FP64 GPU at 1e-6"
+UNIT = "voxel-iter/s"
+TOL = 1e-5            # relative residual; gives max|dA_H|/max|A_H| ~ 1e-8 here
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tol", type=float, default=TOL)
+    return ap.parse_args()
+
+
+def workload():
+    import workloads as W
+    ms = W.circles_2d()
+    cfg = {
+        "workload": "729x729 GaNi cell problem, 40 seeded non-overlapping circles r~U[10,30] "
+                    "(vf %.3f), isotropic phases 1*I / 100*I, A0=I, loads e1,e2; FP32 CG + FP64 "
+                    "dots, FP64 residual refinement and A_H; stop at rel. residual %g" % (ms.meta["vf"], TOL),
+        "grid": list(ms.N),
+        "loads": 2,
+        "contrast": 100.0,
+        "inclusions": ms.meta["count"],
+        "volume_fraction": round(ms.meta["vf"], 4),
+        "precision": "mixed (FP32 bulk, FP64 dots/residual/A_H)",
+        "tol": TOL,
+        "l2": "flushed between steps (512 MiB write)",
+    }
+    return ms, cfg
+
+
+def reference_AH():
+    path = os.path.join(ROOT, "tests", "golden", "circles_729_AH.json")
+    with open(path) as f:
+        return np.array(json.load(f)["AH"])
+
+
+def ah_err(AH, ref):
+    return float(np.max(np.abs(AH - ref)) / np.max(np.abs(ref)))
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except Exception:
+            self.proc.kill()
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# roofline bookkeeping (algorithmic bytes per launch of each pass, 2D path)
+# ----------------------------------------------------------------------------
+def pass_bytes(N, L, prec_bytes, n_phases_bytes=1):
+    """Algorithmic HBM bytes of one launch of each CG pass (all L loads).
+
+    2D grid N0 x N1 with half spectrum N0 x H, H = (N1+1)/2, d = 2, w = word:
+      row_fwd : read r, p; write p (3 d w per voxel) + phase byte + write
+                half spectrum (d * 2w per (N0 x H) entry)
+      strided : read + write the half spectrum (2 * d * 2w per entry)
+      row_inv : read spectrum; read x, r, p; write x, r (5 d w per voxel)
+    """
+    N0, N1 = N
+    d = 2
+    M = N0 * N1
+    Ms = N0 * ((N1 + 1) // 2)
+    w = prec_bytes
+    spec = L * d * Ms * 2 * w
+    vec = L * d * M * w
+    return {
+        "row_fwd": 3 * vec + M * n_phases_bytes + spec,
+        "strided": 2 * spec,
+        "row_inv": spec + 5 * vec,
+    }
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("hg_kernels.cu", "fft_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1311_0089_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        ent = t.get(kernel_key)
+        if ent and ent.get("kernel_source_sha") == kernel_source_hash():
+            return ent["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample(ms, seconds):
+    """Times the oracle's CG on load e1 of the workload for a bounded number of
+    iterations (chosen to take about `seconds`).  Returns (voxel-iter/s, desc)."""
+    import oracle as O
+    A = ms.full_field()
+    N = ms.N
+    d = len(N)
+    u = np.ones((d,) + N)
+    t0 = time.perf_counter()
+    O.apply_K(A, u, N)
+    t_apply = time.perf_counter() - t0
+    iters = int(max(3, min(500, seconds / max(t_apply, 1e-6))))
+    t0 = time.perf_counter()
+    out = O.cg(A, np.array([1.0, 0.0]), N, tol=1e-30, maxiter=iters)
+    t = time.perf_counter() - t0
+    M = int(np.prod(N))
+    return M * out["iters"] / t, ("oracle CG (numpy FP64) on load e1 of the 729x729 workload, "
+                                  "%d iterations incl. right-hand side and final true residual, %.1f s"
+                                  % (out["iters"], t)), out["iters"], t
+
+
+# ----------------------------------------------------------------------------
+# distributed helpers (replicas only)
+# ----------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    lrank = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, lrank
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    ms, cfg = workload()
+    vals, descs = [], []
+    per = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup + args.steps):
+        v, desc, it, t = oracle_sample(ms, per)
+        if i >= args.warmup:
+            vals.append((v, t))
+            descs.append(desc)
+    value = float(np.mean([v for v, _ in vals]))
+    ms_per_step = float(np.mean([t for _, t in vals]) * 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": descs[-1] + "; each step is one such bounded sample",
+                         "host_cpus": os.cpu_count()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_1311_0089_gb300 as hg
+
+    ws, rank, lrank = dist_env()
+    torch.cuda.set_device(lrank)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
+    hg.load()
+    ms, cfg = workload()
+    d = ms.d
+    M = int(np.prod(ms.N))
+    ref = reference_AH()
+    dev = torch.device("cuda", lrank)
+    stream = torch.cuda.current_stream(dev)
+    ctx = hg.Context(lrank, stream=stream)
+    g = ctx.grid(ms.N)
+    phase_d = torch.from_numpy(ms.phase).to(dev)
+    table_d = torch.from_numpy(ms.table).to(dev)
+    g.set_coeffs_phase(phase_d, table_d)        # inputs resident in HBM
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    o_mixed = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED)
+    o_fp64 = hg.default_opts(tol=args.tol, prec=hg.HG_FP64)
+
+    def step(opts):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = g.solve(opts)
+        e1.record(stream)
+        e1.synchronize()
+        return res, e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        step(o_mixed)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(lrank)
+    sampler.start()
+    launches0 = ctx.launches()
+    times, vox, results = [], 0, []
+    for _ in range(args.steps):
+        res, ms_ = step(o_mixed)
+        times.append(ms_)
+        vox += M * sum(res["iters"])
+        results.append(res)
+    torch.cuda.synchronize()
+    launches = ctx.launches() - launches0
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    t_total = sum(times) / 1e3
+    tmax = t_total
+    vox_all = vox
+    if dist:
+        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tmax = float(tt.item())
+        vv = torch.tensor([float(vox)], device=dev, dtype=torch.float64)
+        dist.all_reduce(vv, op=dist.ReduceOp.SUM)
+        vox_all = float(vv.item())
+    value = vox_all / tmax
+    solves_per_s = ws * args.steps / tmax
+    last = results[-1]
+    err_mixed = ah_err(last["AH"], ref)
+
+    # plain FP64 GPU solve of the same problem at the same tolerance
+    f_times, f_vox, f_res = [], 0, None
+    for _ in range(max(1, args.fp64_steps)):
+        r64, t64 = step(o_fp64)
+        f_times.append(t64)
+        f_vox += M * sum(r64["iters"])
+        f_res = r64
+    fp64 = {
+        "solves_per_s": len(f_times) / (sum(f_times) / 1e3),
+        "voxel_iter_per_s": f_vox / (sum(f_times) / 1e3),
+        "ms_per_solve": float(np.mean(f_times)),
+        "iters": f_res["iters"],
+        "AH_rel_err_vs_oracle": ah_err(f_res["AH"], ref),
+    }
+
+    # end to end through the C ABI with host buffers: coefficients from host
+    # memory (H2D inside hg_set_coeffs_phase), solve, A_H back to the host
+    e2e_t, e2e_vox = [], 0
+    phase_h = np.ascontiguousarray(ms.phase)
+    table_h = np.ascontiguousarray(ms.table)
+    for _ in range(max(1, args.steps // 2)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_coeffs_phase(phase_h, table_h)
+        r = g.solve(o_mixed)
+        e2e_t.append(time.perf_counter() - t0)
+        e2e_vox += M * sum(r["iters"])
+    e2e = {"value": e2e_vox / sum(e2e_t), "unit": UNIT,
+           "h2d_bytes_per_step": int(phase_h.nbytes + table_h.nbytes),
+           "d2h_bytes_per_step": int(2 * d * d * 8)}
+
+    # roofline of the dominant kernel (per-pass CUDA-event timing, FP32 passes)
+    peaks, peak_kind = measured_peaks()
+    pb = pass_bytes(ms.N, d, 4)
+    passes = []
+    for p in range(g.num_passes()):
+        t_ms, name = g.time_pass(p, hg.HG_MIXED, reps=50)
+        key = ["row_fwd", "strided", "row_inv"][p]
+        passes.append({"pass": p, "kernel": name, "ms": t_ms, "bytes": pb[key], "key": key})
+    passes64 = []
+    pb64 = pass_bytes(ms.N, d, 8)
+    for p in range(g.num_passes()):
+        t_ms, name = g.time_pass(p, hg.HG_FP64, reps=10)
+        key = ["row_fwd", "strided", "row_inv"][p]
+        passes64.append({"kernel": name, "ms": t_ms, "GBs": pb64[key] / (t_ms * 1e-3) / 1e9})
+    dom = max(passes, key=lambda x: x["ms"])
+    achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
+    roof = {
+        "bound": "hbm", "kernel": dom["kernel"], "achieved": achieved,
+        "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+        "peak_kind": peak_kind, "traffic": profiled_traffic("fp32_" + dom["key"]),
+        "bytes_per_launch": dom["bytes"], "ms_per_launch": dom["ms"],
+        "note": "working set of one solve (~45 MB FP32) is L2-resident between passes",
+        "passes_fp32": [{k: v for k, v in x.items() if k != "key"} for x in passes],
+        "passes_fp64": passes64,
+    }
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        v, desc, it, t = oracle_sample(ms, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+               "host_cpus": os.cpu_count()}
+
+    lat = sorted(times)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(times)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": cfg,
+        "solves_per_s": solves_per_s,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "iters": last["iters"], "outer": last["outer"],
+        "AH_rel_err_vs_oracle": err_mixed,
+        "fp64_plain": fp64,
+        "speedup_vs_fp64_plain_solves": solves_per_s / ws / fp64["solves_per_s"],
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * hg.h -- C ABI of the GB300 FFT-Galerkin homogenization library (libhg.so).
+ *
+ * The library solves the cell problem of periodic homogenization discretised
+ * by trigonometric polynomials with numerical integration (GaNi), following
+ * Vondrejc, Zeman & Marek, "An FFT-based Galerkin method for homogenization
+ * of periodic media" (arXiv:1311.0089):
+ *
+ *   G_N A_N e~ = -G_N A_N E            (Sec. 5.2, Eq. final_system, A0 = I)
+ *
+ * by conjugate gradients (Sec. 5.3, Lemma on CG), where A_N is the pointwise
+ * coefficient matrix at the grid points (Sec. 5.1), G_N = F^-1 Gamma_hat F A0
+ * (Eq. FFT_matrices) and Gamma_hat(k) = xi xi^T / (A0 xi . xi), zero at k = 0
+ * (Sec. 3, Eq. Gamma_hat).  For each macroscopic load E = e_j it returns the
+ * fluctuation e~_j and the homogenized matrix
+ *
+ *   A_H[i][j] = (A_N (E_j + e~_j), E_i + e~_i)    (energy of Eq. forms_def1;
+ *                                                   the paper does not define A_H)
+ *
+ * with the scalar product (u,v) = 1/|N| sum_k u^k . v^k of Sec. 5.1.
+ *
+ * Conventions common to every call:
+ *   - Status codes only (hg_status); nothing aborts, traps or throws.
+ *   - Grids: d in {2,3}; every N_a odd (assumption A4, Sec. 4.1), a product
+ *     of the primes 3, 5 and 7 (a limit of this library's FFT kernels, not of
+ *     the paper), 1 <= N_a <= 1024.
+ *   - Arrays are C order, first index slowest.  A field of d components is
+ *     stored component-major: u[a * |N| + k] (d x |N| doubles).
+ *   - The library owns every device buffer it allocates; coefficient arrays
+ *     passed in are copied, the caller keeps ownership of its pointers.
+ *   - "on_device" flags say whether a pointer is a device pointer (1) or a
+ *     host pointer (0).  Host pointers are copied through the context stream.
+ *   - Every call that launches work runs on the context's stream and returns
+ *     after that work has completed, unless documented otherwise.
+ */
+#ifndef HG_H
+#define HG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hg_ctx hg_ctx;
+typedef struct hg_grid hg_grid;
+
+typedef enum {
+    HG_OK = 0,
+    HG_PENDING = 1,                 /* hg_poll: the ticket is still running      */
+    HG_ERR_ARG = -1,                /* null pointer, bad enum, d not in {2,3}     */
+    HG_ERR_UNSUPPORTED_SIZE = -2,   /* even N_a (A4) or prime factor not 3/5/7   */
+    HG_ERR_NOT_SPD = -3,            /* a coefficient tensor is not symmetric PD  */
+    HG_ERR_NO_MEMORY = -4,          /* device allocation or the ctx budget failed */
+    HG_ERR_NOT_CONVERGED = -5,      /* max_iter reached; best iterate is kept     */
+    HG_ERR_DEVICE_TIMEOUT = -6,     /* a bounded device-side wait gave up         */
+    HG_ERR_BUSY = -7,               /* grid borrowed by a pending ticket          */
+    HG_ERR_CUDA = -8,               /* a CUDA runtime call failed                 */
+    HG_ERR_CANCELLED = -9,          /* the ticket was cancelled                   */
+    HG_ERR_BREAKDOWN = -10,         /* CG breakdown: (p, A p) <= 0 or not finite   */
+    HG_ERR_NO_COEFFS = -11          /* solve requested before hg_set_coeffs*       */
+} hg_status;
+
+typedef enum {
+    HG_FP64 = 0,    /* every step in FP64 */
+    HG_MIXED = 1    /* FP32 FFTs/products/axpys, FP64 dots, FP64 outer residual
+                       and A_H (iterative refinement) */
+} hg_precision;
+
+typedef enum {
+    HG_COEFF_FULL = 0,    /* |N| x d x d doubles, voxel-major, symmetric      */
+    HG_COEFF_PACKED = 1   /* d(d+1)/2 x |N| doubles, component-major; the
+                             packed order is (11,22[,33],12[,13,23])          */
+} hg_coeff_layout;
+
+typedef struct {
+    double tol;          /* stop when ||r_i|| / ||b|| <= tol (default 1e-10)     */
+    int max_iter;        /* CG iterations per load (default 10000)              */
+    int prec;            /* hg_precision (default HG_FP64)                      */
+    double lambda_ref;   /* A0 = lambda I; the system does not depend on it
+                            (Lemma FD_projection (v)); kept for the record     */
+    unsigned loads_mask; /* bit j set: solve load E = e_j (default all)        */
+    double inner_tol;    /* HG_MIXED: relative tolerance of each FP32 inner solve
+                            (default 1e-4)                                      */
+    int check_every;     /* iterations between host reads of the convergence
+                            flags (default 8); each chunk is one CUDA graph    */
+    int max_outer;       /* HG_MIXED: refinement steps (default 30)            */
+} hg_solve_opts;
+
+typedef struct {
+    int status;             /* hg_status of the solve                          */
+    int d;
+    double AH[9];           /* d x d row-major energy form                     */
+    double AH_flux[9];      /* d x d mean-flux form <A e_j>_i (check)          */
+    int iters[3];           /* CG iterations per load (HG_MIXED: inner FP32
+                               iterations summed over refinement steps)        */
+    int outer[3];           /* HG_MIXED: FP64 residual evaluations per load    */
+    double rel_res[3];      /* final ||r|| / ||b|| (FP64 true residual for
+                               HG_MIXED, recursive residual for HG_FP64)       */
+    double device_ms;       /* time of the solve on the context stream         */
+    double wall_ms;         /* host wall time of the call                      */
+    long long launches;     /* kernels launched by this solve                  */
+} hg_result;
+
+/* Fill opts with the defaults listed above. */
+void hg_default_opts(hg_solve_opts* opts);
+
+/* Context: one device, one stream.  cuda_stream = NULL creates an owned
+ * non-blocking stream; otherwise the given cudaStream_t is used (borrowed).
+ * mem_budget_bytes = 0 means no budget; otherwise device allocations made
+ * through this context beyond the budget fail with HG_ERR_NO_MEMORY. */
+int hg_create(hg_ctx** out, int device, size_t mem_budget_bytes, void* cuda_stream);
+/* Fails with HG_ERR_BUSY while grids created on ctx are still alive. */
+int hg_destroy(hg_ctx* ctx);
+
+/* Grid of Sec. 4.1: d axes of N[a] points on the cell prod_a [-Y_a, Y_a]
+ * (Y = NULL: all Y_a = 1).  xi(k) = (k_a / Y_a)_a (Sec. 2).  Allocates the
+ * plans and twiddle tables; work buffers are allocated on first solve. */
+int hg_create_grid(hg_ctx* ctx, int d, const int* N, const double* Y, hg_grid** out);
+int hg_destroy_grid(hg_grid* grid);   /* HG_ERR_BUSY if a ticket holds it */
+
+/* Coefficients A(x_k) of Sec. 5.1 (A_N), assumptions A1-A2 (Sec. 3): symmetric
+ * positive definite per voxel.  Copied into device memory.  Symmetry and
+ * positive definiteness are checked on the host for every voxel (device inputs
+ * are staged through host memory for the check); a violation returns
+ * HG_ERR_NOT_SPD and leaves the previous coefficients. */
+int hg_set_coeffs(hg_grid* grid, const double* A, int layout, int on_device);
+
+/* Coefficients as a phase map: phase[k] in [0, n_phases) per voxel (uint8),
+ * table = n_phases x d x d doubles (row-major, each SPD).  1 <= n_phases <= 256. */
+int hg_set_coeffs_phase(hg_grid* grid, const uint8_t* phase, int n_phases,
+                        const double* table, int on_device);
+
+/* Blocking solve of Eq. final_system for the loads in opts->loads_mask and
+ * assembly of A_H (rows/columns of unsolved loads are left 0).  AH_out may be
+ * NULL (d*d doubles, row-major); info may be NULL. */
+int hg_solve_AH(hg_grid* grid, const hg_solve_opts* opts, double* AH_out, hg_result* info);
+
+/* Copy e~_load of the last solve (d x |N| doubles, component-major). */
+int hg_get_field(hg_grid* grid, int load, double* e_out, int on_device);
+
+/* Asynchronous solve through the context's scheduler (continuous batching:
+ * iterations of all admitted requests run together).  The grid is borrowed
+ * until the ticket completes or is cancelled.  Admission waits for memory
+ * within the context budget. */
+int hg_submit(hg_ctx* ctx, hg_grid* grid, const hg_solve_opts* opts, uint64_t* ticket);
+/* HG_PENDING while running; otherwise fills *out and releases the ticket.
+ * timeout_us = 0 polls once; < 0 waits without limit. */
+int hg_poll(hg_ctx* ctx, uint64_t ticket, hg_result* out, int timeout_us);
+int hg_cancel(hg_ctx* ctx, uint64_t ticket);
+
+/* ---- operator-level entry points (parity tests and diagnostics) ---------- */
+
+/* out = G_N A_N u (with_A = 1) or out = G_N u (with_A = 0), for one d x |N|
+ * field, with G_N = F^-1 Gamma_hat F A0 (Eq. FFT_matrices).  A0 = NULL means
+ * I; otherwise a d x d SPD matrix (row-major).  prec = hg_precision: HG_MIXED
+ * runs the FP32 kernels (inputs/outputs still FP64 at the boundary). */
+int hg_apply(hg_grid* grid, const double* u, double* out, int with_A,
+             const double* A0, int prec, int on_device);
+
+/* Forward DFT of Eq. DFT_def (with 1/|N|) of a real d x |N| field, returned as
+ * the half spectrum over the last axis: d x (|N|/N_d) x ((N_d+1)/2) complex
+ * values, interleaved (re, im) doubles; bin j of an axis holds frequency
+ * j or j - N_a (Sec. 4.1); the last axis keeps j = 0..(N_d-1)/2. */
+int hg_spectrum(hg_grid* grid, const double* u, double* S_out, int prec, int on_device);
+
+/* Kernel launches made through this context so far (all entry points). */
+long long hg_launch_count(hg_ctx* ctx);
+
+/* Time `reps` back-to-back launches of one pass of the CG iteration on the
+ * grid's current state with CUDA events on the context stream.
+ * pass: 0 = first-axis forward pass (A.p product + FFT), 1.. = strided-axis
+ * passes in launch order, last = last-axis inverse pass (update).  Writes the
+ * mean milliseconds per launch and the pass name (<= 63 chars). */
+int hg_time_pass(hg_grid* grid, int prec, int pass, int reps, double* ms_out,
+                 char* name_out);
+int hg_num_passes(hg_grid* grid);
+
+const char* hg_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HG_H */

@@ -1,0 +1,193 @@
+// Device-side mixed-radix (3/5/7) Stockham FFT on pencils staged in shared
+// memory.  The DFT convention is Eq. DFT_def (Sec. 4.1): the forward kernel is
+// omega^{-km} = exp(-2 pi i k m / N), the inverse exp(+2 pi i k m / N); both are
+// unnormalised here (the 1/|N| of the forward transform is folded into the
+// Fourier projection by the callers).
+//
+// A stage of radix R with Ns = product of the radices already applied maps,
+// for every butterfly j in [0, N/R) with k = j mod Ns,
+//     v_r = x[j + r N/R] * W_N^{r k N/(Ns R)}     (r = 0..R-1, W_N = e^{-2 pi i/N})
+//     y   = DFT_R(v)
+//     x'[(j / Ns) Ns R + k + r Ns] = y_r
+// (the self-sorting Stockham formulation: no bit/digit reversal pass).  The
+// stage is done in place: every thread first loads all of its butterflies
+// into registers, the block synchronises, then every thread stores.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <type_traits>
+#include "hg_internal.h"
+
+namespace hgk {
+
+template <typename T> struct cplx_t;
+template <> struct cplx_t<double> { typedef double2 type; };
+template <> struct cplx_t<float>  { typedef float2 type; };
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2  cadd(float2 a, float2 b)   { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2  csub(float2 a, float2 b)   { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2  cscale(float2 a, float s)   { return make_float2(a.x * s, a.y * s); }
+// a * w  (CONJ: a * conj(w))
+template <bool CONJ> __device__ __forceinline__ double2 cmulw(double2 a, double2 w) {
+    return CONJ ? make_double2(fma(a.x, w.x, a.y * w.y), fma(a.y, w.x, -a.x * w.y))
+                : make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+}
+template <bool CONJ> __device__ __forceinline__ float2 cmulw(float2 a, float2 w) {
+    return CONJ ? make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y))
+                : make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+
+// Constants cos/sin(2 pi k / R), written out to 20 digits from their closed
+// forms (R = 3: sqrt(3)/2; R = 5: (sqrt(5)-1)/4 etc.).
+#define HG_S3   0.86602540378443864676   // sin(2pi/3)
+#define HG_C51  0.30901699437494742410   // cos(2pi/5)
+#define HG_C52 -0.80901699437494742410   // cos(4pi/5)
+#define HG_S51  0.95105651629515357212   // sin(2pi/5)
+#define HG_S52  0.58778525229247312917   // sin(4pi/5)
+#define HG_C71  0.62348980185873353053   // cos(2pi/7)
+#define HG_C72 -0.22252093395631440429   // cos(4pi/7)
+#define HG_C73 -0.90096886790241912624   // cos(6pi/7)
+#define HG_S71  0.78183148246802980871   // sin(2pi/7)
+#define HG_S72  0.97492791218182360702   // sin(4pi/7)
+#define HG_S73  0.43388373911755812048   // sin(6pi/7)
+
+// y = x0 + c * (a) - i * s  with s complex: returns (t.x + s.y, t.y - s.x) for
+// the forward sign; INV flips the sign of the i-term.
+template <bool INV, typename C>
+__device__ __forceinline__ void pm_i(C t, C s, C& ym, C& yp) {
+    // ym = t - i s, yp = t + i s   (forward);  swapped for the inverse
+    C a, b;
+    a.x = t.x + s.y; a.y = t.y - s.x;
+    b.x = t.x - s.y; b.y = t.y + s.x;
+    if (INV) { ym = b; yp = a; } else { ym = a; yp = b; }
+}
+
+template <int R, bool INV, typename C> struct Dft;
+
+template <bool INV, typename C> struct Dft<3, INV, C> {
+    __device__ __forceinline__ static void run(C* v) {
+        typedef decltype(C().x) T;
+        C s = cadd(v[1], v[2]);
+        C dd = csub(v[1], v[2]);
+        C m; m.x = v[0].x - T(0.5) * s.x; m.y = v[0].y - T(0.5) * s.y;
+        v[0] = cadd(v[0], s);
+        C sd = cscale(dd, T(HG_S3));
+        pm_i<INV>(m, sd, v[1], v[2]);
+    }
+};
+
+template <bool INV, typename C> struct Dft<5, INV, C> {
+    __device__ __forceinline__ static void run(C* v) {
+        typedef decltype(C().x) T;
+        C a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+        C a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+        C x0 = v[0];
+        C t1, t2, u1, u2;
+        t1.x = x0.x + T(HG_C51) * a1.x + T(HG_C52) * a2.x;
+        t1.y = x0.y + T(HG_C51) * a1.y + T(HG_C52) * a2.y;
+        t2.x = x0.x + T(HG_C52) * a1.x + T(HG_C51) * a2.x;
+        t2.y = x0.y + T(HG_C52) * a1.y + T(HG_C51) * a2.y;
+        u1.x = T(HG_S51) * b1.x + T(HG_S52) * b2.x;
+        u1.y = T(HG_S51) * b1.y + T(HG_S52) * b2.y;
+        u2.x = T(HG_S52) * b1.x - T(HG_S51) * b2.x;
+        u2.y = T(HG_S52) * b1.y - T(HG_S51) * b2.y;
+        v[0] = cadd(x0, cadd(a1, a2));
+        C y1, y4, y2, y3;
+        pm_i<INV>(t1, u1, y1, y4);
+        pm_i<INV>(t2, u2, y2, y3);
+        v[1] = y1; v[2] = y2; v[3] = y3; v[4] = y4;
+    }
+};
+
+template <bool INV, typename C> struct Dft<7, INV, C> {
+    __device__ __forceinline__ static void run(C* v) {
+        typedef decltype(C().x) T;
+        C a1 = cadd(v[1], v[6]), b1 = csub(v[1], v[6]);
+        C a2 = cadd(v[2], v[5]), b2 = csub(v[2], v[5]);
+        C a3 = cadd(v[3], v[4]), b3 = csub(v[3], v[4]);
+        C x0 = v[0];
+        C t1, t2, t3, u1, u2, u3;
+        // y_m = x0 + sum_k cos(2 pi m k/7) a_k -/+ i sum_k sin(2 pi m k/7) b_k
+        t1.x = x0.x + T(HG_C71) * a1.x + T(HG_C72) * a2.x + T(HG_C73) * a3.x;
+        t1.y = x0.y + T(HG_C71) * a1.y + T(HG_C72) * a2.y + T(HG_C73) * a3.y;
+        t2.x = x0.x + T(HG_C72) * a1.x + T(HG_C73) * a2.x + T(HG_C71) * a3.x;
+        t2.y = x0.y + T(HG_C72) * a1.y + T(HG_C73) * a2.y + T(HG_C71) * a3.y;
+        t3.x = x0.x + T(HG_C73) * a1.x + T(HG_C71) * a2.x + T(HG_C72) * a3.x;
+        t3.y = x0.y + T(HG_C73) * a1.y + T(HG_C71) * a2.y + T(HG_C72) * a3.y;
+        u1.x = T(HG_S71) * b1.x + T(HG_S72) * b2.x + T(HG_S73) * b3.x;
+        u1.y = T(HG_S71) * b1.y + T(HG_S72) * b2.y + T(HG_S73) * b3.y;
+        u2.x = T(HG_S72) * b1.x - T(HG_S73) * b2.x - T(HG_S71) * b3.x;
+        u2.y = T(HG_S72) * b1.y - T(HG_S73) * b2.y - T(HG_S71) * b3.y;
+        u3.x = T(HG_S73) * b1.x - T(HG_S71) * b2.x + T(HG_S72) * b3.x;
+        u3.y = T(HG_S73) * b1.y - T(HG_S71) * b2.y + T(HG_S72) * b3.y;
+        v[0] = cadd(x0, cadd(a1, cadd(a2, a3)));
+        C y1, y6, y2, y5, y3, y4;
+        pm_i<INV>(t1, u1, y1, y6);
+        pm_i<INV>(t2, u2, y2, y5);
+        pm_i<INV>(t3, u3, y3, y4);
+        v[1] = y1; v[2] = y2; v[3] = y3; v[4] = y4; v[5] = y5; v[6] = y6;
+    }
+};
+
+// One in-place Stockham stage over `npen` pencils of length n stored at
+// buf + p * pstride.  MAXB butterflies per thread at most (host guarantees
+// blockDim.x * MAXB >= npen * n / R).
+template <typename T, int R, bool INV, int MAXB>
+__device__ __forceinline__ void stage(typename cplx_t<T>::type* buf, int npen, int pstride,
+                                      int n, int Ns, const typename cplx_t<T>::type* __restrict__ tw) {
+    typedef typename cplx_t<T>::type C;
+    const int nb = n / R;
+    const int total = npen * nb;
+    const int twstep = n / (Ns * R);
+    C v[MAXB][R];
+    int dst[MAXB];
+#pragma unroll
+    for (int b = 0; b < MAXB; ++b) {
+        int idx = threadIdx.x + b * blockDim.x;
+        dst[b] = -1;
+        if (idx < total) {
+            int pen = idx / nb;
+            int j = idx - pen * nb;
+            int k = j % Ns;
+            const C* src = buf + pen * pstride + j;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b][r] = src[r * nb];
+            if (Ns > 1) {
+                int step = k * twstep;
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[b][r] = cmulw<INV>(v[b][r], __ldg(&tw[r * step]));
+            }
+            Dft<R, INV, C>::run(v[b]);
+            dst[b] = pen * pstride + (j - k) * R + k;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < MAXB; ++b) {
+        if (dst[b] >= 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[dst[b] + r * Ns] = v[b][r];
+        }
+    }
+    __syncthreads();
+}
+
+// Full transform of npen pencils (forward: INV = false).
+template <typename T, bool INV, int MAXB>
+__device__ void fft_pencils(typename cplx_t<T>::type* buf, int npen, int pstride,
+                            const AxisPlanH& pl, const typename cplx_t<T>::type* __restrict__ twall) {
+    const typename cplx_t<T>::type* tw = twall + pl.tw_off;
+    int Ns = 1;
+    for (int s = 0; s < pl.nstages; ++s) {
+        int R = pl.radix[s];
+        if (R == 3)      stage<T, 3, INV, MAXB>(buf, npen, pstride, pl.n, Ns, tw);
+        else if (R == 5) stage<T, 5, INV, MAXB>(buf, npen, pstride, pl.n, Ns, tw);
+        else             stage<T, 7, INV, MAXB>(buf, npen, pstride, pl.n, Ns, tw);
+        Ns *= R;
+    }
+}
+
+}  // namespace hgk

@@ -1,0 +1,572 @@
+// Host runtime of libhg: contexts, grids, FFT plans, device buffers, the
+// CUDA-graph-captured CG loop, mixed-precision refinement and the request
+// scheduler behind hg_submit / hg_poll.  See include/hg.h for the contract.
+#include "hg.h"
+#include "hg_internal.h"
+#include "hg_runtime.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+using namespace hgk;
+
+namespace hgrt {
+
+// ----------------------------------------------------------------------------
+// helpers
+// ----------------------------------------------------------------------------
+static double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+#define HG_CU(call)                                  \
+    do {                                             \
+        cudaError_t _e = (call);                     \
+        if (_e != cudaSuccess) {                     \
+            set_last_cuda_error(_e, #call);          \
+            return HG_ERR_CUDA;                      \
+        }                                            \
+    } while (0)
+
+static thread_local char g_last_err[256];
+void set_last_cuda_error(cudaError_t e, const char* what) {
+    snprintf(g_last_err, sizeof(g_last_err), "%s: %s", what, cudaGetErrorString(e));
+}
+const char* last_cuda_error() { return g_last_err; }
+
+int dev_alloc(hg_ctx* ctx, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (ctx->budget) {
+        size_t cur = ctx->used.load();
+        if (cur + bytes > ctx->budget) return HG_ERR_NO_MEMORY;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return HG_ERR_NO_MEMORY;
+    }
+    ctx->used += bytes;
+    ctx->alloc_sizes[*p] = bytes;
+    return HG_OK;
+}
+
+void dev_free(hg_ctx* ctx, void* p) {
+    if (!p) return;
+    auto it = ctx->alloc_sizes.find(p);
+    if (it != ctx->alloc_sizes.end()) {
+        ctx->used -= it->second;
+        ctx->alloc_sizes.erase(it);
+    }
+    cudaFree(p);
+}
+
+// Factor n into radices 3, 5, 7 (application order: 3s, then 5s, then 7s).
+static bool factor(int n, AxisPlanH& pl) {
+    pl.n = n;
+    pl.nstages = 0;
+    int m = n;
+    for (int r : {3, 5, 7}) {
+        while (m % r == 0) {
+            if (pl.nstages >= 16) return false;
+            pl.radix[pl.nstages++] = r;
+            m /= r;
+        }
+    }
+    return m == 1;
+}
+
+static int min_radix(const AxisPlanH& pl) {
+    int r = 7;
+    for (int s = 0; s < pl.nstages; ++s) r = std::min(r, pl.radix[s]);
+    return pl.nstages ? r : 1;
+}
+
+// Row pass: choose loads-per-CTA LB and rows-per-CTA RB.
+static bool choose_row_cfg(int n, int d, int L, int minR, size_t csize, int max_smem, long long rows,
+                           RowCfg& cfg) {
+    const int maxb = 2, maxt = row_max_threads();
+    const size_t target = 32 * 1024;
+    for (int LB = L; LB >= 1; --LB) {
+        int bestRB = 0;
+        for (int RB = 1; RB <= 64; ++RB) {
+            const int nreal = RB * LB * d;
+            const int ncplx = (nreal + 1) / 2;
+            const long long bfly = (long long)ncplx * n / std::max(minR, 1);
+            const size_t smem = (size_t)ncplx * n * csize;
+            if (bfly > (long long)maxb * maxt || smem > (size_t)max_smem) break;
+            if (RB > 1 && (smem > target || rows / RB < 2 * 152)) break;
+            if (RB > rows) break;
+            bestRB = RB;
+        }
+        if (bestRB > 0) {
+            const int nreal = bestRB * LB * d;
+            const int ncplx = (nreal + 1) / 2;
+            const long long bfly = std::max<long long>((long long)ncplx * n / std::max(minR, 1), 1);
+            int thr = (int)((bfly + maxb - 1) / maxb);
+            thr = std::max(64, std::min(maxt, ((thr + 31) / 32) * 32));
+            cfg.RB = bestRB;
+            cfg.LB = LB;
+            cfg.threads = thr;
+            cfg.smem = (int)((size_t)ncplx * n * csize);
+            cfg.nbx = (rows + bestRB - 1) / bestRB;
+            cfg.nby = (L + LB - 1) / LB;
+            return true;
+        }
+    }
+    return false;
+}
+
+static bool choose_str_cfg(int n, int d, int minR, size_t csize, int max_smem, long long inner,
+                           int prefer_lanes, StrCfg& cfg) {
+    const int maxb = 2, maxt = row_max_threads();
+    int best = 0;
+    for (int Cl = 1; Cl <= 32; ++Cl) {
+        const long long bfly = (long long)d * Cl * n / std::max(minR, 1);
+        const size_t smem = (size_t)d * Cl * n * csize;
+        if (bfly > (long long)maxb * maxt || smem > (size_t)max_smem) break;
+        if (Cl > 1 && (Cl > prefer_lanes || Cl > inner)) break;
+        best = Cl;
+    }
+    if (!best) return false;
+    const long long bfly = std::max<long long>((long long)d * best * n / std::max(minR, 1), 1);
+    int thr = (int)((bfly + maxb - 1) / maxb);
+    thr = std::max(64, std::min(maxt, ((thr + 31) / 32) * 32));
+    cfg.Cl = best;
+    cfg.threads = thr;
+    cfg.smem = (int)((size_t)d * best * n * csize);
+    return true;
+}
+
+// ----------------------------------------------------------------------------
+// grid construction
+// ----------------------------------------------------------------------------
+int grid_init_plans(hg_grid* g) {
+    GridDev& gd = g->gd;
+    const int d = gd.d;
+    // twiddles, one table per distinct length
+    std::map<int, int> off;
+    std::vector<double> tw64;
+    for (int a = 0; a < d; ++a) {
+        const int n = gd.N[a];
+        if (!factor(n, g->plan[a])) return HG_ERR_UNSUPPORTED_SIZE;
+        if (!off.count(n)) {
+            off[n] = (int)(tw64.size() / 2);
+            for (int m = 0; m < n; ++m) {
+                // W_n^m = exp(-2 pi i m / n), evaluated in extended precision
+                const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)m / (long double)n;
+                tw64.push_back((double)cosl(ang));
+                tw64.push_back((double)sinl(ang));
+            }
+        }
+        g->plan[a].tw_off = off[n];
+    }
+    std::vector<float> tw32(tw64.size());
+    for (size_t i = 0; i < tw64.size(); ++i) tw32[i] = (float)tw64[i];
+    int st = dev_alloc(g->ctx, &g->tw[0], tw64.size() * sizeof(double));
+    if (st) return st;
+    st = dev_alloc(g->ctx, &g->tw[1], tw32.size() * sizeof(float));
+    if (st) return st;
+    HG_CU(cudaMemcpyAsync(g->tw[0], tw64.data(), tw64.size() * sizeof(double), cudaMemcpyHostToDevice, g->ctx->stream));
+    HG_CU(cudaMemcpyAsync(g->tw[1], tw32.data(), tw32.size() * sizeof(float), cudaMemcpyHostToDevice, g->ctx->stream));
+    HG_CU(cudaStreamSynchronize(g->ctx->stream));
+
+    // launch geometry per precision
+    const int max_smem = g->ctx->max_smem;
+    for (int prec = 0; prec < 2; ++prec) {
+        const size_t cs = prec == 0 ? 16 : 8;
+        const int last = d - 1;
+        if (!choose_row_cfg(gd.Nl, d, d, min_radix(g->plan[last]), cs, max_smem, gd.rows, g->rowcfg[prec]))
+            return HG_ERR_UNSUPPORTED_SIZE;
+        for (int a = 0; a < last; ++a) {
+            long long inner = (a == 0) ? gd.Ms / gd.N[0] : gd.H;  // axis 0: all other axes; axis 1 (3D): last
+            const int prefer = prec == 0 ? 2 : 4;
+            if (!choose_str_cfg(gd.N[a], d, min_radix(g->plan[a]), cs, max_smem, inner, prefer, g->strcfg[prec][a]))
+                return HG_ERR_UNSUPPORTED_SIZE;
+        }
+    }
+    return HG_OK;
+}
+
+int grid_alloc_work(hg_grid* g, int prec) {
+    if (g->work[prec].ready) return HG_OK;
+    const GridDev& gd = g->gd;
+    const int L = gd.d;
+    const size_t ts = prec == 0 ? 8 : 4;
+    const size_t nv = (size_t)L * gd.d * gd.M;
+    const size_t ns = (size_t)L * gd.d * gd.Ms;
+    Work& w = g->work[prec];
+    int st;
+    if ((st = dev_alloc(g->ctx, &w.x, nv * ts))) return st;
+    if ((st = dev_alloc(g->ctx, &w.r, nv * ts))) return st;
+    if ((st = dev_alloc(g->ctx, &w.p, nv * ts))) return st;
+    if ((st = dev_alloc(g->ctx, &w.S, ns * 2 * ts))) return st;
+    if ((st = dev_alloc(g->ctx, (void**)&w.sc, sizeof(Scalars) * MAXL))) return st;
+    HG_CU(cudaMemsetAsync(w.sc, 0, sizeof(Scalars) * MAXL, g->ctx->stream));
+    HG_CU(cudaMemsetAsync(w.x, 0, nv * ts, g->ctx->stream));
+    HG_CU(cudaMemsetAsync(w.p, 0, nv * ts, g->ctx->stream));
+    w.ready = true;
+    return HG_OK;
+}
+
+// Releases the solver state (work buffers, graphs that point at them and the
+// reduction scratch); the plans, twiddles and coefficients stay.
+void grid_free_work(hg_grid* g) {
+    hg_ctx* c = g->ctx;
+    for (int p = 0; p < 2; ++p) {
+        if (g->graphs[p].exec) cudaGraphExecDestroy(g->graphs[p].exec);
+        g->graphs[p] = GraphCache();
+        Work& w = g->work[p];
+        dev_free(c, w.x); dev_free(c, w.r); dev_free(c, w.p); dev_free(c, w.S); dev_free(c, w.sc);
+        w = Work();
+    }
+    dev_free(c, g->partial); g->partial = nullptr;
+    dev_free(c, g->counters); g->counters = nullptr;
+    dev_free(c, g->d_AH); g->d_AH = nullptr;
+    dev_free(c, g->d_E); g->d_E = nullptr;
+    dev_free(c, g->d_A0); g->d_A0 = nullptr;
+}
+
+int grid_alloc_common(hg_grid* g) {
+    if (g->partial) return HG_OK;
+    const GridDev& gd = g->gd;
+    long long slots = std::max<long long>(g->rowcfg[0].nbx, g->rowcfg[1].nbx) * MAXL;
+    slots = std::max<long long>(slots, 18LL * 8 * 1024);
+    int st;
+    if ((st = dev_alloc(g->ctx, (void**)&g->partial, slots * sizeof(double)))) return st;
+    g->partial_slots = slots;
+    if ((st = dev_alloc(g->ctx, (void**)&g->counters, 16 * sizeof(unsigned)))) return st;
+    HG_CU(cudaMemsetAsync(g->counters, 0, 16 * sizeof(unsigned), g->ctx->stream));
+    if ((st = dev_alloc(g->ctx, (void**)&g->d_AH, 32 * sizeof(double)))) return st;
+    if ((st = dev_alloc(g->ctx, (void**)&g->d_E, MAXL * MAXD * sizeof(double)))) return st;
+    double E[MAXL * MAXD] = {0};
+    for (int l = 0; l < gd.d; ++l) E[l * gd.d + l] = 1.0;
+    HG_CU(cudaMemcpyAsync(g->d_E, E, sizeof(E), cudaMemcpyHostToDevice, g->ctx->stream));
+    if ((st = dev_alloc(g->ctx, (void**)&g->d_A0, 16 * sizeof(double)))) return st;
+    HG_CU(cudaStreamSynchronize(g->ctx->stream));
+    (void)gd;
+    return HG_OK;
+}
+
+CoeffsDev coeffs_for(const hg_grid* g, int prec, bool withA) {
+    CoeffsDev c;
+    c.phase = g->d_phase;
+    c.table = g->d_table[prec];
+    c.field = g->d_field[prec];
+    c.mode = !withA ? 2 : (g->coeff_mode == 0 ? 0 : 1);
+    return c;
+}
+
+// ----------------------------------------------------------------------------
+// pass enqueueing (every CG iteration / operator application)
+// ----------------------------------------------------------------------------
+int enqueue_forward_strided(hg_grid* g, int prec, int L, int check_status, int gamma_mode,
+                            const double* A0, cudaStream_t s) {
+    // 3D: axis 1 forward, axis 0 (fwd + Gamma + inv | fwd+scale), axis 1 inverse
+    const GridDev& gd = g->gd;
+    Work& w = g->work[prec];
+    const int d = gd.d;
+    StrArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.L = L;
+    sa.S = w.S;
+    sa.sc = w.sc;
+    sa.check_status = check_status;
+    if (A0) {
+        sa.has_A0 = 1;
+        for (int i = 0; i < d * d; ++i) sa.A0[i] = A0[i];
+    }
+    if (d == 3) {
+        sa.mode = STR_FWD; sa.axis = 1; sa.outer = gd.N[0]; sa.n = gd.N[1]; sa.inner = gd.H;
+        HG_CU(launch_strided(prec, gd, g->plan[1], g->tw[prec], g->strcfg[prec][1], sa, s));
+        g->ctx->launches++;
+    }
+    sa.mode = gamma_mode; sa.axis = 0; sa.outer = 1; sa.n = gd.N[0]; sa.inner = gd.Ms / gd.N[0];
+    HG_CU(launch_strided(prec, gd, g->plan[0], g->tw[prec], g->strcfg[prec][0], sa, s));
+    g->ctx->launches++;
+    if (d == 3 && gamma_mode == STR_GAMMA) {
+        sa.mode = STR_INV; sa.axis = 1; sa.outer = gd.N[0]; sa.n = gd.N[1]; sa.inner = gd.H;
+        HG_CU(launch_strided(prec, gd, g->plan[1], g->tw[prec], g->strcfg[prec][1], sa, s));
+        g->ctx->launches++;
+    }
+    return HG_OK;
+}
+
+int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s) {
+    const GridDev& gd = g->gd;
+    Work& w = g->work[prec];
+    const int last = gd.d - 1;
+    RowFwdArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.mode = FWD_CG; fa.L = L; fa.co = coeffs_for(g, prec, true);
+    fa.p = w.p; fa.r = w.r; fa.S = w.S; fa.sc = w.sc;
+    fa.partial = g->partial; fa.counter = g->counters + 0; fa.check_status = 1;
+    HG_CU(launch_row_fwd(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], fa, s));
+    g->ctx->launches++;
+    int st = enqueue_forward_strided(g, prec, L, 1, STR_GAMMA, nullptr, s);
+    if (st) return st;
+    RowInvArgs ia;
+    memset(&ia, 0, sizeof(ia));
+    ia.mode = INV_CG; ia.L = L; ia.S = w.S; ia.x = w.x; ia.r = w.r; ia.p = w.p;
+    ia.sc = w.sc; ia.partial = g->partial; ia.counter = g->counters + 1; ia.check_status = 1;
+    HG_CU(launch_row_inv(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], ia, s));
+    g->ctx->launches++;
+    return HG_OK;
+}
+
+// q = G A (E + u) followed by the epilogue `inv_mode` (INV_RHS / INV_RESID /
+// INV_OUT); u may be null.
+int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, const double* E, bool withA,
+                   const double* A0dev, const double* A0host, int inv_mode, void* out,
+                   int check_status, cudaStream_t s) {
+    const GridDev& gd = g->gd;
+    Work& w = g->work[prec];
+    const int last = gd.d - 1;
+    RowFwdArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.mode = FWD_APPLY; fa.L = L; fa.co = coeffs_for(g, prec, withA);
+    fa.u = u; fa.E = E; fa.A0 = A0dev; fa.S = w.S; fa.sc = w.sc;
+    fa.partial = g->partial; fa.counter = g->counters + 2; fa.check_status = check_status;
+    HG_CU(launch_row_fwd(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], fa, s));
+    g->ctx->launches++;
+    int st = enqueue_forward_strided(g, prec, L, check_status, STR_GAMMA, A0host, s);
+    if (st) return st;
+    RowInvArgs ia;
+    memset(&ia, 0, sizeof(ia));
+    ia.mode = inv_mode; ia.L = L; ia.S = w.S; ia.x = w.x; ia.r = w.r; ia.p = w.p; ia.out = out;
+    ia.sc = w.sc; ia.partial = g->partial; ia.counter = g->counters + 3; ia.check_status = check_status;
+    HG_CU(launch_row_inv(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], ia, s));
+    g->ctx->launches++;
+    return HG_OK;
+}
+
+// A CUDA graph of `chunk` CG iterations, cached per precision.
+int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nkern) {
+    GraphCache& gc = g->graphs[prec];
+    if (gc.exec && gc.chunk == chunk) {
+        *out = gc.exec;
+        *nkern = gc.nkern;
+        return HG_OK;
+    }
+    if (gc.exec) {
+        cudaGraphExecDestroy(gc.exec);
+        gc.exec = nullptr;
+    }
+    cudaStream_t s = g->ctx->cap_stream;
+    const long long before = g->ctx->launches.load();
+    HG_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int st = HG_OK;
+    for (int i = 0; i < chunk && st == HG_OK; ++i) st = enqueue_cg_iteration(g, prec, g->gd.d, s);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    const long long nk = g->ctx->launches.load() - before;
+    g->ctx->launches -= nk;   // capture is not execution
+    if (st) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess) { set_last_cuda_error(e, "cudaStreamEndCapture"); return HG_ERR_CUDA; }
+    e = cudaGraphInstantiate(&gc.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { set_last_cuda_error(e, "cudaGraphInstantiate"); gc.exec = nullptr; return HG_ERR_CUDA; }
+    gc.chunk = chunk;
+    gc.nkern = (int)nk;
+    *out = gc.exec;
+    *nkern = gc.nkern;
+    return HG_OK;
+}
+
+static int map_status(int s) {
+    switch (s) {
+        case ST_CONVERGED: case ST_ZERO_RHS: case ST_IDLE: return HG_OK;
+        case ST_MAXITER: case ST_ACTIVE: return HG_ERR_NOT_CONVERGED;
+        case ST_BREAKDOWN: return HG_ERR_BREAKDOWN;
+        default: return HG_ERR_CUDA;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// resumable solve (shared by the blocking call and the request scheduler)
+// ----------------------------------------------------------------------------
+// Enqueue one graph chunk of CG iterations of precision `prec`, then the copy
+// of that precision's scalars to pinned host memory and the tick event.
+static int job_launch_chunk(Job& j, int prec) {
+    hg_grid* g = j.g;
+    cudaGraphExec_t ge;
+    int nk = 0;
+    int st = get_cg_graph(g, prec, j.chunk, &ge, &nk);
+    if (st) return st;
+    HG_CU(cudaGraphLaunch(ge, j.s));
+    g->ctx->launches += nk;
+    j.launched += j.chunk;
+    j.cg_prec = prec;
+    HG_CU(cudaMemcpyAsync(g->h_sc, g->work[prec].sc, sizeof(Scalars) * MAXL, cudaMemcpyDeviceToHost, j.s));
+    HG_CU(cudaEventRecord(j.tick, j.s));
+    return HG_OK;
+}
+
+static int job_tick_copy(Job& j, int prec) {
+    HG_CU(cudaMemcpyAsync(j.g->h_sc, j.g->work[prec].sc, sizeof(Scalars) * MAXL, cudaMemcpyDeviceToHost, j.s));
+    HG_CU(cudaEventRecord(j.tick, j.s));
+    return HG_OK;
+}
+
+static bool any_active(const Scalars* h, int L) {
+    for (int l = 0; l < L; ++l)
+        if (h[l].status == ST_ACTIVE) return true;
+    return false;
+}
+
+static int job_start_inner(Job& j) {
+    hg_grid* g = j.g;
+    const GridDev& gd = g->gd;
+    HG_CU(launch_inner_init(gd, gd.d, (const double*)g->work[0].r, (float*)g->work[1].r,
+                            (float*)g->work[1].p, (float*)g->work[1].x, g->work[0].sc, g->work[1].sc,
+                            j.o.inner_tol, j.o.max_iter, g->partial, g->counters + 4, j.s));
+    g->ctx->launches++;
+    j.launched = 0;
+    j.phase = Job::INNER;
+    return job_launch_chunk(j, 1);
+}
+
+static int job_finish_enqueue(Job& j) {
+    hg_grid* g = j.g;
+    const GridDev& gd = g->gd;
+    CoeffsDev c64 = coeffs_for(g, 0, true);
+    HG_CU(launch_energy(gd, gd.d, c64, (const double*)g->work[0].x, j.o.loads_mask, g->partial,
+                        g->counters + 5, g->d_AH, j.s));
+    g->ctx->launches++;
+    HG_CU(cudaEventRecord(j.ev1, j.s));
+    HG_CU(cudaMemcpyAsync(g->h_AH, g->d_AH, sizeof(double) * 2 * gd.d * gd.d, cudaMemcpyDeviceToHost, j.s));
+    j.phase = Job::FINAL;
+    return job_tick_copy(j, 0);
+}
+
+int job_begin(Job& j) {
+    hg_grid* g = j.g;
+    hg_ctx* ctx = g->ctx;
+    const GridDev& gd = g->gd;
+    const int L = gd.d;
+    j.t0 = now_ms();
+    j.launches0 = ctx->launches.load();
+    j.prec = j.o.prec == HG_MIXED ? 1 : 0;
+    j.chunk = std::max(1, j.o.check_every);
+    j.outer = 0;
+    j.launched = 0;
+    j.result = HG_OK;
+    if (g->coeff_mode < 0) return HG_ERR_NO_COEFFS;
+    int st;
+    if ((st = grid_alloc_common(g))) return st;
+    if ((st = grid_alloc_work(g, 0))) return st;
+    if (j.prec == 1 && (st = grid_alloc_work(g, 1))) return st;
+    HG_CU(cudaEventRecord(j.ev0, j.s));
+    int init_st[MAXL];
+    for (int l = 0; l < MAXL; ++l) init_st[l] = (l < L && ((j.o.loads_mask >> l) & 1u)) ? ST_ACTIVE : ST_IDLE;
+    HG_CU(launch_init_scalars(g->work[0].sc, L, init_st, j.o.tol, j.prec ? j.o.max_outer : j.o.max_iter, j.s));
+    ctx->launches++;
+    // b = -G A E  ->  r = p = b, x = 0  (Eq. final_system), in FP64
+    if ((st = enqueue_matvec(g, 0, L, nullptr, g->d_E, true, nullptr, nullptr, INV_RHS, nullptr, 1, j.s))) return st;
+    if (j.prec == 0) {
+        j.phase = Job::PLAIN;
+        return job_launch_chunk(j, 0);
+    }
+    return job_start_inner(j);
+}
+
+// Called once the job's tick event has completed.  Enqueues the next step or
+// completes the job (*done = true, result in j.res).
+int job_advance(Job& j, bool* done) {
+    hg_grid* g = j.g;
+    const GridDev& gd = g->gd;
+    const int L = gd.d;
+    *done = false;
+    const Scalars* h = g->h_sc;
+    switch (j.phase) {
+        case Job::PLAIN:
+        case Job::INNER: {
+            const int mi = j.o.max_iter;
+            if (any_active(h, L) && j.launched <= (long long)mi + 2 * j.chunk)
+                return job_launch_chunk(j, j.cg_prec);
+            if (j.phase == Job::PLAIN) return job_finish_enqueue(j);
+            // x64 += x32, then the FP64 residual r = -G A (E + x)
+            HG_CU(launch_outer_update(gd, L, (double*)g->work[0].x, (const float*)g->work[1].x,
+                                      g->work[0].sc, g->work[1].sc, j.s));
+            g->ctx->launches++;
+            int st = enqueue_matvec(g, 0, L, g->work[0].x, g->d_E, true, nullptr, nullptr, INV_RESID,
+                                    nullptr, 1, j.s);
+            if (st) return st;
+            j.outer++;
+            j.phase = Job::RESID;
+            return job_tick_copy(j, 0);
+        }
+        case Job::RESID:
+            if (any_active(h, L) && j.outer < std::max(1, j.o.max_outer)) return job_start_inner(j);
+            return job_finish_enqueue(j);
+        case Job::FINAL: {
+            float dms = 0.f;
+            cudaEventElapsedTime(&dms, j.ev0, j.ev1);
+            int result = HG_OK;
+            hg_result& r = j.res;
+            memset(&r, 0, sizeof(r));
+            r.d = gd.d;
+            for (int i = 0; i < gd.d * gd.d; ++i) { r.AH[i] = g->h_AH[i]; r.AH_flux[i] = g->h_AH[gd.d * gd.d + i]; }
+            for (int l = 0; l < L; ++l) {
+                const Scalars& sc = h[l];
+                int ms = map_status(sc.status);
+                if (j.prec == 0) {
+                    r.iters[l] = sc.iters;
+                } else {
+                    r.iters[l] = sc.total_iters;
+                    r.outer[l] = sc.iters;
+                }
+                if (ms != HG_OK && result == HG_OK) result = ms;
+                r.rel_res[l] = sc.relres;
+            }
+            r.status = result;
+            r.device_ms = dms;
+            r.wall_ms = now_ms() - j.t0;
+            r.launches = g->ctx->launches.load() - j.launches0;
+            g->last_prec = j.prec;
+            j.result = result;
+            j.phase = Job::DONE;
+            *done = true;
+            return HG_OK;
+        }
+        default:
+            *done = true;
+            return HG_OK;
+    }
+}
+
+int solve_impl(hg_grid* g, const hg_solve_opts* o, double* AH_out, hg_result* info) {
+    Job j;
+    j.g = g;
+    j.o = *o;
+    j.s = g->ctx->stream;
+    j.ev0 = g->ev0;
+    j.ev1 = g->ev1;
+    j.tick = g->ev_tick;
+    int st = job_begin(j);
+    bool done = false;
+    while (st == HG_OK && !done) {
+        HG_CU(cudaEventSynchronize(j.tick));
+        st = job_advance(j, &done);
+    }
+    if (st != HG_OK) {
+        cudaStreamSynchronize(j.s);
+        return st;
+    }
+    if (AH_out) memcpy(AH_out, j.res.AH, sizeof(double) * g->gd.d * g->gd.d);
+    if (info) *info = j.res;
+    return j.result;
+}
+
+}  // namespace hgrt

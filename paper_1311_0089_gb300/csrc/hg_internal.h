@@ -1,0 +1,148 @@
+// Internal interface between the host runtime (hg_api.cpp) and the CUDA
+// kernels (hg_kernels.cu).  Plain structs and pointers only.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hgk {
+
+enum { MAXD = 3, MAXL = 3 };
+
+// Status of one CG system on the device.
+enum {
+    ST_ACTIVE = 0,
+    ST_CONVERGED = 1,
+    ST_ZERO_RHS = 2,
+    ST_MAXITER = 3,
+    ST_BREAKDOWN = 4,
+    ST_IDLE = 5        // not part of this solve (load not requested)
+};
+
+// Per-system CG scalars kept on the device (written by the last CTA of a
+// reduction, read by the following kernels).
+struct Scalars {
+    double rr;       // (r, r) of the current residual
+    double pt;       // (p, A p)
+    double alpha;    // rr / pt
+    double beta;     // rr_new / rr_old (0 before the first step)
+    double bnorm;    // ||b|| of this system
+    double aen;      // ||A E|| (zero right-hand-side test)
+    double relres;   // last ||r|| / ||b||
+    double tol;      // stopping tolerance of this system
+    int iters;
+    int status;
+    int max_iter;
+    int total_iters; // accumulated over refinement steps
+};
+
+struct GridDev {
+    int d;                 // dimension (2 or 3)
+    int N[3];              // axis lengths
+    int Nl;                // last axis length
+    int H;                 // (Nl + 1) / 2
+    long long M;           // |N|
+    long long rows;        // M / Nl
+    long long Ms;          // rows * H (complex half-spectrum entries per component)
+    double Y[3];           // cell half sizes
+    double invM;
+};
+
+struct AxisPlanH {
+    int n;
+    int nstages;
+    int radix[16];
+    int tw_off;
+};
+
+struct CoeffsDev {
+    int mode;                  // 0 phase map, 1 packed field, 2 identity
+    const uint8_t* phase;
+    const void* table;         // n_phases x d x d (T)
+    const void* field;         // npk x M (T), order 11,22[,33],12[,13,23]
+};
+
+// Row (last-axis) pass launch geometry.
+struct RowCfg { int RB; int LB; int threads; int smem; long long nbx; int nby; };
+// Strided-axis pass launch geometry.
+struct StrCfg { int Cl; int threads; int smem; };
+
+enum RowFwdMode { FWD_CG = 0, FWD_APPLY = 1 };
+enum RowInvMode { INV_CG = 0, INV_RHS = 1, INV_OUT = 2, INV_RESID = 3 };
+enum StrMode { STR_FWD = 0, STR_INV = 1, STR_GAMMA = 2, STR_FWD_SCALE = 3 };
+
+struct RowFwdArgs {
+    int mode;
+    int L;                      // systems in this launch (loads)
+    CoeffsDev co;
+    void* p;                    // FWD_CG: in/out search direction [L][d][M]
+    const void* r;              // FWD_CG: residual
+    const void* u;              // FWD_APPLY: input field [L][d][M] or null (= 0)
+    const double* E;            // FWD_APPLY: loads [L][d] or null (= 0)
+    const double* A0;           // FWD_APPLY: d x d reference medium applied after A, or null
+    void* S;                    // out: half spectra [L][d][rows][H]
+    Scalars* sc;                // per system
+    double* partial;            // reduction scratch [L][nbx]
+    unsigned* counter;          // one counter, reset by the last CTA
+    int check_status;           // skip systems that are not ACTIVE
+};
+
+struct StrArgs {
+    int mode;
+    int L;
+    int axis;
+    long long outer, inner;
+    int n;
+    void* S;
+    const Scalars* sc;
+    int check_status;
+    int has_A0;
+    double A0[9];
+};
+
+struct RowInvArgs {
+    int mode;
+    int L;
+    const void* S;
+    void* x;                    // INV_CG / INV_RHS
+    void* r;                    // INV_CG / INV_RHS / INV_RESID
+    void* p;                    // INV_CG (read) / INV_RHS (write)
+    void* out;                  // INV_OUT
+    Scalars* sc;
+    double* partial;
+    unsigned* counter;
+    int check_status;
+};
+
+// Launchers (prec: 0 = double, 1 = float).  Return cudaGetLastError().
+cudaError_t launch_row_fwd(int prec, const GridDev& g, const AxisPlanH& pl, const void* tw,
+                           const RowCfg& cfg, const RowFwdArgs& a, cudaStream_t s);
+cudaError_t launch_strided(int prec, const GridDev& g, const AxisPlanH& pl, const void* tw,
+                           const StrCfg& cfg, const StrArgs& a, cudaStream_t s);
+cudaError_t launch_row_inv(int prec, const GridDev& g, const AxisPlanH& pl, const void* tw,
+                           const RowCfg& cfg, const RowInvArgs& a, cudaStream_t s);
+
+// Small helpers.
+cudaError_t launch_init_scalars(Scalars* sc, int L, const int* status_init, double tol,
+                                int max_iter, cudaStream_t s);
+// Mixed precision: r32 = (float) r64, p32 = r32, x32 = 0, inner scalars from
+// the outer status; reduction of (r32, r32).
+cudaError_t launch_inner_init(const GridDev& g, int L, const double* r64, float* r32, float* p32,
+                              float* x32, const Scalars* outer, Scalars* inner, double inner_tol,
+                              int inner_max, double* partial, unsigned* counter, cudaStream_t s);
+// x64 += x32 for systems whose outer status is ACTIVE; inner iterations are
+// added to the outer totals.
+cudaError_t launch_outer_update(const GridDev& g, int L, double* x64, const float* x32,
+                                Scalars* outer, const Scalars* inner, cudaStream_t s);
+// Energy and flux forms of A_H from the FP64 fluctuations.
+cudaError_t launch_energy(const GridDev& g, int L, const CoeffsDev& co64, const double* x,
+                          unsigned loadmask, double* partial, unsigned* counter, double* out,
+                          cudaStream_t s);
+cudaError_t launch_convert(const void* src, int src_prec, void* dst, int dst_prec, long long n,
+                           cudaStream_t s);
+cudaError_t launch_convert_spectrum(const void* src, int src_prec, double* dst, long long ncomplex,
+                                    cudaStream_t s);
+int row_max_threads();
+int max_dyn_smem_configured(int prec);
+cudaError_t configure_kernels(int max_smem);
+
+}  // namespace hgk

@@ -1,0 +1,127 @@
+// Host-side objects behind the opaque hg_ctx / hg_grid handles.
+#pragma once
+#include "hg.h"
+#include "hg_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+namespace hgrt {
+struct Scheduler;
+}
+
+struct hg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private, always idle: CUDA graph capture
+    bool own_stream = false;
+    size_t budget = 0;
+    std::atomic<size_t> used{0};
+    std::map<void*, size_t> alloc_sizes;
+    std::atomic<long long> launches{0};
+    std::atomic<int> ngrids{0};         // live grids (hg_destroy refuses while > 0)
+    int max_smem = 48 * 1024;
+    std::recursive_mutex mu;            // serialises device work issued by callers
+    hgrt::Scheduler* sched = nullptr;   // request scheduler (hg_submit / hg_poll)
+};
+
+namespace hgrt {
+
+struct Work {
+    void* x = nullptr;
+    void* r = nullptr;
+    void* p = nullptr;
+    void* S = nullptr;
+    hgk::Scalars* sc = nullptr;
+    bool ready = false;
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int chunk = 0;
+    int nkern = 0;
+};
+
+}  // namespace hgrt
+
+struct hg_grid {
+    hg_ctx* ctx = nullptr;
+    hgk::GridDev gd{};
+    hgk::AxisPlanH plan[3]{};
+    hgk::RowCfg rowcfg[2]{};
+    hgk::StrCfg strcfg[2][3]{};
+    void* tw[2] = {nullptr, nullptr};
+    // coefficients
+    int coeff_mode = -1;          // -1 none, 0 phase, 1 packed field
+    int n_phases = 0;
+    uint8_t* d_phase = nullptr;
+    void* d_table[2] = {nullptr, nullptr};
+    void* d_field[2] = {nullptr, nullptr};
+    // solver state
+    hgrt::Work work[2];
+    double* partial = nullptr;
+    long long partial_slots = 0;
+    unsigned* counters = nullptr;
+    double* d_AH = nullptr;
+    double* d_E = nullptr;
+    double* d_A0 = nullptr;
+    hgk::Scalars* h_sc = nullptr;  // pinned: scalars of the last tick
+    double* h_AH = nullptr;        // pinned: 2 d x d (energy, flux)
+    hgrt::GraphCache graphs[2];
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_tick = nullptr;
+    int last_prec = 0;
+    bool counted = false;
+    std::atomic<int> borrowed{0};
+};
+
+namespace hgrt {
+void set_last_cuda_error(cudaError_t e, const char* what);
+const char* last_cuda_error();
+int dev_alloc(hg_ctx* ctx, void** p, size_t bytes);
+void dev_free(hg_ctx* ctx, void* p);
+int grid_init_plans(hg_grid* g);
+int grid_alloc_work(hg_grid* g, int prec);
+int grid_alloc_common(hg_grid* g);
+hgk::CoeffsDev coeffs_for(const hg_grid* g, int prec, bool withA);
+int enqueue_forward_strided(hg_grid* g, int prec, int L, int check_status, int gamma_mode,
+                            const double* A0, cudaStream_t s);
+int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s);
+int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, const double* E, bool withA,
+                   const double* A0dev, const double* A0host, int inv_mode, void* out,
+                   int check_status, cudaStream_t s);
+int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nkern);
+
+// One solve as a resumable state machine: job_begin enqueues the first
+// steps; each time the job's tick event has completed, job_advance reads the
+// copied scalars and enqueues the next steps, until *done.
+struct Job {
+    enum Phase { PLAIN = 0, INNER = 1, RESID = 2, FINAL = 3, DONE = 4 };
+    hg_grid* g = nullptr;
+    hg_solve_opts o{};
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, tick = nullptr;
+    int prec = 0, cg_prec = 0, phase = PLAIN, outer = 0, chunk = 8, result = 0;
+    long long launched = 0, launches0 = 0;
+    double t0 = 0.0;
+    hg_result res{};
+};
+int job_begin(Job& j);
+int job_advance(Job& j, bool* done);
+void grid_free_work(hg_grid* g);
+int solve_impl(hg_grid* g, const hg_solve_opts* o, double* AH_out, hg_result* info);
+
+// scheduler (hg_sched.cpp)
+Scheduler* sched_create(hg_ctx* ctx);
+void sched_destroy(Scheduler* s);
+int sched_submit(Scheduler* s, hg_grid* g, const hg_solve_opts* o, uint64_t* ticket);
+int sched_poll(Scheduler* s, uint64_t ticket, hg_result* out, int timeout_us);
+int sched_cancel(Scheduler* s, uint64_t ticket);
+}  // namespace hgrt

@@ -46,9 +46,28 @@ def laminate():
     }
 
 
+def circles_729():
+    # the 729x729 two-phase workload (40 circles, contrast 100): reference A_H
+    # of the oracle at tol 1e-12, used to state the error of the GPU paths
+    ms = W.circles_2d()
+    res = O.solve_AH(ms.full_field(), ms.N, tol=1e-12)
+    return {
+        "citation": "Sec. 5.2 Eq. final_system solved by CG (Sec. 5.3 Lemma); A_H by the "
+                    "energy form of Eq. forms_def1; workloads.circles_2d() defaults "
+                    "(729x729, 40 seeded circles, phases 1*I and 100*I)",
+        "N": list(ms.N),
+        "tol": 1e-12,
+        "vf": ms.meta["vf"],
+        "AH": res["AH"].tolist(),
+        "iters": res["iters"],
+    }
+
+
 if __name__ == "__main__":
-    for name, fn in (("square_inclusion_15.json", square_inclusion),
-                     ("laminate_9x7.json", laminate)):
+    todo = [("square_inclusion_15.json", square_inclusion), ("laminate_9x7.json", laminate)]
+    if "--large" in sys.argv:
+        todo.append(("circles_729_AH.json", circles_729))
+    for name, fn in todo:
         with open(os.path.join(HERE, name), "w") as f:
             json.dump(fn(), f, indent=1)
         print("wrote", name)

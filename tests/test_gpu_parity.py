@@ -1,0 +1,246 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+GRIDS_2D = [(3, 3), (5, 3), (15, 15), (45, 75), (135, 27), (81, 243), (7, 49), (1, 5), (9, 1), (625, 9)]
+GRIDS_3D = [(3, 3, 3), (5, 3, 7), (15, 9, 25), (27, 45, 21), (1, 3, 5), (7, 1, 9)]
+
+
+def rel_max(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def ctx(hg):
+    c = hg.Context(0)
+    yield c
+    c.close()
+
+
+# ---------------------------------------------------------------- DFT (Eq. DFT_def)
+@pytest.mark.parametrize("N", GRIDS_2D + GRIDS_3D)
+def test_spectrum_fp64_matches_oracle_dft(hg, ctx, N):
+    rng = np.random.default_rng(abs(hash(N)) % 2**32)
+    d = len(N)
+    u = rng.standard_normal((d,) + N)
+    g = ctx.grid(N)
+    S = g.spectrum(u, hg.HG_FP64)
+    ref = O.dft(u, d)[..., : (N[-1] + 1) // 2]
+    assert S.shape == ref.shape
+    assert rel_max(S, ref) < 1e-12
+    g.close()
+
+
+@pytest.mark.parametrize("N", [(45, 75), (15, 9, 25), (729, 15)])
+def test_spectrum_fp32_matches_oracle_dft(hg, ctx, N):
+    rng = np.random.default_rng(5)
+    d = len(N)
+    u = rng.standard_normal((d,) + N)
+    g = ctx.grid(N)
+    S = g.spectrum(u, hg.HG_MIXED)
+    ref = O.dft(u, d)[..., : (N[-1] + 1) // 2]
+    assert rel_max(S, ref) < 2e-6
+    g.close()
+
+
+# ------------------------------------------------------- projection and matvec
+@pytest.mark.parametrize("N", GRIDS_2D[:8] + GRIDS_3D)
+def test_apply_G_and_GA_fp64(hg, ctx, N):
+    rng = np.random.default_rng(11)
+    d = len(N)
+    u = rng.standard_normal((d,) + N)
+    A = W.random_spd_field(N, rng, 1.0, 20.0)
+    g = ctx.grid(N)
+    g.set_coeffs_field(A)
+    np.testing.assert_allclose(g.apply(u, with_A=False), O.apply_gamma(u, N), atol=1e-12)
+    np.testing.assert_allclose(g.apply(u, with_A=True), O.apply_K(A, u, N), atol=1e-11)
+    g.close()
+
+
+def test_apply_general_reference_medium_and_cell(hg, ctx):
+    N, Y = (15, 21), (1.0, 2.5)
+    rng = np.random.default_rng(2)
+    u = rng.standard_normal((2,) + N)
+    A0 = np.array([[3.0, 1.0], [1.0, 2.0]])
+    g = ctx.grid(N, Y)
+    np.testing.assert_allclose(g.apply(u, with_A=False, A0=A0), O.apply_G(u, N, Y, A0), atol=1e-12)
+    np.testing.assert_allclose(g.apply(u, with_A=False), O.apply_gamma(u, N, Y), atol=1e-12)
+    g.close()
+    N3, Y3 = (9, 5, 7), (1.0, 0.5, 2.0)
+    u3 = rng.standard_normal((3,) + N3)
+    A03 = np.array([[2.0, 0.3, 0.1], [0.3, 1.5, 0.2], [0.1, 0.2, 1.0]])
+    g3 = ctx.grid(N3, Y3)
+    np.testing.assert_allclose(g3.apply(u3, with_A=False, A0=A03), O.apply_G(u3, N3, Y3, A03), atol=1e-12)
+    g3.close()
+
+
+@pytest.mark.parametrize("N", [(45, 75), (27, 45, 21)])
+def test_apply_fp32(hg, ctx, N):
+    rng = np.random.default_rng(3)
+    d = len(N)
+    u = rng.standard_normal((d,) + N)
+    ms = W.Microstructure(N, (rng.random(N) < 0.3).astype(np.uint8), W.isotropic_table([1.0, 50.0], d))
+    g = ctx.grid(N)
+    g.set_coeffs_phase(ms.phase, ms.table)
+    ref = O.apply_K(ms.full_field(), u, N)
+    assert rel_max(g.apply(u, prec=hg.HG_MIXED), ref) < 2e-5
+    g.close()
+
+
+# ------------------------------------------------------------------ CG and A_H
+def solve_both(hg, ctx, ms_or_A, N, tol=1e-10, prec=0, table=None, **kw):
+    g = ctx.grid(N)
+    if table is not None:
+        g.set_coeffs_phase(ms_or_A, table)
+        A = W.Microstructure(N, ms_or_A, table).full_field()
+    else:
+        g.set_coeffs_field(ms_or_A)
+        A = ms_or_A
+    res = g.solve(hg.default_opts(tol=tol, prec=prec, **kw))
+    ref = O.solve_AH(A, N, tol=tol)
+    fields = [g.field(j) for j in range(len(N))]
+    g.close()
+    return res, ref, fields
+
+
+def test_square_inclusion_fp64_against_golden_and_oracle(hg, ctx):
+    gold = json.load(open(os.path.join(HERE, "golden", "square_inclusion_15.json")))
+    ms = W.square_inclusion_15()
+    res, ref, fields = solve_both(hg, ctx, ms.phase, ms.N, tol=1e-12, table=ms.table)
+    assert rel_max(res["AH"], np.array(gold["AH"])) < 1e-10
+    assert rel_max(res["AH"], ref["AH"]) < 1e-10
+    assert all(abs(a - b) <= 1 for a, b in zip(res["iters"], ref["iters"]))
+    for j in range(2):
+        np.testing.assert_allclose(fields[j], ref["x"][j], atol=1e-9)
+    np.testing.assert_allclose(res["AH_flux"], res["AH"], atol=1e-9)
+
+
+@pytest.mark.parametrize("N,kind", [((15, 21), "spd"), ((45, 45), "phase"), ((9, 7, 11), "spd"),
+                                    ((15, 15, 15), "phase"), ((81, 5), "phase"), ((3, 3), "spd"),
+                                    ((5, 3, 3), "phase")])
+def test_solve_fp64_parity(hg, ctx, N, kind):
+    rng = np.random.default_rng(sum(N))
+    d = len(N)
+    if kind == "spd":
+        A = W.random_spd_field(N, rng, 1.0, 80.0)
+        res, ref, fields = solve_both(hg, ctx, A, N)
+    else:
+        ph = (rng.random(N) < 0.35).astype(np.uint8)
+        res, ref, fields = solve_both(hg, ctx, ph, N, table=W.isotropic_table([1.0, 100.0], d))
+    assert res["status"] == 0
+    assert rel_max(res["AH"], ref["AH"]) < 1e-8
+    assert all(abs(a - b) <= 2 for a, b in zip(res["iters"], ref["iters"]))
+    for j in range(d):
+        err = np.sqrt(O.inner(fields[j] - ref["x"][j], fields[j] - ref["x"][j]))
+        assert err <= 1e-7 * max(1.0, np.sqrt(O.inner(ref["x"][j], ref["x"][j])))
+
+
+def test_solve_mixed_parity(hg, ctx):
+    ms = W.circles_2d(n=135, count=10, r_lo=5, r_hi=12, contrast=100.0, seed=4)
+    res, ref, _ = solve_both(hg, ctx, ms.phase, ms.N, tol=1e-10, prec=1, table=ms.table)
+    assert res["status"] == 0
+    assert rel_max(res["AH"], ref["AH"]) < 1e-6
+    assert max(res["rel_res"]) <= 1e-10
+    ms3 = W.spheres_3d(n=27, count=6, r_lo=2, r_hi=5, seed=8)
+    res3, ref3, _ = solve_both(hg, ctx, ms3.phase, ms3.N, tol=1e-10, prec=1, table=ms3.table)
+    assert res3["status"] == 0
+    assert rel_max(res3["AH"], ref3["AH"]) < 1e-6
+
+
+def test_laminate_and_homogeneous_exact(hg, ctx):
+    gold = json.load(open(os.path.join(HERE, "golden", "laminate_9x7.json")))
+    ms = W.laminate(tuple(gold["N"]), gold["layers_axis0"])
+    g = ctx.grid(ms.N)
+    g.set_coeffs_phase(ms.phase, ms.table)
+    res = g.solve(hg.default_opts(tol=1e-14))
+    np.testing.assert_allclose(res["AH"], np.array(gold["AH"]), rtol=1e-11, atol=1e-12)
+    assert res["iters"][1] == 0
+    g.close()
+    N = (7, 5, 3)
+    A0 = np.array([[4.0, 1.0, 0.5], [1.0, 3.0, 0.2], [0.5, 0.2, 2.0]])
+    g = ctx.grid(N)
+    g.set_coeffs_phase(np.zeros(N, np.uint8), A0[None])
+    res = g.solve()
+    assert res["iters"] == [0, 0, 0]
+    np.testing.assert_allclose(res["AH"], A0, atol=1e-13)
+    g.close()
+
+
+def test_loads_mask_and_packed_layout(hg, ctx):
+    N = (25, 15)
+    rng = np.random.default_rng(9)
+    A = W.random_spd_field(N, rng, 1.0, 10.0)
+    g = ctx.grid(N)
+    pk = np.stack([A[0, 0].ravel(), A[1, 1].ravel(), A[0, 1].ravel()])
+    g.set_coeffs(pk, hg.HG_COEFF_PACKED)
+    full = g.solve(hg.default_opts(tol=1e-12))
+    only1 = g.solve(hg.default_opts(tol=1e-12, loads_mask=2))
+    assert only1["iters"][0] == 0
+    assert abs(only1["AH"][1, 1] - full["AH"][1, 1]) < 1e-12 * full["AH"][1, 1]
+    assert only1["AH"][0, 0] == 0.0
+    g.close()
+
+
+# ------------------------------------------------------------------ errors
+def test_error_codes(hg, ctx):
+    with pytest.raises(hg.HGError) as e:
+        ctx.grid((4, 5))
+    assert e.value.status == -2
+    with pytest.raises(hg.HGError) as e:
+        ctx.grid((11, 5))          # prime factor 11
+    assert e.value.status == -2
+    g = ctx.grid((5, 5))
+    with pytest.raises(hg.HGError) as e:
+        g.solve()
+    assert e.value.status == -11
+    bad = np.array([[[1.0, 2.0], [2.0, 1.0]]])      # indefinite
+    with pytest.raises(hg.HGError) as e:
+        g.set_coeffs_phase(np.zeros((5, 5), np.uint8), bad)
+    assert e.value.status == -3
+    with pytest.raises(hg.HGError) as e:
+        g.set_coeffs_phase(np.ones((5, 5), np.uint8), np.eye(2)[None])   # phase out of range
+    assert e.value.status == -1
+    g.set_coeffs_phase(np.zeros((5, 5), np.uint8), np.eye(2)[None] * 2.0)
+    res = g.solve(hg.default_opts(max_iter=1), raise_on_error=False)
+    assert res["status"] == 0           # homogeneous: zero right-hand side
+    g.close()
+
+
+def test_not_converged_status(hg, ctx):
+    ms = W.circles_2d(n=45, count=5, r_lo=4, r_hi=8, contrast=1000.0, seed=2)
+    g = ctx.grid(ms.N)
+    g.set_coeffs_phase(ms.phase, ms.table)
+    res = g.solve(hg.default_opts(tol=1e-12, max_iter=3, check_every=2), raise_on_error=False)
+    assert res["status"] == -5
+    assert max(res["iters"]) == 3
+    g.close()
+
+
+# ------------------------------------------------------------------ serving
+def test_submit_poll_matches_blocking(hg, ctx):
+    probs = [W.circles_2d(n=45, count=4, r_lo=3, r_hi=8, contrast=c, seed=int(c)) for c in (10.0, 100.0)]
+    probs.append(W.spheres_3d(n=15, count=3, r_lo=2, r_hi=4, seed=3, anisotropic=False, contrast=30.0))
+    blocking, grids = [], []
+    for ms in probs:
+        g = ctx.grid(ms.N)
+        g.set_coeffs_phase(ms.phase, ms.table)
+        blocking.append(g.solve(hg.default_opts(tol=1e-10)))
+        grids.append(g)
+    tickets = [ctx.submit(g, hg.default_opts(tol=1e-10)) for g in grids]
+    with pytest.raises(hg.HGError):
+        ctx.submit(grids[0], hg.default_opts())        # borrowed
+    out = [ctx.poll(t, timeout_us=-1) for t in tickets]
+    for a, b in zip(out, blocking):
+        assert a["status"] == 0
+        assert rel_max(a["AH"], b["AH"]) < 1e-12
+    for g in grids:
+        g.close()
