@@ -191,3 +191,177 @@ __device__ void fft_pencils(typename cplx_t<T>::type* buf, int npen, int pstride
 }
 
 }  // namespace hgk
+
+// ===========================================================================
+// Compile-time FFT: per-length plans, composite register codelets
+// ===========================================================================
+namespace hgk {
+
+// W_R^m = exp(-2 pi i m / R) for the composite codelet lengths.  Every
+// translation unit holds its own copy; configure_t() fills it per device from
+// extended-precision host values.
+static __constant__ double2 c_ctw64[CTW_TOTAL];
+static __constant__ float2 c_ctw32[CTW_TOTAL];
+
+template <int R> struct CtwOff;
+template <> struct CtwOff<9>  { static constexpr int v = CTW_9; };
+template <> struct CtwOff<15> { static constexpr int v = CTW_15; };
+template <> struct CtwOff<25> { static constexpr int v = CTW_25; };
+template <> struct CtwOff<27> { static constexpr int v = CTW_27; };
+
+template <int R, int M> __device__ __forceinline__ double2 ctw(double2) { return c_ctw64[CtwOff<R>::v + (M % R)]; }
+template <int R, int M> __device__ __forceinline__ float2 ctw(float2) { return c_ctw32[CtwOff<R>::v + (M % R)]; }
+
+// DFT of length R = R1 * R2 in registers (R1, R2 smaller codelets):
+//   n = n1 + R1 n2, k = k1 + R2 k2,  W_R^{nk} = W_R^{n1 k1} W_R1^{n1 k2} W_R2^{n2 k1}
+// -> R1 DFTs of length R2 over n2, twiddles W_R^{n1 k1}, R2 DFTs of length R1 over n1.
+template <int R1, int R2, bool INV, typename C> struct DftComposite;
+
+template <int R, bool INV, typename C> struct DftAny { };
+template <bool INV, typename C> struct DftAny<3, INV, C> { __device__ __forceinline__ static void run(C* v) { Dft<3, INV, C>::run(v); } };
+template <bool INV, typename C> struct DftAny<5, INV, C> { __device__ __forceinline__ static void run(C* v) { Dft<5, INV, C>::run(v); } };
+template <bool INV, typename C> struct DftAny<7, INV, C> { __device__ __forceinline__ static void run(C* v) { Dft<7, INV, C>::run(v); } };
+template <bool INV, typename C> struct DftAny<9, INV, C> { __device__ __forceinline__ static void run(C* v) { DftComposite<3, 3, INV, C>::run(v); } };
+template <bool INV, typename C> struct DftAny<15, INV, C> { __device__ __forceinline__ static void run(C* v) { DftComposite<3, 5, INV, C>::run(v); } };
+template <bool INV, typename C> struct DftAny<25, INV, C> { __device__ __forceinline__ static void run(C* v) { DftComposite<5, 5, INV, C>::run(v); } };
+template <bool INV, typename C> struct DftAny<27, INV, C> { __device__ __forceinline__ static void run(C* v) { DftComposite<3, 9, INV, C>::run(v); } };
+
+template <int R1, int R2, bool INV, typename C> struct DftComposite {
+    static constexpr int R = R1 * R2;
+    template <int N1, int K1>
+    __device__ __forceinline__ static void tw(C (&t)[R1][R2]) {
+        if constexpr (N1 > 0 && K1 > 0) t[N1][K1] = cmulw<INV>(t[N1][K1], ctw<R, N1 * K1>(C()));
+        if constexpr (K1 + 1 < R2) tw<N1, K1 + 1>(t);
+        else if constexpr (N1 + 1 < R1) tw<N1 + 1, 0>(t);
+    }
+    __device__ __forceinline__ static void run(C* v) {
+        C t[R1][R2];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) {
+            C col[R2];
+#pragma unroll
+            for (int n2 = 0; n2 < R2; ++n2) col[n2] = v[n1 + R1 * n2];
+            DftAny<R2, INV, C>::run(col);
+#pragma unroll
+            for (int k1 = 0; k1 < R2; ++k1) t[n1][k1] = col[k1];
+        }
+        tw<0, 0>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < R2; ++k1) {
+            C row[R1];
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) row[n1] = t[n1][k1];
+            DftAny<R1, INV, C>::run(row);
+#pragma unroll
+            for (int k2 = 0; k2 < R1; ++k2) v[k1 + R2 * k2] = row[k2];
+        }
+    }
+};
+
+// Compile-time radix plans per transform length and precision (double:
+// smaller codelets, the FP64 path is register- and ALU-bound).
+template <typename T, int N> struct CtPlan;
+template <int... Rs> struct RadixList {};
+#define HG_PLAN(TT, NN, ...) template <> struct CtPlan<TT, NN> { typedef RadixList<__VA_ARGS__> type; static constexpr bool ok = true; };
+HG_PLAN(float, 729, 27, 27)
+HG_PLAN(float, 375, 15, 25)
+HG_PLAN(float, 243, 27, 9)
+HG_PLAN(float, 135, 15, 9)
+HG_PLAN(float, 81, 9, 9)
+HG_PLAN(float, 75, 25, 3)
+HG_PLAN(float, 45, 9, 5)
+HG_PLAN(float, 27, 27)
+HG_PLAN(float, 15, 15)
+HG_PLAN(double, 729, 9, 9, 9)
+HG_PLAN(double, 375, 15, 5, 5)
+HG_PLAN(double, 243, 9, 9, 3)
+HG_PLAN(double, 135, 15, 9)
+HG_PLAN(double, 81, 9, 9)
+HG_PLAN(double, 75, 15, 5)
+HG_PLAN(double, 45, 9, 5)
+HG_PLAN(double, 27, 9, 3)
+HG_PLAN(double, 15, 15)
+#undef HG_PLAN
+
+// Threads per CTA of the compile-time kernels and the largest number of
+// pencils one CTA stages (bounded by 48 KB of data per CTA and 16 pencils).
+constexpr int CT_THREADS = 256;
+template <typename T, int N> struct CtCaps {
+    static constexpr int csize = (int)sizeof(typename cplx_t<T>::type);
+    static constexpr int by_smem = (48 * 1024) / (N * csize);
+    static constexpr int npmax = by_smem < 1 ? 1 : (by_smem > 16 ? 16 : by_smem);
+};
+
+// One in-place Stockham stage (see the formulation at the top of this file)
+// with every size known at compile time.
+template <typename T, int N, int R, int NS, bool INV, int NPMAX>
+__device__ __forceinline__ void stage_ct(typename cplx_t<T>::type* buf, int npen,
+                                         const typename cplx_t<T>::type* tw) {
+    typedef typename cplx_t<T>::type C;
+    constexpr int NB = N / R;
+    constexpr int TWS = N / (NS * R);
+    constexpr int B = (NPMAX * NB + CT_THREADS - 1) / CT_THREADS;
+    const int total = npen * NB;
+    C v[B][R];
+    int dst[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int idx = threadIdx.x + b * CT_THREADS;
+        dst[b] = -1;
+        if (idx < total) {
+            const int pen = idx / NB;
+            const int j = idx - pen * NB;
+            const int k = j % NS;
+            const C* src = buf + pen * N + j;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b][r] = src[r * NB];
+            if constexpr (NS > 1) {
+                const int step = k * TWS;
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[b][r] = cmulw<INV>(v[b][r], tw[r * step]);
+            }
+            DftAny<R, INV, C>::run(v[b]);
+            dst[b] = pen * N + (j - k) * R + k;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        if (dst[b] >= 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[dst[b] + r * NS] = v[b][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T, int N, bool INV, int NPMAX, int NS, int... Rs> struct CtStages;
+template <typename T, int N, bool INV, int NPMAX, int NS> struct CtStages<T, N, INV, NPMAX, NS> {
+    __device__ __forceinline__ static void run(typename cplx_t<T>::type*, int, const typename cplx_t<T>::type*) {}
+};
+template <typename T, int N, bool INV, int NPMAX, int NS, int R, int... Rs>
+struct CtStages<T, N, INV, NPMAX, NS, R, Rs...> {
+    __device__ __forceinline__ static void run(typename cplx_t<T>::type* buf, int npen,
+                                               const typename cplx_t<T>::type* tw) {
+        stage_ct<T, N, R, NS, INV, NPMAX>(buf, npen, tw);
+        CtStages<T, N, INV, NPMAX, NS * R, Rs...>::run(buf, npen, tw);
+    }
+};
+
+template <typename T, int N, bool INV, typename L> struct CtRun;
+template <typename T, int N, bool INV, int... Rs> struct CtRun<T, N, INV, RadixList<Rs...>> {
+    __device__ __forceinline__ static void run(typename cplx_t<T>::type* buf, int npen,
+                                               const typename cplx_t<T>::type* tw) {
+        CtStages<T, N, INV, CtCaps<T, N>::npmax, 1, Rs...>::run(buf, npen, tw);
+    }
+};
+
+// npen pencils of length N, contiguous (stride N) at buf; tw = N twiddles in
+// shared memory.
+template <typename T, int N, bool INV>
+__device__ __forceinline__ void fft_ct(typename cplx_t<T>::type* buf, int npen,
+                                       const typename cplx_t<T>::type* tw) {
+    CtRun<T, N, INV, typename CtPlan<T, N>::type>::run(buf, npen, tw);
+}
+
+}  // namespace hgk

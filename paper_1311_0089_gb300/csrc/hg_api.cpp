@@ -94,10 +94,33 @@ static int min_radix(const AxisPlanH& pl) {
 }
 
 // Row pass: choose loads-per-CTA LB and rows-per-CTA RB.
-static bool choose_row_cfg(int n, int d, int L, int minR, size_t csize, int max_smem, long long rows,
-                           RowCfg& cfg) {
+static bool choose_row_cfg(int prec, int n, int d, int L, int minR, size_t csize, int max_smem,
+                           long long rows, RowCfg& cfg) {
     const int maxb = 2, maxt = row_max_threads();
     const size_t target = 32 * 1024;
+    if (ct_length(d, n)) {
+        // compile-time kernel: 256 threads, at most ct_npmax pencils per CTA
+        const int npmax = ct_npmax(prec, n);
+        for (int LB = L; LB >= 1; --LB) {
+            int bestRB = 0;
+            for (int RB = 1; RB <= 64; ++RB) {
+                const int ncplx = (RB * LB * d + 1) / 2;
+                if (ncplx > npmax || RB > rows) break;
+                if (RB > 1 && rows / RB < 4 * 152) break;
+                bestRB = RB;
+            }
+            if (bestRB > 0) {
+                const int ncplx = (bestRB * LB * d + 1) / 2;
+                cfg.RB = bestRB; cfg.LB = LB; cfg.threads = CT_THREADS_HOST;
+                cfg.smem = (int)((size_t)(ncplx + 1) * n * csize);
+                cfg.nbx = (rows + bestRB - 1) / bestRB;
+                cfg.nby = (L + LB - 1) / LB;
+                cfg.ct = 1;
+                return true;
+            }
+        }
+        return false;
+    }
     for (int LB = L; LB >= 1; --LB) {
         int bestRB = 0;
         for (int RB = 1; RB <= 64; ++RB) {
@@ -122,15 +145,33 @@ static bool choose_row_cfg(int n, int d, int L, int minR, size_t csize, int max_
             cfg.smem = (int)((size_t)ncplx * n * csize);
             cfg.nbx = (rows + bestRB - 1) / bestRB;
             cfg.nby = (L + LB - 1) / LB;
+            cfg.ct = 0;
             return true;
         }
     }
     return false;
 }
 
-static bool choose_str_cfg(int n, int d, int minR, size_t csize, int max_smem, long long inner,
-                           int prefer_lanes, StrCfg& cfg) {
+static bool choose_str_cfg(int prec, int n, int d, int minR, size_t csize, int max_smem,
+                           long long inner, long long outer, int L, StrCfg& cfg) {
     const int maxb = 2, maxt = row_max_threads();
+    const int prefer_lanes = prec == 0 ? 2 : 4;
+    if (ct_length(d, n)) {
+        const int npmax = ct_npmax(prec, n);
+        int best = 0;
+        for (int Cl = 1; Cl <= 16; ++Cl) {
+            if (d * Cl > npmax || (Cl > 1 && Cl > inner)) break;
+            if (Cl > prefer_lanes && ((inner + Cl - 1) / Cl) * outer * L < 4 * 152) break;
+            if (Cl > 2 * prefer_lanes) break;
+            best = Cl;
+        }
+        if (!best) return false;
+        cfg.Cl = best;
+        cfg.threads = CT_THREADS_HOST;
+        cfg.smem = (int)((size_t)(d * best + 1) * n * csize);
+        cfg.ct = 1;
+        return true;
+    }
     int best = 0;
     for (int Cl = 1; Cl <= 32; ++Cl) {
         const long long bfly = (long long)d * Cl * n / std::max(minR, 1);
@@ -146,6 +187,7 @@ static bool choose_str_cfg(int n, int d, int minR, size_t csize, int max_smem, l
     cfg.Cl = best;
     cfg.threads = thr;
     cfg.smem = (int)((size_t)d * best * n * csize);
+    cfg.ct = 0;
     return true;
 }
 
@@ -187,12 +229,14 @@ int grid_init_plans(hg_grid* g) {
     for (int prec = 0; prec < 2; ++prec) {
         const size_t cs = prec == 0 ? 16 : 8;
         const int last = d - 1;
-        if (!choose_row_cfg(gd.Nl, d, d, min_radix(g->plan[last]), cs, max_smem, gd.rows, g->rowcfg[prec]))
+        if (!choose_row_cfg(prec, gd.Nl, d, d, min_radix(g->plan[last]), cs, max_smem, gd.rows, g->rowcfg[prec]))
             return HG_ERR_UNSUPPORTED_SIZE;
         for (int a = 0; a < last; ++a) {
-            long long inner = (a == 0) ? gd.Ms / gd.N[0] : gd.H;  // axis 0: all other axes; axis 1 (3D): last
-            const int prefer = prec == 0 ? 2 : 4;
-            if (!choose_str_cfg(gd.N[a], d, min_radix(g->plan[a]), cs, max_smem, inner, prefer, g->strcfg[prec][a]))
+            // axis 0: lanes run over all other axes; axis 1 (3D): over the last
+            const long long inner = (a == 0) ? gd.Ms / gd.N[0] : gd.H;
+            const long long outer = (a == 0) ? 1 : gd.N[0];
+            if (!choose_str_cfg(prec, gd.N[a], d, min_radix(g->plan[a]), cs, max_smem, inner, outer, d,
+                                g->strcfg[prec][a]))
                 return HG_ERR_UNSUPPORTED_SIZE;
         }
     }

@@ -8,6 +8,9 @@ namespace hgk {
 
 enum { MAXD = 3, MAXL = 3 };
 
+// Composite codelet twiddle table layout (W_R^m for R = 9, 15, 25, 27).
+enum { CTW_9 = 0, CTW_15 = 9, CTW_25 = 24, CTW_27 = 49, CTW_TOTAL = 76 };
+
 // Status of one CG system on the device.
 enum {
     ST_ACTIVE = 0,
@@ -62,9 +65,10 @@ struct CoeffsDev {
 };
 
 // Row (last-axis) pass launch geometry.
-struct RowCfg { int RB; int LB; int threads; int smem; long long nbx; int nby; };
+// ct = 1: the compile-time kernel for this length is used (256 threads).
+struct RowCfg { int RB; int LB; int threads; int smem; long long nbx; int nby; int ct; };
 // Strided-axis pass launch geometry.
-struct StrCfg { int Cl; int threads; int smem; };
+struct StrCfg { int Cl; int threads; int smem; int ct; };
 
 enum RowFwdMode { FWD_CG = 0, FWD_APPLY = 1 };
 enum RowInvMode { INV_CG = 0, INV_RHS = 1, INV_OUT = 2, INV_RESID = 3 };
@@ -142,7 +146,21 @@ cudaError_t launch_convert(const void* src, int src_prec, void* dst, int dst_pre
 cudaError_t launch_convert_spectrum(const void* src, int src_prec, double* dst, long long ncomplex,
                                     cudaStream_t s);
 int row_max_threads();
-int max_dyn_smem_configured(int prec);
 cudaError_t configure_kernels(int max_smem);
+// Lengths with compile-time kernels (per dimension) and the pencils one CTA
+// of such a kernel may stage (mirrors CtCaps in fft_device.cuh).
+bool ct_length(int d, int n);
+int ct_npmax(int prec, int n);
+enum { CT_THREADS_HOST = 256 };
+
+// per-precision launchers (hg_kernels_f32.cu, hg_kernels_f64.cu)
+cudaError_t launch_row_fwd_f32(const GridDev&, const AxisPlanH&, const void*, const RowCfg&, const RowFwdArgs&, cudaStream_t);
+cudaError_t launch_row_fwd_f64(const GridDev&, const AxisPlanH&, const void*, const RowCfg&, const RowFwdArgs&, cudaStream_t);
+cudaError_t launch_row_inv_f32(const GridDev&, const AxisPlanH&, const void*, const RowCfg&, const RowInvArgs&, cudaStream_t);
+cudaError_t launch_row_inv_f64(const GridDev&, const AxisPlanH&, const void*, const RowCfg&, const RowInvArgs&, cudaStream_t);
+cudaError_t launch_strided_f32(const GridDev&, const AxisPlanH&, const void*, const StrCfg&, const StrArgs&, cudaStream_t);
+cudaError_t launch_strided_f64(const GridDev&, const AxisPlanH&, const void*, const StrCfg&, const StrArgs&, cudaStream_t);
+cudaError_t configure_f32(int max_smem, const double* ctw);
+cudaError_t configure_f64(int max_smem, const double* ctw);
 
 }  // namespace hgk
