@@ -59,7 +59,9 @@ typedef enum {
     HG_ERR_CUDA = -8,               /* a CUDA runtime call failed                 */
     HG_ERR_CANCELLED = -9,          /* the ticket was cancelled                   */
     HG_ERR_BREAKDOWN = -10,         /* CG breakdown: (p, A p) <= 0 or not finite   */
-    HG_ERR_NO_COEFFS = -11          /* solve requested before hg_set_coeffs*       */
+    HG_ERR_NO_COEFFS = -11,         /* solve requested before hg_set_coeffs*       */
+    HG_ERR_TOO_LARGE = -12          /* grid exceeds the fixed scratch of
+                                       hg_apply_noalloc                            */
 } hg_status;
 
 typedef enum {
@@ -164,6 +166,29 @@ int hg_apply(hg_grid* grid, const double* u, double* out, int with_A,
  * values, interleaved (re, im) doubles; bin j of an axis holds frequency
  * j or j - N_a (Sec. 4.1); the last axis keeps j = 0..(N_d-1)/2. */
 int hg_spectrum(hg_grid* grid, const double* u, double* S_out, int prec, int on_device);
+
+/* out = G_N A_N u for one d x |N| field, like hg_apply(with_A = 1, A0 = NULL,
+ * HG_FP64) on a grid with Y = 1, but without allocating any device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they need the operator (plug-ins whose
+ * device memory belongs to their host application's allocator, real-time
+ * loops in which cudaMalloc/cudaFree and their synchronisation are not
+ * allowed).  It needs no hg_ctx or hg_grid.
+ *   d, N      : as hg_create_grid (N_a odd, factors 3/5/7, <= 1024).
+ *   phase     : device pointer, |N| uint8 phase indices (< n_phases).
+ *   table     : device pointer, n_phases x d x d doubles (SPD, not checked).
+ *   u, out    : device pointers, d x |N| doubles each (component-major).
+ *   cuda_stream: cudaStream_t to enqueue on (NULL = the legacy default stream).
+ * Scratch: a fixed 16 MiB static device array per GPU that loads the library,
+ * held until process exit; grids whose twiddles, reduction slots and half
+ * spectrum (d * |N|/N_d * (N_d+1)/2 complex doubles) do not fit return
+ * HG_ERR_TOO_LARGE before any work is enqueued.  The call only enqueues work
+ * (out is ready when the stream reaches it).  Every call shares the scratch:
+ * calls whose work overlaps on the GPU race; each call clears what must start
+ * at zero.  The first call on a device sets up that device (scratch address,
+ * kernel attributes, codelet constants): make it before any stream capture. */
+int hg_apply_noalloc(int d, const int* N, const uint8_t* phase, int n_phases,
+                     const double* table, const double* u, double* out, void* cuda_stream);
 
 /* Kernel launches made through this context so far (all entry points). */
 long long hg_launch_count(hg_ctx* ctx);

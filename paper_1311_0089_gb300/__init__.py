@@ -31,6 +31,7 @@ STATUS = {
     -3: "HG_ERR_NOT_SPD", -4: "HG_ERR_NO_MEMORY", -5: "HG_ERR_NOT_CONVERGED",
     -6: "HG_ERR_DEVICE_TIMEOUT", -7: "HG_ERR_BUSY", -8: "HG_ERR_CUDA",
     -9: "HG_ERR_CANCELLED", -10: "HG_ERR_BREAKDOWN", -11: "HG_ERR_NO_COEFFS",
+    -12: "HG_ERR_TOO_LARGE",
 }
 
 
@@ -89,6 +90,7 @@ SIGNATURES = [
     ("hg_cancel", _I, [_VP, ctypes.c_uint64]),
     ("hg_apply", _I, [_VP, _VP, _VP, _I, _VP, _I, _I]),
     ("hg_spectrum", _I, [_VP, _VP, _VP, _I, _I]),
+    ("hg_apply_noalloc", _I, [_I, ctypes.POINTER(_I), _VP, _I, _VP, _VP, _VP, _VP]),
     ("hg_launch_count", ctypes.c_longlong, [_VP]),
     ("hg_time_pass", _I, [_VP, _I, _I, _I, ctypes.POINTER(_D), ctypes.c_char_p]),
     ("hg_num_passes", _I, [_VP]),

@@ -73,7 +73,7 @@ void dev_free(hg_ctx* ctx, void* p) {
 }
 
 // Factor n into radices 3, 5, 7 (application order: 3s, then 5s, then 7s).
-static bool factor(int n, AxisPlanH& pl) {
+bool factor(int n, AxisPlanH& pl) {
     pl.n = n;
     pl.nstages = 0;
     int m = n;
@@ -87,15 +87,15 @@ static bool factor(int n, AxisPlanH& pl) {
     return m == 1;
 }
 
-static int min_radix(const AxisPlanH& pl) {
+int min_radix(const AxisPlanH& pl) {
     int r = 7;
     for (int s = 0; s < pl.nstages; ++s) r = std::min(r, pl.radix[s]);
     return pl.nstages ? r : 1;
 }
 
 // Row pass: choose loads-per-CTA LB and rows-per-CTA RB.
-static bool choose_row_cfg(int prec, int n, int d, int L, int minR, size_t csize, int max_smem,
-                           long long rows, RowCfg& cfg) {
+bool choose_row_cfg(int prec, int n, int d, int L, int minR, size_t csize, int max_smem,
+                    long long rows, RowCfg& cfg) {
     const int maxb = 2, maxt = row_max_threads();
     const size_t target = 32 * 1024;
     if (ct_length(d, n)) {
@@ -152,8 +152,8 @@ static bool choose_row_cfg(int prec, int n, int d, int L, int minR, size_t csize
     return false;
 }
 
-static bool choose_str_cfg(int prec, int n, int d, int minR, size_t csize, int max_smem,
-                           long long inner, long long outer, int L, StrCfg& cfg) {
+bool choose_str_cfg(int prec, int n, int d, int minR, size_t csize, int max_smem,
+                    long long inner, long long outer, int L, StrCfg& cfg) {
     const int maxb = 2, maxt = row_max_threads();
     const int prefer_lanes = prec == 0 ? 2 : 4;
     if (ct_length(d, n)) {

@@ -106,6 +106,7 @@ const char* hg_strerror(int s) {
         case HG_ERR_CANCELLED: return "cancelled";
         case HG_ERR_BREAKDOWN: return "CG breakdown ((p, A p) <= 0 or not finite)";
         case HG_ERR_NO_COEFFS: return "coefficients not set";
+        case HG_ERR_TOO_LARGE: return "grid too large for the fixed 16 MiB scratch of hg_apply_noalloc";
         default: return "unknown status";
     }
 }

@@ -88,6 +88,13 @@ const char* last_cuda_error();
 int dev_alloc(hg_ctx* ctx, void** p, size_t bytes);
 void dev_free(hg_ctx* ctx, void* p);
 int grid_init_plans(hg_grid* g);
+// FFT plan and launch geometry helpers (hg_api.cpp)
+bool factor(int n, hgk::AxisPlanH& pl);
+int min_radix(const hgk::AxisPlanH& pl);
+bool choose_row_cfg(int prec, int n, int d, int L, int minR, size_t csize, int max_smem,
+                    long long rows, hgk::RowCfg& cfg);
+bool choose_str_cfg(int prec, int n, int d, int minR, size_t csize, int max_smem,
+                    long long inner, long long outer, int L, hgk::StrCfg& cfg);
 int grid_alloc_work(hg_grid* g, int prec);
 int grid_alloc_common(hg_grid* g);
 hgk::CoeffsDev coeffs_for(const hg_grid* g, int prec, bool withA);
