@@ -293,13 +293,14 @@ template <typename T, int N> struct CtCaps {
 };
 
 // One in-place Stockham stage (see the formulation at the top of this file)
-// with every size known at compile time.
+// with every size known at compile time.  `tw` is this stage's twiddle table
+// in shared memory, laid out [r-1][k] (k = j mod NS): consecutive threads read
+// consecutive entries.
 template <typename T, int N, int R, int NS, bool INV, int NPMAX>
 __device__ __forceinline__ void stage_ct(typename cplx_t<T>::type* buf, int npen,
                                          const typename cplx_t<T>::type* tw) {
     typedef typename cplx_t<T>::type C;
     constexpr int NB = N / R;
-    constexpr int TWS = N / (NS * R);
     constexpr int B = (NPMAX * NB + CT_THREADS - 1) / CT_THREADS;
     const int total = npen * NB;
     C v[B][R];
@@ -316,9 +317,8 @@ __device__ __forceinline__ void stage_ct(typename cplx_t<T>::type* buf, int npen
 #pragma unroll
             for (int r = 0; r < R; ++r) v[b][r] = src[r * NB];
             if constexpr (NS > 1) {
-                const int step = k * TWS;
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[b][r] = cmulw<INV>(v[b][r], tw[r * step]);
+                for (int r = 1; r < R; ++r) v[b][r] = cmulw<INV>(v[b][r], tw[(r - 1) * NS + k]);
             }
             DftAny<R, INV, C>::run(v[b]);
             dst[b] = pen * N + (j - k) * R + k;
@@ -335,33 +335,60 @@ __device__ __forceinline__ void stage_ct(typename cplx_t<T>::type* buf, int npen
     __syncthreads();
 }
 
-template <typename T, int N, bool INV, int NPMAX, int NS, int... Rs> struct CtStages;
-template <typename T, int N, bool INV, int NPMAX, int NS> struct CtStages<T, N, INV, NPMAX, NS> {
+// Per-stage twiddle tables: stage s (NS > 1) holds W_N^{r k N/(NS R)} at
+// [(r-1) NS + k], r = 1..R-1, k < NS; OFF is the running offset.
+template <typename T, int N, bool INV, int NPMAX, int NS, int OFF, int... Rs> struct CtStages;
+template <typename T, int N, bool INV, int NPMAX, int NS, int OFF> struct CtStages<T, N, INV, NPMAX, NS, OFF> {
+    static constexpr int tw_size = OFF;
     __device__ __forceinline__ static void run(typename cplx_t<T>::type*, int, const typename cplx_t<T>::type*) {}
+    __device__ __forceinline__ static void build(typename cplx_t<T>::type*, const typename cplx_t<T>::type*) {}
 };
-template <typename T, int N, bool INV, int NPMAX, int NS, int R, int... Rs>
-struct CtStages<T, N, INV, NPMAX, NS, R, Rs...> {
+template <typename T, int N, bool INV, int NPMAX, int NS, int OFF, int R, int... Rs>
+struct CtStages<T, N, INV, NPMAX, NS, OFF, R, Rs...> {
+    static constexpr int here = NS > 1 ? (R - 1) * NS : 0;
+    typedef CtStages<T, N, INV, NPMAX, NS * R, OFF + here, Rs...> Next;
+    static constexpr int tw_size = Next::tw_size;
     __device__ __forceinline__ static void run(typename cplx_t<T>::type* buf, int npen,
-                                               const typename cplx_t<T>::type* tw) {
-        stage_ct<T, N, R, NS, INV, NPMAX>(buf, npen, tw);
-        CtStages<T, N, INV, NPMAX, NS * R, Rs...>::run(buf, npen, tw);
+                                               const typename cplx_t<T>::type* twst) {
+        stage_ct<T, N, R, NS, INV, NPMAX>(buf, npen, twst + OFF);
+        Next::run(buf, npen, twst);
+    }
+    // twst[OFF + (r-1) NS + k] = tw_nat[r k N/(NS R)]
+    __device__ __forceinline__ static void build(typename cplx_t<T>::type* twst,
+                                                 const typename cplx_t<T>::type* __restrict__ tw_nat) {
+        if constexpr (NS > 1) {
+            constexpr int TWS = N / (NS * R);
+            for (int idx = threadIdx.x; idx < here; idx += blockDim.x) {
+                const int r = idx / NS + 1;
+                const int k = idx - (r - 1) * NS;
+                twst[OFF + idx] = tw_nat[r * k * TWS];
+            }
+        }
+        Next::build(twst, tw_nat);
     }
 };
 
 template <typename T, int N, bool INV, typename L> struct CtRun;
 template <typename T, int N, bool INV, int... Rs> struct CtRun<T, N, INV, RadixList<Rs...>> {
+    typedef CtStages<T, N, INV, CtCaps<T, N>::npmax, 1, 0, Rs...> S;
     __device__ __forceinline__ static void run(typename cplx_t<T>::type* buf, int npen,
-                                               const typename cplx_t<T>::type* tw) {
-        CtStages<T, N, INV, CtCaps<T, N>::npmax, 1, Rs...>::run(buf, npen, tw);
+                                               const typename cplx_t<T>::type* twst) {
+        S::run(buf, npen, twst);
     }
 };
 
-// npen pencils of length N, contiguous (stride N) at buf; tw = N twiddles in
-// shared memory.
+// npen pencils of length N, contiguous (stride N) at buf; twst = the
+// per-stage twiddle tables built by fft_ct_twiddles.
 template <typename T, int N, bool INV>
 __device__ __forceinline__ void fft_ct(typename cplx_t<T>::type* buf, int npen,
-                                       const typename cplx_t<T>::type* tw) {
-    CtRun<T, N, INV, typename CtPlan<T, N>::type>::run(buf, npen, tw);
+                                       const typename cplx_t<T>::type* twst) {
+    CtRun<T, N, INV, typename CtPlan<T, N>::type>::run(buf, npen, twst);
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void fft_ct_twiddles(typename cplx_t<T>::type* twst,
+                                                const typename cplx_t<T>::type* __restrict__ tw_nat) {
+    CtRun<T, N, false, typename CtPlan<T, N>::type>::S::build(twst, tw_nat);
 }
 
 }  // namespace hgk

@@ -106,7 +106,7 @@ bool choose_row_cfg(int prec, int n, int d, int L, int minR, size_t csize, int m
             for (int RB = 1; RB <= 64; ++RB) {
                 const int ncplx = (RB * LB * d + 1) / 2;
                 if (ncplx > npmax || RB > rows) break;
-                if (RB > 1 && rows / RB < 4 * 152) break;
+                if (RB > 1 && rows / RB < 2 * 152) break;
                 bestRB = RB;
             }
             if (bestRB > 0) {
@@ -159,7 +159,7 @@ bool choose_str_cfg(int prec, int n, int d, int minR, size_t csize, int max_smem
     if (ct_length(d, n)) {
         const int npmax = ct_npmax(prec, n);
         int best = 0;
-        for (int Cl = 1; Cl <= 16; ++Cl) {
+        for (int Cl = 1; Cl <= 16; Cl *= 2) {   // powers of two (lane = tid & (Cl-1))
             if (d * Cl > npmax || (Cl > 1 && Cl > inner)) break;
             if (Cl > prefer_lanes && ((inner + Cl - 1) / Cl) * outer * L < 4 * 152) break;
             if (Cl > 2 * prefer_lanes) break;
@@ -173,7 +173,7 @@ bool choose_str_cfg(int prec, int n, int d, int minR, size_t csize, int max_smem
         return true;
     }
     int best = 0;
-    for (int Cl = 1; Cl <= 32; ++Cl) {
+    for (int Cl = 1; Cl <= 32; Cl *= 2) {   // powers of two (lane = tid & (Cl-1))
         const long long bfly = (long long)d * Cl * n / std::max(minR, 1);
         const size_t smem = (size_t)d * Cl * n * csize;
         if (bfly > (long long)maxb * maxt || smem > (size_t)max_smem) break;
@@ -309,6 +309,7 @@ CoeffsDev coeffs_for(const hg_grid* g, int prec, bool withA) {
     c.table = g->d_table[prec];
     c.field = g->d_field[prec];
     c.mode = !withA ? 2 : (g->coeff_mode == 0 ? 0 : 1);
+    c.n_phases = g->n_phases;
     return c;
 }
 

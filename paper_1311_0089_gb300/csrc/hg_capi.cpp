@@ -183,13 +183,19 @@ int hg_create_grid(hg_ctx* c, int d, const int* N, const double* Y, hg_grid** ou
     GridDev& gd = g->gd;
     gd.d = d;
     gd.M = 1;
-    for (int a = 0; a < 3; ++a) { gd.N[a] = a < d ? N[a] : 1; gd.Y[a] = (a < d && Y) ? Y[a] : 1.0; }
+    for (int a = 0; a < 3; ++a) {
+        gd.N[a] = a < d ? N[a] : 1;
+        gd.Y[a] = (a < d && Y) ? Y[a] : 1.0;
+        gd.invY[a] = 1.0 / gd.Y[a];
+        gd.invYf[a] = (float)gd.invY[a];
+    }
     for (int a = 0; a < d; ++a) gd.M *= N[a];
     gd.Nl = N[d - 1];
     gd.H = (gd.Nl + 1) / 2;
     gd.rows = gd.M / gd.Nl;
     gd.Ms = gd.rows * gd.H;
     gd.invM = 1.0 / (double)gd.M;
+    gd.invMf = (float)gd.invM;
     int st = grid_init_plans(g);
     if (st == HG_OK) {
         cudaError_t e = cudaMallocHost((void**)&g->h_sc, sizeof(Scalars) * MAXL);
@@ -455,6 +461,7 @@ int hg_time_pass(hg_grid* g, int prec, int pass, int reps, double* ms_out, char*
     memset(hs, 0, sizeof(hs));
     for (int l = 0; l < MAXL; ++l) {
         hs[l].rr = 1.0; hs[l].alpha = 0.5; hs[l].beta = 0.5; hs[l].bnorm = 1.0; hs[l].tol = 0.0;
+        hs[l].alpha_f = 0.5f; hs[l].beta_f = 0.5f;
         hs[l].max_iter = 1 << 30; hs[l].status = ST_ACTIVE;
     }
     HG_CU(cudaMemcpyAsync(w.sc, hs, sizeof(hs), cudaMemcpyHostToDevice, s));

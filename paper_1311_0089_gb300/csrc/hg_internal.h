@@ -36,6 +36,8 @@ struct Scalars {
     int status;
     int max_iter;
     int total_iters; // accumulated over refinement steps
+    float alpha_f;   // alpha and beta rounded to FP32 for the FP32 kernels
+    float beta_f;
 };
 
 struct GridDev {
@@ -47,7 +49,10 @@ struct GridDev {
     long long rows;        // M / Nl
     long long Ms;          // rows * H (complex half-spectrum entries per component)
     double Y[3];           // cell half sizes
+    double invY[3];        // 1 / Y
     double invM;
+    float invYf[3];        // FP32 copies for the FP32 kernels
+    float invMf;
 };
 
 struct AxisPlanH {
@@ -59,6 +64,7 @@ struct AxisPlanH {
 
 struct CoeffsDev {
     int mode;                  // 0 phase map, 1 packed field, 2 identity
+    int n_phases;              // mode 0: table entries (<= 16 are staged in shared memory)
     const uint8_t* phase;
     const void* table;         // n_phases x d x d (T)
     const void* field;         // npk x M (T), order 11,22[,33],12[,13,23]

@@ -13,6 +13,7 @@ __global__ void k_init_scalars(Scalars* sc, int L, int s0, int s1, int s2, doubl
     if (l >= L) return;
     Scalars s;
     s.rr = 0; s.pt = 0; s.alpha = 0; s.beta = 0; s.bnorm = 0; s.aen = 0; s.relres = 1.0;
+    s.alpha_f = 0.f; s.beta_f = 0.f;
     s.tol = tol; s.iters = 0; s.max_iter = max_iter; s.total_iters = 0;
     s.status = (l == 0) ? s0 : (l == 1) ? s1 : s2;
     sc[l] = s;
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(256) k_inner_init(GridDev g, int L, const doub
     if (threadIdx.x == 0) {
         for (int l = 0; l < L; ++l) {
             Scalars s;
-            s.rr = tot[l] * g.invM; s.pt = 0; s.alpha = 0; s.beta = 0;
+            s.rr = tot[l] * g.invM; s.pt = 0; s.alpha = 0; s.beta = 0; s.alpha_f = 0.f; s.beta_f = 0.f;
             s.bnorm = sqrt(s.rr); s.aen = 0; s.relres = 1.0; s.tol = inner_tol;
             s.iters = 0; s.max_iter = inner_max; s.total_iters = 0;
             s.status = act[l] ? (s.rr > 0.0 ? ST_ACTIVE : ST_CONVERGED) : ST_IDLE;
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(256) k_energy(GridDev g, int L, CoeffsDev co, 
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < M;
          k += (long long)gridDim.x * blockDim.x) {
         double am[D][D];
-        load_coeffs<double, D>(co, k, M, am);
+        load_coeffs<double, D>(co, k, M, am, static_cast<const double*>(co.table));
         double e[D][D], f[D][D];   // e[j] = E_j + x_j ; f[j] = A e[j]
 #pragma unroll
         for (int j = 0; j < D; ++j) {

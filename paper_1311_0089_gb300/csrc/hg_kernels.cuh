@@ -65,6 +65,33 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     __syncthreads();
 }
 
+// Block sum of per-thread partials held in T: warp sums in T (32 terms), FP64
+// across the warps of the block (and, through publish/final_sums, across the
+// grid).  Result valid in thread 0.
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum_t(const T (&v)[NV], double (&out)[NV]) {
+    __shared__ double red[NV][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        T x = v[i];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+        if (lane == 0) red[i][wid] = (double)x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double sum = 0.0;
+            for (int w = 0; w < nw; ++w) sum += red[i][w];
+            out[i] = sum;
+        }
+    }
+    __syncthreads();
+}
+
 // Writes `cnt` partials (slot s of this CTA at partial[s * stride + bid]) and
 // returns true in the last CTA to finish (of `nblocks`).
 __device__ __forceinline__ bool publish(const double* vals, const int* slots, int cnt,
@@ -109,8 +136,31 @@ __device__ __forceinline__ void final_sums(const double* partial, long long stri
 // ---------------------------------------------------------------------------
 // coefficients A(x_k) (Sec. 5.1: A_N = diag_k A(x_k))
 // ---------------------------------------------------------------------------
+// A phase table of at most 16 entries is staged in shared memory (the
+// lookup then follows the phase byte load with a shared-memory read).
+constexpr int SMEM_PHASES = 16;
+
 template <typename T, int D>
-__device__ __forceinline__ void load_coeffs(const CoeffsDev& co, long long k, long long M, T (&a)[D][D]) {
+__device__ __forceinline__ const T* stage_table(const CoeffsDev& co, T* s_tab) {
+    if (co.mode == 0 && co.n_phases <= SMEM_PHASES) {
+        const T* tb = static_cast<const T*>(co.table);
+        for (int i = threadIdx.x; i < co.n_phases * D * D; i += blockDim.x) s_tab[i] = tb[i];
+        return s_tab;
+    }
+    return static_cast<const T*>(co.table);
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void load_coeffs(const CoeffsDev& co, long long k, long long M, T (&a)[D][D],
+                                            const T* tab) {
+    if (co.mode == 0) {
+        const T* tb = tab + (int)co.phase[k] * D * D;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) a[i][j] = tb[i * D + j];
+        return;
+    }
     if (co.mode == 0) {
         const T* tb = static_cast<const T*>(co.table) + (int)co.phase[k] * D * D;
 #pragma unroll
@@ -137,6 +187,17 @@ __device__ __forceinline__ void load_coeffs(const CoeffsDev& co, long long k, lo
 
 __device__ __forceinline__ int freq_of(int j, int n) { return (2 * j <= n - 1) ? j : j - n; }
 
+// 1/x: FP32 correctly rounded reciprocal; FP64 by two Newton-Raphson steps
+// y <- y (2 - x y) from the FP32 reciprocal (quadratic convergence: 2^-24 ->
+// 2^-48 -> below FP64 rounding), avoiding a full FP64 division.
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) {
+    double y = (double)__frcp_rn((float)x);
+    y = y * fma(-x, y, 2.0);
+    y = y * fma(-x, y, 2.0);
+    return y;
+}
+
 // Transform of `npen` staged pencils of length n (forward or inverse).
 template <typename T, int NN, bool INV>
 __device__ __forceinline__ void fft_any(Cx<T>* buf, int npen, int n, const AxisPlanH& pl,
@@ -145,14 +206,14 @@ __device__ __forceinline__ void fft_any(Cx<T>* buf, int npen, int n, const AxisP
     else fft_pencils<T, INV, MAXB>(buf, npen, n, pl, twg);
 }
 
-// Twiddles of the compile-time kernels are staged in shared memory after the
-// pencils (n entries); the runtime kernels read them from global memory.
+// The compile-time kernels stage their per-stage twiddle tables in shared
+// memory after the pencils (fewer than n entries); the runtime kernels read
+// the natural table from global memory.
 template <typename T, int NN>
 __device__ __forceinline__ Cx<T>* stage_twiddles(Cx<T>* smem_after, const AxisPlanH& pl,
                                                  const Cx<T>* __restrict__ twg) {
     if constexpr (NN > 0) {
-        const Cx<T>* src = twg + pl.tw_off;
-        for (int i = threadIdx.x; i < NN; i += blockDim.x) smem_after[i] = src[i];
+        fft_ct_twiddles<T, NN>(smem_after, twg + pl.tw_off);
         return smem_after;
     } else {
         return nullptr;
@@ -160,6 +221,37 @@ __device__ __forceinline__ Cx<T>* stage_twiddles(Cx<T>* smem_after, const AxisPl
 }
 
 template <int NN> struct PassThreads { static constexpr int v = NN > 0 ? CT_THREADS : MAXT; };
+
+// CG scalars in the kernel's precision (FP32 copies are written beside the
+// FP64 values by the reducing CTA).
+__device__ __forceinline__ float beta_of(const Scalars& s, float) { return s.beta_f; }
+__device__ __forceinline__ double beta_of(const Scalars& s, double) { return s.beta; }
+__device__ __forceinline__ float alpha_of(const Scalars& s, float) { return s.alpha_f; }
+__device__ __forceinline__ double alpha_of(const Scalars& s, double) { return s.alpha; }
+__device__ __forceinline__ float inv_y(const GridDev& g, int a, float) { return g.invYf[a]; }
+__device__ __forceinline__ double inv_y(const GridDev& g, int a, double) { return g.invY[a]; }
+__device__ __forceinline__ float inv_m(const GridDev& g, float) { return g.invMf; }
+__device__ __forceinline__ double inv_m(const GridDev& g, double) { return g.invM; }
+// f / den for the projection: FP32 fast division (2 ulp), FP64 Newton reciprocal
+__device__ __forceinline__ float div_proj(float f, float den) { return __fdividef(f, den); }
+__device__ __forceinline__ double div_proj(double f, double den) { return f * recip(den); }
+
+// Largest number of real rows a row-pass CTA stages (RB * LB * D).
+constexpr int MAX_REAL_ROWS = 64;
+
+// Offset of the half-spectrum row of real row rr (-1: none) for a row tile:
+// real row rr = (rowi * nl + li) * D + al holds component al of load l0 + li
+// on spatial row row0 + rowi.
+template <int D>
+__device__ __forceinline__ void row_offsets(long long* s_off, int nreal, int nl, int l0, long long row0,
+                                            int nrow, const int* s_act, long long rows, int H) {
+    for (int rr = threadIdx.x; rr < nreal; rr += blockDim.x) {
+        const int rowi = rr / (nl * D);
+        const int li = (rr / D) % nl;
+        const int al = rr % D;
+        s_off[rr] = (rowi < nrow && s_act[li]) ? ((((long long)(l0 + li) * D + al) * rows + row0 + rowi) * H) : -1;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // last-axis forward pass (prologue + real-to-complex DFT)
@@ -175,89 +267,129 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
     const int H = (Nl + 1) >> 1;
     const long long M = g.M, rows = g.rows;
     const long long row0 = (long long)blockIdx.x * RB;
+    const int nrow = (int)min((long long)RB, rows - row0);
     const int l0 = blockIdx.y * LB;
     const int nl = min(LB, a.L - l0);
     const int nreal = RB * nl * D;
     const int ncplx = (nreal + 1) >> 1;
     const C* tws = stage_twiddles<T, NN>(buf + ncplx * Nl, pl, tw);
 
-    __shared__ double s_beta[MAXL];
-    __shared__ int s_act[MAXL];
+    __shared__ T s_beta[D];
+    __shared__ int s_act[D];
+    __shared__ T s_tab[SMEM_PHASES * D * D];
+    __shared__ long long s_off[MAX_REAL_ROWS];
     if (threadIdx.x < nl) {
         const Scalars& s = a.sc[l0 + threadIdx.x];
         s_act[threadIdx.x] = (!a.check_status) || (s.status == ST_ACTIVE);
-        s_beta[threadIdx.x] = s.beta;
+        s_beta[threadIdx.x] = beta_of(s, T());
     }
+    const T* tab = stage_table<T, D>(a.co, s_tab);
     __syncthreads();
-
-    T* __restrict__ P = static_cast<T*>(a.p);
-    const T* __restrict__ R = static_cast<const T*>(a.r);
-    const T* __restrict__ U = static_cast<const T*>(a.u);
-    double acc[MAXL] = {0.0, 0.0, 0.0};
-
-    for (int e = threadIdx.x; e < RB * Nl; e += blockDim.x) {
-        const int rowi = e / Nl;
-        const int i = e - rowi * Nl;
-        const long long grow = row0 + rowi;
-        const bool valid = grow < rows;
-        const long long k = grow * Nl + i;
-        T am[D][D];
-        if (valid) load_coeffs<T, D>(a.co, k, M, am);
+    row_offsets<D>(s_off, nreal, nl, l0, row0, nrow, s_act, rows, H);
+    T beta_t[D];
+    bool act[D];
 #pragma unroll
-        for (int li = 0; li < MAXL; ++li) {
-            if (li >= nl) break;
-            const int l = l0 + li;
-            T t[D];
+    for (int li = 0; li < D; ++li) {
+        act[li] = li < nl && s_act[li];
+        beta_t[li] = li < nl ? s_beta[li] : T(0);
+    }
+
+    // tile base pointers: the RB rows of a tile are contiguous in memory
+    const long long kb = row0 * Nl;
+    const bool cg = a.mode == FWD_CG;
+    T* Pb[D][D];
+    const T* Rb[D][D];
+    T Ev[D][D];
 #pragma unroll
-            for (int al = 0; al < D; ++al) t[al] = T(0);
-            if (valid && s_act[li]) {
-                T v[D];
-                if (a.mode == FWD_CG) {
-                    const T beta = (T)s_beta[li];
+    for (int li = 0; li < D; ++li)
+#pragma unroll
+        for (int al = 0; al < D; ++al) {
+            const long long off = ((long long)(l0 + li) * D + al) * M + kb;
+            Pb[li][al] = cg ? static_cast<T*>(a.p) + off : nullptr;
+            Rb[li][al] = cg ? static_cast<const T*>(a.r) + off : (a.u ? static_cast<const T*>(a.u) + off : nullptr);
+            Ev[li][al] = (!cg && a.E && li < nl) ? (T)a.E[(l0 + li) * D + al] : T(0);
+        }
+    const uint8_t* phb = a.co.phase ? a.co.phase + kb : nullptr;
+    CoeffsDev co = a.co;     // phase map / packed field shifted to the tile
+    co.phase = phb;
+    if (co.mode == 1) co.field = static_cast<const T*>(a.co.field) + kb;
+
+    // per-thread partial sums in T over this thread's voxels, FP64 above the warp
+    T tacc[MAXL] = {T(0), T(0), T(0)};
+    const int total = nrow * Nl;
+    constexpr int UNR = 2;
+    for (int e0 = threadIdx.x; e0 < RB * Nl; e0 += UNR * blockDim.x) {
+        T vv[UNR][D][D];
+        T pp[UNR][D][D];
+        T am[UNR][D][D];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const bool valid = e < total;
+            if (valid) load_coeffs<T, D>(co, e, M, am[u], tab);
+#pragma unroll
+            for (int li = 0; li < D; ++li) {
+                if (li >= nl) break;
+                const bool on = valid && act[li];
+#pragma unroll
+                for (int al = 0; al < D; ++al) {
+                    vv[u][li][al] = (on && Rb[li][al]) ? Rb[li][al][e] : T(0);
+                    pp[u][li][al] = (on && cg) ? Pb[li][al][e] : T(0);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e >= RB * Nl) break;
+            const bool valid = e < total;
+            const int rowi = e / Nl;
+            const int i = e - rowi * Nl;
+#pragma unroll
+            for (int li = 0; li < D; ++li) {
+                if (li >= nl) break;
+                T t[D];
+#pragma unroll
+                for (int al = 0; al < D; ++al) t[al] = T(0);
+                if (valid && act[li]) {
+                    T v[D];
 #pragma unroll
                     for (int al = 0; al < D; ++al) {
-                        const long long idx = ((long long)l * D + al) * M + k;
-                        const T pv = R[idx] + beta * P[idx];
-                        P[idx] = pv;
-                        v[al] = pv;
+                        if (cg) {
+                            v[al] = vv[u][li][al] + beta_t[li] * pp[u][li][al];
+                            Pb[li][al][e] = v[al];
+                        } else {
+                            v[al] = vv[u][li][al] + Ev[li][al];
+                        }
                     }
-                } else {
 #pragma unroll
                     for (int al = 0; al < D; ++al) {
-                        const long long idx = ((long long)l * D + al) * M + k;
-                        v[al] = (U ? U[idx] : T(0)) + (a.E ? (T)a.E[l * D + al] : T(0));
+                        T sacc = T(0);
+#pragma unroll
+                        for (int be = 0; be < D; ++be) sacc += am[u][al][be] * v[be];
+                        t[al] = sacc;
                     }
+                    if (!cg && a.A0) {
+                        T w[D];
+#pragma unroll
+                        for (int al = 0; al < D; ++al) {
+                            T sacc = T(0);
+#pragma unroll
+                            for (int be = 0; be < D; ++be) sacc += (T)a.A0[al * D + be] * t[be];
+                            w[al] = sacc;
+                        }
+#pragma unroll
+                        for (int al = 0; al < D; ++al) t[al] = w[al];
+                    }
+#pragma unroll
+                    for (int al = 0; al < D; ++al) tacc[li] += cg ? v[al] * t[al] : t[al] * t[al];
                 }
 #pragma unroll
                 for (int al = 0; al < D; ++al) {
-                    T s = T(0);
-#pragma unroll
-                    for (int be = 0; be < D; ++be) s += am[al][be] * v[be];
-                    t[al] = s;
+                    const int rr = (rowi * nl + li) * D + al;
+                    C* z = &buf[(rr >> 1) * Nl + i];
+                    if (rr & 1) z->y = t[al]; else z->x = t[al];
                 }
-                if (a.mode == FWD_APPLY && a.A0) {
-                    T w[D];
-#pragma unroll
-                    for (int al = 0; al < D; ++al) {
-                        T s = T(0);
-#pragma unroll
-                        for (int be = 0; be < D; ++be) s += (T)a.A0[al * D + be] * t[be];
-                        w[al] = s;
-                    }
-#pragma unroll
-                    for (int al = 0; al < D; ++al) t[al] = w[al];
-                }
-                double dsum = 0.0;
-#pragma unroll
-                for (int al = 0; al < D; ++al)
-                    dsum += (a.mode == FWD_CG) ? (double)v[al] * (double)t[al] : (double)t[al] * (double)t[al];
-                acc[li] += dsum;
-            }
-#pragma unroll
-            for (int al = 0; al < D; ++al) {
-                const int rr = (rowi * nl + li) * D + al;
-                C* z = &buf[(rr >> 1) * Nl + i];
-                if (rr & 1) z->y = t[al]; else z->x = t[al];
             }
         }
     }
@@ -275,24 +407,23 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
         const int kk = e - c * H;
         const C z = buf[c * Nl + kk];
         const C zm = buf[c * Nl + (kk ? Nl - kk : 0)];
-        C A, B;
-        A.x = T(0.5) * (z.x + zm.x); A.y = T(0.5) * (z.y - zm.y);
-        B.x = T(0.5) * (z.y + zm.y); B.y = T(0.5) * (zm.x - z.x);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int rr = 2 * c + h;
-            if (rr >= nreal) break;
-            const int rowi = rr / (nl * D);
-            const int li = (rr / D) % nl;
-            const int al = rr % D;
-            const long long grow = row0 + rowi;
-            if (grow < rows && s_act[li])
-                S[(((long long)(l0 + li) * D + al) * rows + grow) * H + kk] = h ? B : A;
+        const long long o0 = s_off[2 * c];
+        const long long o1 = (2 * c + 1 < nreal) ? s_off[2 * c + 1] : -1;
+        if (o0 >= 0) {
+            C A;
+            A.x = T(0.5) * (z.x + zm.x); A.y = T(0.5) * (z.y - zm.y);
+            S[o0 + kk] = A;
+        }
+        if (o1 >= 0) {
+            C B;
+            B.x = T(0.5) * (z.y + zm.y); B.y = T(0.5) * (zm.x - z.x);
+            S[o1 + kk] = B;
         }
     }
 
     // reductions
-    block_sum<MAXL>(acc);
+    double acc[MAXL];
+    block_sum_t<T, MAXL>(tacc, acc);
     const long long nbx = gridDim.x;
     const unsigned nblocks = gridDim.x * gridDim.y;
     int slots[MAXL];
@@ -314,6 +445,7 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
                 } else {
                     s.alpha = s.rr / val;
                 }
+                s.alpha_f = (float)s.alpha;
             } else {
                 s.aen = sqrt(val);
             }
@@ -337,19 +469,22 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_strided(GridDev g, AxisP
     const int l = blockIdx.z;
     if (a.check_status && a.sc[l].status != ST_ACTIVE) return;
     const int n = NN > 0 ? NN : a.n;
-    const long long inner = a.inner;
-    C* __restrict__ S = static_cast<C*>(a.S);
-    const long long cstride = g.Ms;
-    const long long base = (long long)l * D * cstride + o * n * inner + i0;
+    const int inner = (int)a.inner;
     const C* tws = stage_twiddles<T, NN>(buf + D * Cl * n, pl, tw);
 
-    for (int e = threadIdx.x; e < D * Cl * n; e += blockDim.x) {
-        const int lane = e % Cl;
-        const int rest = e / Cl;
-        const int m = rest % n;
-        const int al = rest / n;
+    // Cl is a power of two dividing blockDim.x: each thread keeps one lane and
+    // walks the (component, position) rows with stride blockDim.x / Cl.
+    const int lane = threadIdx.x & (Cl - 1);
+    const int rstep = blockDim.x / Cl;
+    const bool lane_ok = i0 + lane < inner;
+    C* Sb = static_cast<C*>(a.S) + (long long)l * D * g.Ms + o * (long long)n * inner + i0 + lane;
+    const long long cstride = g.Ms;
+#pragma unroll 4
+    for (int row = threadIdx.x / Cl; row < D * n; row += rstep) {
+        const int al = row / n;
+        const int m = row - al * n;
         C v = czero<T>();
-        if (i0 + lane < inner) v = S[base + al * cstride + (long long)m * inner + lane];
+        if (lane_ok) v = Sb[al * cstride + m * inner];
         buf[(al * Cl + lane) * n + m] = v;
     }
     __syncthreads();
@@ -357,27 +492,32 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_strided(GridDev g, AxisP
     if (a.mode != STR_INV) fft_any<T, NN, false>(buf, D * Cl, n, pl, tw, tws);
 
     if (a.mode == STR_FWD_SCALE) {
-        const T sc = (T)g.invM;
+        const T sc = inv_m(g, T());
         for (int e = threadIdx.x; e < D * Cl * n; e += blockDim.x) buf[e] = cscale(buf[e], sc);
         __syncthreads();
     } else if (a.mode == STR_GAMMA) {
         // q_hat = xi (xi . t_hat) / (xi . A0 xi) / |N| with t = A0 A u (Eq. Gamma_hat,
-        // G = Gamma A0); A0 = I unless has_A0
-        for (int e = threadIdx.x; e < Cl * n; e += blockDim.x) {
-            const int lane = e % Cl;
-            const int m = e / Cl;
-            const long long i = i0 + lane;
-            if (i >= inner) continue;
-            T xi[D];
-            xi[0] = (T)((double)freq_of(m, g.N[0]) / g.Y[0]);
+        // G = Gamma A0); A0 = I unless has_A0.  Computed in T.
+        const long long i = i0 + lane;
+        T xi_rest[D];        // the components of xi fixed by this lane
+        xi_rest[0] = T(0);
+        if (lane_ok) {
             if (D == 2) {
-                xi[1] = (T)((double)i / g.Y[1]);
+                xi_rest[1] = (T)i * inv_y(g, 1, T());
             } else {
                 const int k2 = (int)(i % g.H);
                 const int k1 = (int)(i / g.H);
-                xi[1] = (T)((double)freq_of(k1, g.N[1]) / g.Y[1]);
-                xi[D - 1] = (T)((double)k2 / g.Y[2]);
+                xi_rest[1] = (T)freq_of(k1, g.N[1]) * inv_y(g, 1, T());
+                xi_rest[D - 1] = (T)k2 * inv_y(g, D - 1, T());
             }
+        }
+        const T invY0 = inv_y(g, 0, T());
+        const T invM = inv_m(g, T());
+        for (int m = threadIdx.x / Cl; m < n && lane_ok; m += rstep) {
+            T xi[D];
+            xi[0] = (T)freq_of(m, n) * invY0;
+#pragma unroll
+            for (int al = 1; al < D; ++al) xi[al] = xi_rest[al];
             C th[D];
 #pragma unroll
             for (int al = 0; al < D; ++al) th[al] = buf[(al * Cl + lane) * n + m];
@@ -403,7 +543,7 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_strided(GridDev g, AxisP
             }
             C s = czero<T>();
             if (den > T(0)) {
-                const T f = (T)g.invM / den;
+                const T f = div_proj(invM, den);
                 s.x = num.x * f;
                 s.y = num.y * f;
             }
@@ -416,12 +556,13 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_strided(GridDev g, AxisP
         fft_any<T, NN, true>(buf, D * Cl, n, pl, tw, tws);
     }
 
-    for (int e = threadIdx.x; e < D * Cl * n; e += blockDim.x) {
-        const int lane = e % Cl;
-        const int rest = e / Cl;
-        const int m = rest % n;
-        const int al = rest / n;
-        if (i0 + lane < inner) S[base + al * cstride + (long long)m * inner + lane] = buf[(al * Cl + lane) * n + m];
+    if (lane_ok) {
+#pragma unroll 4
+        for (int row = threadIdx.x / Cl; row < D * n; row += rstep) {
+            const int al = row / n;
+            const int m = row - al * n;
+            Sb[al * cstride + m * inner] = buf[(al * Cl + lane) * n + m];
+        }
     }
 }
 
@@ -439,19 +580,23 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
     const int H = (Nl + 1) >> 1;
     const long long M = g.M, rows = g.rows;
     const long long row0 = (long long)blockIdx.x * RB;
+    const int nrow = (int)min((long long)RB, rows - row0);
     const int l0 = blockIdx.y * LB;
     const int nl = min(LB, a.L - l0);
     const int nreal = RB * nl * D;
     const int ncplx = (nreal + 1) >> 1;
     const C* tws = stage_twiddles<T, NN>(buf + ncplx * Nl, pl, tw);
 
-    __shared__ double s_alpha[MAXL];
-    __shared__ int s_act[MAXL];
+    __shared__ T s_alpha[D];
+    __shared__ int s_act[D];
+    __shared__ long long s_off[MAX_REAL_ROWS];
     if (threadIdx.x < nl) {
         const Scalars& s = a.sc[l0 + threadIdx.x];
         s_act[threadIdx.x] = (!a.check_status) || (s.status == ST_ACTIVE);
-        s_alpha[threadIdx.x] = s.alpha;
+        s_alpha[threadIdx.x] = alpha_of(s, T());
     }
+    __syncthreads();
+    row_offsets<D>(s_off, nreal, nl, l0, row0, nrow, s_act, rows, H);
     __syncthreads();
 
     // Rebuild two real rows a, b as one complex row Z = a + i b from their
@@ -462,79 +607,107 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
         const int kk = e - c * Nl;
         const bool up = kk >= H;
         const int ks = up ? Nl - kk : kk;
-        C v[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            v[h] = czero<T>();
-            const int rr = 2 * c + h;
-            if (rr < nreal) {
-                const int rowi = rr / (nl * D);
-                const int li = (rr / D) % nl;
-                const int al = rr % D;
-                const long long grow = row0 + rowi;
-                if (grow < rows && s_act[li])
-                    v[h] = S[(((long long)(l0 + li) * D + al) * rows + grow) * H + ks];
-            }
-            if (up) v[h].y = -v[h].y;
-        }
+        const long long o0 = s_off[2 * c];
+        const long long o1 = (2 * c + 1 < nreal) ? s_off[2 * c + 1] : -1;
+        C v0 = o0 >= 0 ? S[o0 + ks] : czero<T>();
+        C v1 = o1 >= 0 ? S[o1 + ks] : czero<T>();
+        if (up) { v0.y = -v0.y; v1.y = -v1.y; }
         C z;
-        z.x = v[0].x - v[1].y;
-        z.y = v[0].y + v[1].x;
+        z.x = v0.x - v1.y;
+        z.y = v0.y + v1.x;
         buf[c * Nl + kk] = z;
     }
     __syncthreads();
 
     fft_any<T, NN, true>(buf, ncplx, Nl, pl, tw, tws);
 
-    T* __restrict__ X = static_cast<T*>(a.x);
-    T* __restrict__ Rr = static_cast<T*>(a.r);
-    T* __restrict__ P = static_cast<T*>(a.p);
-    T* __restrict__ O = static_cast<T*>(a.out);
-    double acc[MAXL] = {0.0, 0.0, 0.0};
-    for (int e = threadIdx.x; e < RB * Nl; e += blockDim.x) {
-        const int rowi = e / Nl;
-        const int i = e - rowi * Nl;
-        const long long grow = row0 + rowi;
-        if (grow >= rows) continue;
-        const long long k = grow * Nl + i;
+    const long long kb = row0 * Nl;
+    T* Xb[D][D];
+    T* Rb[D][D];
+    T* Pb[D][D];
+    T* Ob[D][D];
 #pragma unroll
-        for (int li = 0; li < MAXL; ++li) {
-            if (li >= nl) break;
-            if (!s_act[li]) continue;
-            const int l = l0 + li;
-            const T alpha = (T)s_alpha[li];
-            double dsum = 0.0;
+    for (int li = 0; li < D; ++li)
 #pragma unroll
-            for (int al = 0; al < D; ++al) {
-                const int rr = (rowi * nl + li) * D + al;
-                const C z = buf[(rr >> 1) * Nl + i];
-                const T q = (rr & 1) ? z.y : z.x;
-                const long long idx = ((long long)l * D + al) * M + k;
-                if (a.mode == INV_CG) {
-                    X[idx] += alpha * P[idx];
-                    const T rv = Rr[idx] - alpha * q;
-                    Rr[idx] = rv;
-                    dsum += (double)rv * (double)rv;
-                } else if (a.mode == INV_RHS) {
-                    const T rv = -q;
-                    Rr[idx] = rv;
-                    P[idx] = rv;
-                    X[idx] = T(0);
-                    dsum += (double)rv * (double)rv;
-                } else if (a.mode == INV_RESID) {
-                    const T rv = -q;
-                    Rr[idx] = rv;
-                    dsum += (double)rv * (double)rv;
-                } else {
-                    O[idx] = q;
+        for (int al = 0; al < D; ++al) {
+            const long long off = ((long long)(l0 + li) * D + al) * M + kb;
+            Xb[li][al] = a.x ? static_cast<T*>(a.x) + off : nullptr;
+            Rb[li][al] = a.r ? static_cast<T*>(a.r) + off : nullptr;
+            Pb[li][al] = a.p ? static_cast<T*>(a.p) + off : nullptr;
+            Ob[li][al] = a.out ? static_cast<T*>(a.out) + off : nullptr;
+        }
+    T alpha_t[D];
+    bool act[D];
+#pragma unroll
+    for (int li = 0; li < D; ++li) {
+        act[li] = li < nl && s_act[li];
+        alpha_t[li] = li < nl ? s_alpha[li] : T(0);
+    }
+    T tacc[MAXL] = {T(0), T(0), T(0)};
+    constexpr int UNR = 2;
+    const int total = nrow * Nl;
+    const bool cgm = a.mode == INV_CG;
+    for (int e0 = threadIdx.x; e0 < total; e0 += UNR * blockDim.x) {
+        T xv[UNR][D][D], rv0[UNR][D][D], pv[UNR][D][D];
+        if (cgm) {
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int e = e0 + u * blockDim.x;
+                const bool valid = e < total;
+#pragma unroll
+                for (int li = 0; li < D; ++li) {
+                    if (li >= nl) break;
+                    const bool on = valid && act[li];
+#pragma unroll
+                    for (int al = 0; al < D; ++al) {
+                        xv[u][li][al] = on ? Xb[li][al][e] : T(0);
+                        rv0[u][li][al] = on ? Rb[li][al][e] : T(0);
+                        pv[u][li][al] = on ? Pb[li][al][e] : T(0);
+                    }
                 }
             }
-            acc[li] += dsum;
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e >= total) break;
+            const int rowi = e / Nl;
+            const int i = e - rowi * Nl;
+#pragma unroll
+            for (int li = 0; li < D; ++li) {
+                if (li >= nl) break;
+                if (!act[li]) continue;
+#pragma unroll
+                for (int al = 0; al < D; ++al) {
+                    const int rr = (rowi * nl + li) * D + al;
+                    const C z = buf[(rr >> 1) * Nl + i];
+                    const T q = (rr & 1) ? z.y : z.x;
+                    if (cgm) {
+                        Xb[li][al][e] = xv[u][li][al] + alpha_t[li] * pv[u][li][al];
+                        const T rnew = rv0[u][li][al] - alpha_t[li] * q;
+                        Rb[li][al][e] = rnew;
+                        tacc[li] += rnew * rnew;
+                    } else if (a.mode == INV_RHS) {
+                        const T rnew = -q;
+                        Rb[li][al][e] = rnew;
+                        Pb[li][al][e] = rnew;
+                        Xb[li][al][e] = T(0);
+                        tacc[li] += rnew * rnew;
+                    } else if (a.mode == INV_RESID) {
+                        const T rnew = -q;
+                        Rb[li][al][e] = rnew;
+                        tacc[li] += rnew * rnew;
+                    } else {
+                        Ob[li][al][e] = q;
+                    }
+                }
+            }
         }
     }
 
     if (a.mode == INV_OUT) return;
-    block_sum<MAXL>(acc);
+    double acc[MAXL];
+    block_sum_t<T, MAXL>(tacc, acc);
     const long long nbx = gridDim.x;
     const unsigned nblocks = gridDim.x * gridDim.y;
     int slots[MAXL];
@@ -557,11 +730,13 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
                 else if (rel <= s.tol) s.status = ST_CONVERGED;
                 else if (s.iters >= s.max_iter) s.status = ST_MAXITER;
                 s.beta = rr / s.rr;
+                s.beta_f = (float)s.beta;
                 s.rr = rr;
             } else if (a.mode == INV_RHS) {
                 s.rr = rr;
                 s.bnorm = sqrt(rr);
                 s.beta = 0.0;
+                s.beta_f = 0.f;
                 s.iters = 0;
                 s.relres = 1.0;
                 // b = -G A E vanishes in exact arithmetic when A E is constant

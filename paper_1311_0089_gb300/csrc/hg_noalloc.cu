@@ -113,13 +113,19 @@ extern "C" int hg_apply_noalloc(int d, const int* N, const uint8_t* phase, int n
     memset(&gd, 0, sizeof(gd));
     gd.d = d;
     gd.M = 1;
-    for (int a = 0; a < 3; ++a) { gd.N[a] = a < d ? N[a] : 1; gd.Y[a] = 1.0; }
+    for (int a = 0; a < 3; ++a) {
+        gd.N[a] = a < d ? N[a] : 1;
+        gd.Y[a] = 1.0;
+        gd.invY[a] = 1.0;
+        gd.invYf[a] = 1.0f;
+    }
     for (int a = 0; a < d; ++a) gd.M *= N[a];
     gd.Nl = N[d - 1];
     gd.H = (gd.Nl + 1) / 2;
     gd.rows = gd.M / gd.Nl;
     gd.Ms = gd.rows * gd.H;
     gd.invM = 1.0 / (double)gd.M;
+    gd.invMf = (float)gd.invM;
 
     // scratch layout: scalars | counters | twiddles | reduction slots | half spectrum
     AxisPlanH plan[3];
@@ -180,6 +186,7 @@ extern "C" int hg_apply_noalloc(int d, const int* N, const uint8_t* phase, int n
 
     CoeffsDev co;
     co.mode = 0;
+    co.n_phases = n_phases;
     co.phase = phase;
     co.table = table;
     co.field = nullptr;
