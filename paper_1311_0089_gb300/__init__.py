@@ -46,7 +46,7 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("prec", ctypes.c_int),
                 ("lambda_ref", ctypes.c_double), ("loads_mask", ctypes.c_uint),
                 ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
-                ("max_outer", ctypes.c_int)]
+                ("max_outer", ctypes.c_int), ("time_pass", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -54,7 +54,8 @@ class Result(ctypes.Structure):
                 ("AH_flux", ctypes.c_double * 9), ("iters", ctypes.c_int * 3),
                 ("outer", ctypes.c_int * 3), ("rel_res", ctypes.c_double * 3),
                 ("device_ms", ctypes.c_double), ("wall_ms", ctypes.c_double),
-                ("launches", ctypes.c_longlong)]
+                ("launches", ctypes.c_longlong), ("pass_ms_total", ctypes.c_double),
+                ("pass_launches", ctypes.c_int)]
 
     def to_dict(self) -> dict:
         d = self.d
@@ -68,6 +69,8 @@ class Result(ctypes.Structure):
             "device_ms": self.device_ms,
             "wall_ms": self.wall_ms,
             "launches": self.launches,
+            "pass_ms_total": self.pass_ms_total,
+            "pass_launches": self.pass_launches,
         }
 
 

@@ -348,24 +348,63 @@ int enqueue_forward_strided(hg_grid* g, int prec, int L, int check_status, int g
     return HG_OK;
 }
 
-int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s) {
+// One CG iteration (d + 1 launches).  prof_pass >= 0: event records bracket
+// that pass (0 row_fwd, 1..d-1 strided in launch order, d row_inv).
+int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_pass,
+                         cudaEvent_t ev_before, cudaEvent_t ev_after) {
     const GridDev& gd = g->gd;
     Work& w = g->work[prec];
     const int last = gd.d - 1;
+    const int d = gd.d;
+    int pass = 0;
+    // inside stream capture only an external event record becomes a real event
+    // record node (a plain record just orders the graph)
+    auto mark = [&](bool before) -> cudaError_t {
+        if (prof_pass != pass) return cudaSuccess;
+        return cudaEventRecordWithFlags(before ? ev_before : ev_after, s, cudaEventRecordExternal);
+    };
     RowFwdArgs fa;
     memset(&fa, 0, sizeof(fa));
     fa.mode = FWD_CG; fa.L = L; fa.co = coeffs_for(g, prec, true);
     fa.p = w.p; fa.r = w.r; fa.S = w.S; fa.sc = w.sc;
     fa.partial = g->partial; fa.counter = g->counters + 0; fa.check_status = 1;
+    HG_CU(mark(true));
     HG_CU(launch_row_fwd(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], fa, s));
+    HG_CU(mark(false));
     g->ctx->launches++;
-    int st = enqueue_forward_strided(g, prec, L, 1, STR_GAMMA, nullptr, s);
-    if (st) return st;
+    ++pass;
+    StrArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.L = L; sa.S = w.S; sa.sc = w.sc; sa.check_status = 1;
+    if (d == 3) {
+        sa.mode = STR_FWD; sa.axis = 1; sa.outer = gd.N[0]; sa.n = gd.N[1]; sa.inner = gd.H;
+        HG_CU(mark(true));
+        HG_CU(launch_strided(prec, gd, g->plan[1], g->tw[prec], g->strcfg[prec][1], sa, s));
+        HG_CU(mark(false));
+        g->ctx->launches++;
+        ++pass;
+    }
+    sa.mode = STR_GAMMA; sa.axis = 0; sa.outer = 1; sa.n = gd.N[0]; sa.inner = gd.Ms / gd.N[0];
+    HG_CU(mark(true));
+    HG_CU(launch_strided(prec, gd, g->plan[0], g->tw[prec], g->strcfg[prec][0], sa, s));
+    HG_CU(mark(false));
+    g->ctx->launches++;
+    ++pass;
+    if (d == 3) {
+        sa.mode = STR_INV; sa.axis = 1; sa.outer = gd.N[0]; sa.n = gd.N[1]; sa.inner = gd.H;
+        HG_CU(mark(true));
+        HG_CU(launch_strided(prec, gd, g->plan[1], g->tw[prec], g->strcfg[prec][1], sa, s));
+        HG_CU(mark(false));
+        g->ctx->launches++;
+        ++pass;
+    }
     RowInvArgs ia;
     memset(&ia, 0, sizeof(ia));
     ia.mode = INV_CG; ia.L = L; ia.S = w.S; ia.x = w.x; ia.r = w.r; ia.p = w.p;
     ia.sc = w.sc; ia.partial = g->partial; ia.counter = g->counters + 1; ia.check_status = 1;
+    HG_CU(mark(true));
     HG_CU(launch_row_inv(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], ia, s));
+    HG_CU(mark(false));
     g->ctx->launches++;
     return HG_OK;
 }
@@ -397,9 +436,9 @@ int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, const double* E, 
 }
 
 // A CUDA graph of `chunk` CG iterations, cached per precision.
-int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nkern) {
+int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nkern, int prof_pass) {
     GraphCache& gc = g->graphs[prec];
-    if (gc.exec && gc.chunk == chunk) {
+    if (gc.exec && gc.chunk == chunk && gc.prof_pass == prof_pass) {
         *out = gc.exec;
         *nkern = gc.nkern;
         return HG_OK;
@@ -410,9 +449,16 @@ int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nke
     }
     cudaStream_t s = g->ctx->cap_stream;
     const long long before = g->ctx->launches.load();
-    HG_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     int st = HG_OK;
-    for (int i = 0; i < chunk && st == HG_OK; ++i) st = enqueue_cg_iteration(g, prec, g->gd.d, s);
+    HG_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    if (prof_pass >= 0) {
+        for (int i = 0; i < 2 * chunk; ++i)
+            if (!g->prof_ev[i] && cudaEventCreate(&g->prof_ev[i]) != cudaSuccess) st = HG_ERR_CUDA;
+    }
+    for (int i = 0; i < chunk && st == HG_OK; ++i)
+        st = prof_pass >= 0 ? enqueue_cg_iteration(g, prec, g->gd.d, s, prof_pass, g->prof_ev[2 * i],
+                                                   g->prof_ev[2 * i + 1])
+                            : enqueue_cg_iteration(g, prec, g->gd.d, s);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &graph);
     const long long nk = g->ctx->launches.load() - before;
@@ -423,6 +469,7 @@ int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nke
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) { set_last_cuda_error(e, "cudaGraphInstantiate"); gc.exec = nullptr; return HG_ERR_CUDA; }
     gc.chunk = chunk;
+    gc.prof_pass = prof_pass;
     gc.nkern = (int)nk;
     *out = gc.exec;
     *nkern = gc.nkern;
@@ -443,11 +490,31 @@ static int map_status(int s) {
 // ----------------------------------------------------------------------------
 // Enqueue one graph chunk of CG iterations of precision `prec`, then the copy
 // of that precision's scalars to pinned host memory and the tick event.
+// time_pass: add the durations of the timed pass over the iterations of the
+// chunk that just completed in which at least one system was active.
+static void job_collect_pass_times(Job& j) {
+    if (j.o.time_pass < 0) return;
+    const Scalars* h = j.g->h_sc;
+    int it = 0;
+    for (int l = 0; l < j.g->gd.d; ++l) it = std::max(it, h[l].iters);
+    const int k = std::min(j.chunk, std::max(0, it - j.prof_prev_iters));
+    for (int i = 0; i < k; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, j.g->prof_ev[2 * i], j.g->prof_ev[2 * i + 1]) == cudaSuccess) {
+            j.prof_ms += ms;
+            j.prof_n += 1;
+        } else {
+            cudaGetLastError();   // a timing failure must not reach later status checks
+        }
+    }
+    j.prof_prev_iters = it;
+}
+
 static int job_launch_chunk(Job& j, int prec) {
     hg_grid* g = j.g;
     cudaGraphExec_t ge;
     int nk = 0;
-    int st = get_cg_graph(g, prec, j.chunk, &ge, &nk);
+    int st = get_cg_graph(g, prec, j.chunk, &ge, &nk, j.o.time_pass);
     if (st) return st;
     HG_CU(cudaGraphLaunch(ge, j.s));
     g->ctx->launches += nk;
@@ -478,6 +545,7 @@ static int job_start_inner(Job& j) {
                             j.o.inner_tol, j.o.max_iter, g->partial, g->counters + 4, j.s));
     g->ctx->launches++;
     j.launched = 0;
+    j.prof_prev_iters = 0;
     j.phase = Job::INNER;
     return job_launch_chunk(j, 1);
 }
@@ -507,6 +575,9 @@ int job_begin(Job& j) {
     j.outer = 0;
     j.launched = 0;
     j.result = HG_OK;
+    j.prof_prev_iters = 0;
+    j.prof_ms = 0.0;
+    j.prof_n = 0;
     if (g->coeff_mode < 0) return HG_ERR_NO_COEFFS;
     int st;
     if ((st = grid_alloc_common(g))) return st;
@@ -537,6 +608,7 @@ int job_advance(Job& j, bool* done) {
     switch (j.phase) {
         case Job::PLAIN:
         case Job::INNER: {
+            job_collect_pass_times(j);
             const int mi = j.o.max_iter;
             if (any_active(h, L) && j.launched <= (long long)mi + 2 * j.chunk)
                 return job_launch_chunk(j, j.cg_prec);
@@ -579,6 +651,8 @@ int job_advance(Job& j, bool* done) {
             r.device_ms = dms;
             r.wall_ms = now_ms() - j.t0;
             r.launches = g->ctx->launches.load() - j.launches0;
+            r.pass_ms_total = j.prof_ms;
+            r.pass_launches = j.prof_n;
             g->last_prec = j.prec;
             j.result = result;
             j.phase = Job::DONE;

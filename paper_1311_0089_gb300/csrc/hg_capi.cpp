@@ -89,6 +89,7 @@ void hg_default_opts(hg_solve_opts* o) {
     o->inner_tol = 1e-4;
     o->check_every = 8;
     o->max_outer = 30;
+    o->time_pass = -1;
 }
 
 const char* hg_strerror(int s) {
@@ -235,6 +236,8 @@ int hg_destroy_grid(hg_grid* g) {
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     if (g->ev_tick) cudaEventDestroy(g->ev_tick);
+    for (int i = 0; i < 2 * hgrt::MAX_PROF_CHUNK; ++i)
+        if (g->prof_ev[i]) cudaEventDestroy(g->prof_ev[i]);
     if (g->counted) c->ngrids -= 1;
     delete g;
     return HG_OK;
@@ -345,6 +348,8 @@ int hg_solve_AH(hg_grid* g, const hg_solve_opts* opts, double* AH_out, hg_result
     if (opts) o = *opts; else hg_default_opts(&o);
     if (!(o.tol > 0.0) || o.max_iter < 1 || (o.prec != HG_FP64 && o.prec != HG_MIXED) ||
         !(o.inner_tol > 0.0) || o.inner_tol >= 1.0)
+        return HG_ERR_ARG;
+    if (o.time_pass >= hg_num_passes(g) || (o.time_pass >= 0 && o.check_every > hgrt::MAX_PROF_CHUNK))
         return HG_ERR_ARG;
     o.loads_mask &= (1u << g->gd.d) - 1u;
     if (g->borrowed.load() > 0) return HG_ERR_BUSY;

@@ -35,6 +35,8 @@ struct hg_ctx {
 
 namespace hgrt {
 
+constexpr int MAX_PROF_CHUNK = 64;   // iterations per graph when a pass is timed
+
 struct Work {
     void* x = nullptr;
     void* r = nullptr;
@@ -48,6 +50,7 @@ struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int chunk = 0;
     int nkern = 0;
+    int prof_pass = -1;   // pass bracketed by event records (-1: none)
 };
 
 }  // namespace hgrt
@@ -77,6 +80,7 @@ struct hg_grid {
     double* h_AH = nullptr;        // pinned: 2 d x d (energy, flux)
     hgrt::GraphCache graphs[2];
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_tick = nullptr;
+    cudaEvent_t prof_ev[2 * hgrt::MAX_PROF_CHUNK] = {};   // per-iteration pass brackets
     int last_prec = 0;
     bool counted = false;
     std::atomic<int> borrowed{0};
@@ -100,11 +104,12 @@ int grid_alloc_common(hg_grid* g);
 hgk::CoeffsDev coeffs_for(const hg_grid* g, int prec, bool withA);
 int enqueue_forward_strided(hg_grid* g, int prec, int L, int check_status, int gamma_mode,
                             const double* A0, cudaStream_t s);
-int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s);
+int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_pass = -1,
+                         cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);
 int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, const double* E, bool withA,
                    const double* A0dev, const double* A0host, int inv_mode, void* out,
                    int check_status, cudaStream_t s);
-int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nkern);
+int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nkern, int prof_pass = -1);
 
 // One solve as a resumable state machine: job_begin enqueues the first
 // steps; each time the job's tick event has completed, job_advance reads the
@@ -119,6 +124,9 @@ struct Job {
     long long launched = 0, launches0 = 0;
     double t0 = 0.0;
     hg_result res{};
+    int prof_prev_iters = 0;    // time_pass: iterations done before the chunk in flight
+    double prof_ms = 0.0;
+    int prof_n = 0;
 };
 int job_begin(Job& j);
 int job_advance(Job& j, bool* done);

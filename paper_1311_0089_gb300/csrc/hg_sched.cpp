@@ -208,6 +208,7 @@ int sched_submit(Scheduler* S, hg_grid* g, const hg_solve_opts* opts, uint64_t* 
     if (!(o.tol > 0.0) || o.max_iter < 1 || (o.prec != HG_FP64 && o.prec != HG_MIXED) ||
         !(o.inner_tol > 0.0) || o.inner_tol >= 1.0)
         return HG_ERR_ARG;
+    o.time_pass = -1;   // per-pass timing is a blocking-solve diagnostic
     if (g->coeff_mode < 0) return HG_ERR_NO_COEFFS;
     o.loads_mask &= (1u << g->gd.d) - 1u;
     int expect = 0;

@@ -247,3 +247,18 @@ def test_submit_poll_matches_blocking(hg, ctx):
         assert rel_max(a["AH"], b["AH"]) < 1e-12
     for g in grids:
         g.close()
+
+
+def test_time_pass_in_graph(hg, ctx):
+    ms = W.circles_2d(n=45, count=4, r_lo=3, r_hi=8, contrast=50.0, seed=3)
+    g = ctx.grid(ms.N)
+    g.set_coeffs_phase(ms.phase, ms.table)
+    plain = g.solve(hg.default_opts(tol=1e-8))
+    for p in range(g.num_passes()):
+        r = g.solve(hg.default_opts(tol=1e-8, time_pass=p))
+        assert r["pass_launches"] == max(r["iters"])
+        assert r["pass_ms_total"] > 0.0
+        np.testing.assert_allclose(r["AH"], plain["AH"], rtol=1e-13)
+    with pytest.raises(hg.HGError):
+        g.solve(hg.default_opts(time_pass=g.num_passes()))
+    g.close()
