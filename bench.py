@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tol", type=float, default=TOL)
+    ap.add_argument("--passes-once", action="store_true",
+                    help="launch every CG pass twice (FP32 then FP64) on the workload and exit "
+                         "(a short command for ncu captures)")
     return ap.parse_args()
 
 
@@ -437,8 +440,28 @@ def run_ours(args):
     return 0
 
 
+def run_passes_once(args):
+    import torch
+    import paper_1311_0089_gb300 as hg
+    torch.cuda.set_device(0)
+    hg.load()
+    ms, _ = workload()
+    ctx = hg.Context(0)
+    g = ctx.grid(ms.N)
+    g.set_coeffs_phase(ms.phase, ms.table)
+    for prec in (hg.HG_MIXED, hg.HG_FP64):
+        for p in range(g.num_passes()):
+            t, name = g.time_pass(p, prec, reps=1)
+            print(f"{name}: {t * 1e3:.1f} us")
+    g.close()
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.passes_once:
+        return run_passes_once(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -296,13 +296,20 @@ template <typename T, int N> struct CtCaps {
 // with every size known at compile time.  `tw` is this stage's twiddle table
 // in shared memory, laid out [r-1][k] (k = j mod NS): consecutive threads read
 // consecutive entries.
-template <typename T, int N, int R, int NS, bool INV, int NPMAX>
-__device__ __forceinline__ void stage_ct(typename cplx_t<T>::type* buf, int npen,
+//
+// Layouts: ILD = 0 -> pencil p occupies buf[p N .. p N + N) (contiguous);
+// ILD = D > 0 -> pencil (al, lane), al < D, lane < Cl = 2^lgCl, element j at
+// buf[(al N + j) Cl + lane] (interleaved lanes), with the pencil index
+// running fastest across threads so that neighbouring threads touch
+// neighbouring words.
+template <typename T, int N, int R, int NS, bool INV, int NPMAX, int ILD>
+__device__ __forceinline__ void stage_ct(typename cplx_t<T>::type* buf, int npen, int lgCl,
                                          const typename cplx_t<T>::type* tw) {
     typedef typename cplx_t<T>::type C;
     constexpr int NB = N / R;
     constexpr int B = (NPMAX * NB + CT_THREADS - 1) / CT_THREADS;
     const int total = npen * NB;
+    const int es = ILD > 0 ? (1 << lgCl) : 1;     // element stride
     C v[B][R];
     int dst[B];
 #pragma unroll
@@ -310,18 +317,28 @@ __device__ __forceinline__ void stage_ct(typename cplx_t<T>::type* buf, int npen
         const int idx = threadIdx.x + b * CT_THREADS;
         dst[b] = -1;
         if (idx < total) {
-            const int pen = idx / NB;
-            const int j = idx - pen * NB;
+            int base, j;
+            if constexpr (ILD > 0) {
+                const int lane = idx & (es - 1);
+                const int t = idx >> lgCl;
+                const int al = t % ILD;
+                j = t / ILD;
+                base = al * N * es + lane;
+            } else {
+                const int pen = idx / NB;
+                j = idx - pen * NB;
+                base = pen * N;
+            }
             const int k = j % NS;
-            const C* src = buf + pen * N + j;
+            const C* src = buf + base + j * es;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[b][r] = src[r * NB];
+            for (int r = 0; r < R; ++r) v[b][r] = src[r * NB * es];
             if constexpr (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) v[b][r] = cmulw<INV>(v[b][r], tw[(r - 1) * NS + k]);
             }
             DftAny<R, INV, C>::run(v[b]);
-            dst[b] = pen * N + (j - k) * R + k;
+            dst[b] = base + ((j - k) * R + k) * es;
         }
     }
     __syncthreads();
@@ -329,7 +346,7 @@ __device__ __forceinline__ void stage_ct(typename cplx_t<T>::type* buf, int npen
     for (int b = 0; b < B; ++b) {
         if (dst[b] >= 0) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[dst[b] + r * NS] = v[b][r];
+            for (int r = 0; r < R; ++r) buf[dst[b] + r * NS * es] = v[b][r];
         }
     }
     __syncthreads();
@@ -340,7 +357,8 @@ __device__ __forceinline__ void stage_ct(typename cplx_t<T>::type* buf, int npen
 template <typename T, int N, bool INV, int NPMAX, int NS, int OFF, int... Rs> struct CtStages;
 template <typename T, int N, bool INV, int NPMAX, int NS, int OFF> struct CtStages<T, N, INV, NPMAX, NS, OFF> {
     static constexpr int tw_size = OFF;
-    __device__ __forceinline__ static void run(typename cplx_t<T>::type*, int, const typename cplx_t<T>::type*) {}
+    template <int ILD>
+    __device__ __forceinline__ static void run(typename cplx_t<T>::type*, int, int, const typename cplx_t<T>::type*) {}
     __device__ __forceinline__ static void build(typename cplx_t<T>::type*, const typename cplx_t<T>::type*) {}
 };
 template <typename T, int N, bool INV, int NPMAX, int NS, int OFF, int R, int... Rs>
@@ -348,10 +366,11 @@ struct CtStages<T, N, INV, NPMAX, NS, OFF, R, Rs...> {
     static constexpr int here = NS > 1 ? (R - 1) * NS : 0;
     typedef CtStages<T, N, INV, NPMAX, NS * R, OFF + here, Rs...> Next;
     static constexpr int tw_size = Next::tw_size;
-    __device__ __forceinline__ static void run(typename cplx_t<T>::type* buf, int npen,
+    template <int ILD>
+    __device__ __forceinline__ static void run(typename cplx_t<T>::type* buf, int npen, int lgCl,
                                                const typename cplx_t<T>::type* twst) {
-        stage_ct<T, N, R, NS, INV, NPMAX>(buf, npen, twst + OFF);
-        Next::run(buf, npen, twst);
+        stage_ct<T, N, R, NS, INV, NPMAX, ILD>(buf, npen, lgCl, twst + OFF);
+        Next::template run<ILD>(buf, npen, lgCl, twst);
     }
     // twst[OFF + (r-1) NS + k] = tw_nat[r k N/(NS R)]
     __device__ __forceinline__ static void build(typename cplx_t<T>::type* twst,
@@ -371,9 +390,10 @@ struct CtStages<T, N, INV, NPMAX, NS, OFF, R, Rs...> {
 template <typename T, int N, bool INV, typename L> struct CtRun;
 template <typename T, int N, bool INV, int... Rs> struct CtRun<T, N, INV, RadixList<Rs...>> {
     typedef CtStages<T, N, INV, CtCaps<T, N>::npmax, 1, 0, Rs...> S;
-    __device__ __forceinline__ static void run(typename cplx_t<T>::type* buf, int npen,
+    template <int ILD>
+    __device__ __forceinline__ static void run(typename cplx_t<T>::type* buf, int npen, int lgCl,
                                                const typename cplx_t<T>::type* twst) {
-        S::run(buf, npen, twst);
+        S::template run<ILD>(buf, npen, lgCl, twst);
     }
 };
 
@@ -382,7 +402,14 @@ template <typename T, int N, bool INV, int... Rs> struct CtRun<T, N, INV, RadixL
 template <typename T, int N, bool INV>
 __device__ __forceinline__ void fft_ct(typename cplx_t<T>::type* buf, int npen,
                                        const typename cplx_t<T>::type* twst) {
-    CtRun<T, N, INV, typename CtPlan<T, N>::type>::run(buf, npen, twst);
+    CtRun<T, N, INV, typename CtPlan<T, N>::type>::template run<0>(buf, npen, 0, twst);
+}
+
+// Interleaved layout: D components x 2^lgCl lanes (see stage_ct).
+template <typename T, int N, bool INV, int D>
+__device__ __forceinline__ void fft_ct_il(typename cplx_t<T>::type* buf, int lgCl,
+                                          const typename cplx_t<T>::type* twst) {
+    CtRun<T, N, INV, typename CtPlan<T, N>::type>::template run<D>(buf, D << lgCl, lgCl, twst);
 }
 
 template <typename T, int N>

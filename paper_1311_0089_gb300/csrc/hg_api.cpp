@@ -155,7 +155,7 @@ bool choose_row_cfg(int prec, int n, int d, int L, int minR, size_t csize, int m
 bool choose_str_cfg(int prec, int n, int d, int minR, size_t csize, int max_smem,
                     long long inner, long long outer, int L, StrCfg& cfg) {
     const int maxb = 2, maxt = row_max_threads();
-    const int prefer_lanes = prec == 0 ? 2 : 4;
+    const int prefer_lanes = 2;   // more, smaller CTAs beat full 32-byte rows here
     if (ct_length(d, n)) {
         const int npmax = ct_npmax(prec, n);
         int best = 0;

@@ -222,6 +222,14 @@ __device__ __forceinline__ Cx<T>* stage_twiddles(Cx<T>* smem_after, const AxisPl
 
 template <int NN> struct PassThreads { static constexpr int v = NN > 0 ? CT_THREADS : MAXT; };
 
+// Strided-pass transform: interleaved layout for the compile-time kernels.
+template <typename T, int D, int NN, bool INV>
+__device__ __forceinline__ void fft_str(Cx<T>* buf, int Cl, int lgCl, int n, const AxisPlanH& pl,
+                                        const Cx<T>* __restrict__ twg, const Cx<T>* tws) {
+    if constexpr (NN > 0) fft_ct_il<T, NN, INV, D>(buf, lgCl, tws);
+    else fft_pencils<T, INV, MAXB>(buf, D * Cl, n, pl, twg);
+}
+
 // CG scalars in the kernel's precision (FP32 copies are written beside the
 // FP64 values by the reducing CTA).
 __device__ __forceinline__ float beta_of(const Scalars& s, float) { return s.beta_f; }
@@ -284,7 +292,17 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
         s_beta[threadIdx.x] = beta_of(s, T());
     }
     const T* tab = stage_table<T, D>(a.co, s_tab);
+    __shared__ int s_any;
+    if (threadIdx.x == 0) {
+        // a launch in which no system is ACTIVE (the tail of a graph chunk after
+        // convergence) does no work; every CTA sees the same statuses, so none
+        // of them takes a ticket and the counter stays at zero
+        int any = 0;
+        for (int l = 0; l < a.L; ++l) any |= (!a.check_status) || (a.sc[l].status == ST_ACTIVE);
+        s_any = any;
+    }
     __syncthreads();
+    if (!s_any) return;
     row_offsets<D>(s_off, nreal, nl, l0, row0, nrow, s_act, rows, H);
     T beta_t[D];
     bool act[D];
@@ -294,21 +312,19 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
         beta_t[li] = li < nl ? s_beta[li] : T(0);
     }
 
-    // tile base pointers: the RB rows of a tile are contiguous in memory
+    // tile bases: the RB rows of a tile are contiguous in memory; component
+    // (li, al) of the tile starts (li D + al) M after these
     const long long kb = row0 * Nl;
     const bool cg = a.mode == FWD_CG;
-    T* Pb[D][D];
-    const T* Rb[D][D];
+    const long long b0 = (long long)l0 * D * M + kb;
+    T* const Pt = cg ? static_cast<T*>(a.p) + b0 : nullptr;
+    const T* const Rt = cg ? static_cast<const T*>(a.r) + b0 : (a.u ? static_cast<const T*>(a.u) + b0 : nullptr);
+    const unsigned Mu = (unsigned)M;
     T Ev[D][D];
 #pragma unroll
     for (int li = 0; li < D; ++li)
 #pragma unroll
-        for (int al = 0; al < D; ++al) {
-            const long long off = ((long long)(l0 + li) * D + al) * M + kb;
-            Pb[li][al] = cg ? static_cast<T*>(a.p) + off : nullptr;
-            Rb[li][al] = cg ? static_cast<const T*>(a.r) + off : (a.u ? static_cast<const T*>(a.u) + off : nullptr);
-            Ev[li][al] = (!cg && a.E && li < nl) ? (T)a.E[(l0 + li) * D + al] : T(0);
-        }
+        for (int al = 0; al < D; ++al) Ev[li][al] = (!cg && a.E && li < nl) ? (T)a.E[(l0 + li) * D + al] : T(0);
     const uint8_t* phb = a.co.phase ? a.co.phase + kb : nullptr;
     CoeffsDev co = a.co;     // phase map / packed field shifted to the tile
     co.phase = phb;
@@ -317,7 +333,7 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
     // per-thread partial sums in T over this thread's voxels, FP64 above the warp
     T tacc[MAXL] = {T(0), T(0), T(0)};
     const int total = nrow * Nl;
-    constexpr int UNR = 2;
+    constexpr int UNR = D == 2 ? 2 : 1;   // loads in flight vs registers (3D is register-bound)
     for (int e0 = threadIdx.x; e0 < RB * Nl; e0 += UNR * blockDim.x) {
         T vv[UNR][D][D];
         T pp[UNR][D][D];
@@ -333,8 +349,9 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
                 const bool on = valid && act[li];
 #pragma unroll
                 for (int al = 0; al < D; ++al) {
-                    vv[u][li][al] = (on && Rb[li][al]) ? Rb[li][al][e] : T(0);
-                    pp[u][li][al] = (on && cg) ? Pb[li][al][e] : T(0);
+                    const size_t o = (size_t)(li * D + al) * Mu + e;
+                    vv[u][li][al] = (on && Rt) ? Rt[o] : T(0);
+                    pp[u][li][al] = (on && cg) ? Pt[o] : T(0);
                 }
             }
         }
@@ -357,7 +374,7 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
                     for (int al = 0; al < D; ++al) {
                         if (cg) {
                             v[al] = vv[u][li][al] + beta_t[li] * pp[u][li][al];
-                            Pb[li][al][e] = v[al];
+                            Pt[(size_t)(li * D + al) * Mu + e] = v[al];
                         } else {
                             v[al] = vv[u][li][al] + Ev[li][al];
                         }
@@ -477,6 +494,12 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_strided(GridDev g, AxisP
     const int lane = threadIdx.x & (Cl - 1);
     const int rstep = blockDim.x / Cl;
     const bool lane_ok = i0 + lane < inner;
+    const int lgCl = 31 - __clz(Cl);
+    // shared layout: compile-time kernels interleave the lanes
+    // ([component][position][lane]); the runtime kernel keeps pencils contiguous
+    auto sidx = [&](int al, int m) -> int {
+        return NN > 0 ? (al * n + m) * Cl + lane : (al * Cl + lane) * n + m;
+    };
     C* Sb = static_cast<C*>(a.S) + (long long)l * D * g.Ms + o * (long long)n * inner + i0 + lane;
     const long long cstride = g.Ms;
 #pragma unroll 4
@@ -485,11 +508,11 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_strided(GridDev g, AxisP
         const int m = row - al * n;
         C v = czero<T>();
         if (lane_ok) v = Sb[al * cstride + m * inner];
-        buf[(al * Cl + lane) * n + m] = v;
+        buf[sidx(al, m)] = v;
     }
     __syncthreads();
 
-    if (a.mode != STR_INV) fft_any<T, NN, false>(buf, D * Cl, n, pl, tw, tws);
+    if (a.mode != STR_INV) fft_str<T, D, NN, false>(buf, Cl, lgCl, n, pl, tw, tws);
 
     if (a.mode == STR_FWD_SCALE) {
         const T sc = inv_m(g, T());
@@ -520,7 +543,7 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_strided(GridDev g, AxisP
             for (int al = 1; al < D; ++al) xi[al] = xi_rest[al];
             C th[D];
 #pragma unroll
-            for (int al = 0; al < D; ++al) th[al] = buf[(al * Cl + lane) * n + m];
+            for (int al = 0; al < D; ++al) th[al] = buf[sidx(al, m)];
             T den = T(0);
             C num = czero<T>();
             if (a.has_A0) {
@@ -548,12 +571,12 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_strided(GridDev g, AxisP
                 s.y = num.y * f;
             }
 #pragma unroll
-            for (int al = 0; al < D; ++al) buf[(al * Cl + lane) * n + m] = cscale(s, xi[al]);
+            for (int al = 0; al < D; ++al) buf[sidx(al, m)] = cscale(s, xi[al]);
         }
         __syncthreads();
-        fft_any<T, NN, true>(buf, D * Cl, n, pl, tw, tws);
+        fft_str<T, D, NN, true>(buf, Cl, lgCl, n, pl, tw, tws);
     } else if (a.mode == STR_INV) {
-        fft_any<T, NN, true>(buf, D * Cl, n, pl, tw, tws);
+        fft_str<T, D, NN, true>(buf, Cl, lgCl, n, pl, tw, tws);
     }
 
     if (lane_ok) {
@@ -561,7 +584,7 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_strided(GridDev g, AxisP
         for (int row = threadIdx.x / Cl; row < D * n; row += rstep) {
             const int al = row / n;
             const int m = row - al * n;
-            Sb[al * cstride + m * inner] = buf[(al * Cl + lane) * n + m];
+            Sb[al * cstride + m * inner] = buf[sidx(al, m)];
         }
     }
 }
@@ -590,12 +613,19 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
     __shared__ T s_alpha[D];
     __shared__ int s_act[D];
     __shared__ long long s_off[MAX_REAL_ROWS];
+    __shared__ int s_any;
     if (threadIdx.x < nl) {
         const Scalars& s = a.sc[l0 + threadIdx.x];
         s_act[threadIdx.x] = (!a.check_status) || (s.status == ST_ACTIVE);
         s_alpha[threadIdx.x] = alpha_of(s, T());
     }
+    if (threadIdx.x == 0) {
+        int any = 0;   // see k_row_fwd: a launch with no ACTIVE system does nothing
+        for (int l = 0; l < a.L; ++l) any |= (!a.check_status) || (a.sc[l].status == ST_ACTIVE);
+        s_any = any;
+    }
     __syncthreads();
+    if (!s_any) return;
     row_offsets<D>(s_off, nreal, nl, l0, row0, nrow, s_act, rows, H);
     __syncthreads();
 
@@ -621,21 +651,12 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
 
     fft_any<T, NN, true>(buf, ncplx, Nl, pl, tw, tws);
 
-    const long long kb = row0 * Nl;
-    T* Xb[D][D];
-    T* Rb[D][D];
-    T* Pb[D][D];
-    T* Ob[D][D];
-#pragma unroll
-    for (int li = 0; li < D; ++li)
-#pragma unroll
-        for (int al = 0; al < D; ++al) {
-            const long long off = ((long long)(l0 + li) * D + al) * M + kb;
-            Xb[li][al] = a.x ? static_cast<T*>(a.x) + off : nullptr;
-            Rb[li][al] = a.r ? static_cast<T*>(a.r) + off : nullptr;
-            Pb[li][al] = a.p ? static_cast<T*>(a.p) + off : nullptr;
-            Ob[li][al] = a.out ? static_cast<T*>(a.out) + off : nullptr;
-        }
+    const long long b0 = (long long)l0 * D * M + row0 * Nl;
+    T* const Xt = a.x ? static_cast<T*>(a.x) + b0 : nullptr;
+    T* const Rt = a.r ? static_cast<T*>(a.r) + b0 : nullptr;
+    T* const Pt = a.p ? static_cast<T*>(a.p) + b0 : nullptr;
+    T* const Ot = a.out ? static_cast<T*>(a.out) + b0 : nullptr;
+    const unsigned Mu = (unsigned)M;
     T alpha_t[D];
     bool act[D];
 #pragma unroll
@@ -644,7 +665,7 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
         alpha_t[li] = li < nl ? s_alpha[li] : T(0);
     }
     T tacc[MAXL] = {T(0), T(0), T(0)};
-    constexpr int UNR = 2;
+    constexpr int UNR = D == 2 ? 2 : 1;
     const int total = nrow * Nl;
     const bool cgm = a.mode == INV_CG;
     for (int e0 = threadIdx.x; e0 < total; e0 += UNR * blockDim.x) {
@@ -660,9 +681,10 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
                     const bool on = valid && act[li];
 #pragma unroll
                     for (int al = 0; al < D; ++al) {
-                        xv[u][li][al] = on ? Xb[li][al][e] : T(0);
-                        rv0[u][li][al] = on ? Rb[li][al][e] : T(0);
-                        pv[u][li][al] = on ? Pb[li][al][e] : T(0);
+                        const size_t o = (size_t)(li * D + al) * Mu + e;
+                        xv[u][li][al] = on ? Xt[o] : T(0);
+                        rv0[u][li][al] = on ? Rt[o] : T(0);
+                        pv[u][li][al] = on ? Pt[o] : T(0);
                     }
                 }
             }
@@ -682,23 +704,24 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
                     const int rr = (rowi * nl + li) * D + al;
                     const C z = buf[(rr >> 1) * Nl + i];
                     const T q = (rr & 1) ? z.y : z.x;
+                    const size_t o = (size_t)(li * D + al) * Mu + e;
                     if (cgm) {
-                        Xb[li][al][e] = xv[u][li][al] + alpha_t[li] * pv[u][li][al];
+                        Xt[o] = xv[u][li][al] + alpha_t[li] * pv[u][li][al];
                         const T rnew = rv0[u][li][al] - alpha_t[li] * q;
-                        Rb[li][al][e] = rnew;
+                        Rt[o] = rnew;
                         tacc[li] += rnew * rnew;
                     } else if (a.mode == INV_RHS) {
                         const T rnew = -q;
-                        Rb[li][al][e] = rnew;
-                        Pb[li][al][e] = rnew;
-                        Xb[li][al][e] = T(0);
+                        Rt[o] = rnew;
+                        Pt[o] = rnew;
+                        Xt[o] = T(0);
                         tacc[li] += rnew * rnew;
                     } else if (a.mode == INV_RESID) {
                         const T rnew = -q;
-                        Rb[li][al][e] = rnew;
+                        Rt[o] = rnew;
                         tacc[li] += rnew * rnew;
                     } else {
-                        Ob[li][al][e] = q;
+                        Ot[o] = q;
                     }
                 }
             }

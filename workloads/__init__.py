@@ -181,13 +181,27 @@ def spheres_3d(n: int = 135, count: int = 60, r_lo: float = 6.0,
     return ms
 
 
+def _stamp_ellipse(phase: np.ndarray, c0: float, c1: float, a: float, b: float,
+                   th: float, value: int) -> None:
+    """Set the voxels inside a periodic ellipse (centre, semi-axes a >= b, angle)."""
+    n0, n1 = phase.shape
+    R = int(math.ceil(a)) + 1
+    i = np.arange(int(math.floor(c0)) - R, int(math.floor(c0)) + R + 2)
+    j = np.arange(int(math.floor(c1)) - R, int(math.floor(c1)) + R + 2)
+    ii, jj = np.meshgrid(i, j, indexing="ij")
+    d0 = _periodic_delta(ii.astype(np.float64), c0, n0)
+    d1 = _periodic_delta(jj.astype(np.float64), c1, n1)
+    u = math.cos(th) * d0 + math.sin(th) * d1
+    v = -math.sin(th) * d0 + math.cos(th) * d1
+    inside = (u / a) ** 2 + (v / b) ** 2 <= 1.0
+    phase[np.mod(ii[inside], n0), np.mod(jj[inside], n1)] = value
+
+
 def ellipses_2d(n: int, vf_target: float, contrast: float,
                 rng: np.random.Generator, max_inclusions: int = 10000) -> Microstructure:
     """Overlapping random ellipses added until the phase-1 fraction >= vf_target."""
     N = (n, n)
     phase = np.zeros(N, np.uint8)
-    ii, jj = np.meshgrid(np.arange(n, dtype=np.float64),
-                         np.arange(n, dtype=np.float64), indexing="ij")
     k = 0
     while phase.mean() < vf_target and k < max_inclusions:
         k += 1
@@ -195,11 +209,7 @@ def ellipses_2d(n: int, vf_target: float, contrast: float,
         b = a * rng.uniform(0.3, 1.0)
         th = rng.uniform(0, math.pi)
         c0, c1 = rng.uniform(0, n), rng.uniform(0, n)
-        d0 = _periodic_delta(ii, c0, n)
-        d1 = _periodic_delta(jj, c1, n)
-        u = math.cos(th) * d0 + math.sin(th) * d1
-        v = -math.sin(th) * d0 + math.cos(th) * d1
-        phase[(u / a) ** 2 + (v / b) ** 2 <= 1.0] = 1
+        _stamp_ellipse(phase, c0, c1, a, b, th, 1)
     ms = Microstructure(N, phase, isotropic_table([1.0, contrast], 2),
                         name=f"ellipses_{n}x{n}",
                         meta={"contrast": contrast, "vf_target": vf_target})
