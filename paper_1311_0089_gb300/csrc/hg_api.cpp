@@ -282,6 +282,15 @@ void grid_free_work(hg_grid* g) {
     dev_free(c, g->d_A0); g->d_A0 = nullptr;
 }
 
+size_t ctx_reclaim(hg_ctx* ctx, hg_grid* keep) {
+    const size_t before = ctx->used.load();
+    for (hg_grid* g : ctx->grids) {
+        if (g == keep || g->borrowed.load() > 0) continue;
+        if (g->work[0].ready || g->work[1].ready) grid_free_work(g);
+    }
+    return before - ctx->used.load();
+}
+
 int grid_alloc_common(hg_grid* g) {
     if (g->partial) return HG_OK;
     const GridDev& gd = g->gd;
@@ -478,7 +487,7 @@ int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nke
 
 static int map_status(int s) {
     switch (s) {
-        case ST_CONVERGED: case ST_ZERO_RHS: case ST_IDLE: return HG_OK;
+        case ST_CONVERGED: case ST_ZERO_RHS: case ST_IDLE: case ST_STAGNATED: return HG_OK;
         case ST_MAXITER: case ST_ACTIVE: return HG_ERR_NOT_CONVERGED;
         case ST_BREAKDOWN: return HG_ERR_BREAKDOWN;
         default: return HG_ERR_CUDA;
@@ -613,12 +622,19 @@ int job_advance(Job& j, bool* done) {
             if (any_active(h, L) && j.launched <= (long long)mi + 2 * j.chunk)
                 return job_launch_chunk(j, j.cg_prec);
             if (j.phase == Job::PLAIN) return job_finish_enqueue(j);
-            // x64 += x32, then the FP64 residual r = -G A (E + x)
+            // x64 += x32; x64 <- Gamma_N x64 in FP64 (FP32 roundoff leaves a part
+            // of the correction outside E_N, which the residual below cannot
+            // see but A_H would, to first order; Gamma_N is the orthogonal
+            // projection onto E_N, Lemma FD_projection (iii),(v)); then the
+            // FP64 residual r = -G A (E + x)
             HG_CU(launch_outer_update(gd, L, (double*)g->work[0].x, (const float*)g->work[1].x,
                                       g->work[0].sc, g->work[1].sc, j.s));
             g->ctx->launches++;
-            int st = enqueue_matvec(g, 0, L, g->work[0].x, g->d_E, true, nullptr, nullptr, INV_RESID,
+            int st = enqueue_matvec(g, 0, L, g->work[0].x, nullptr, false, nullptr, nullptr, INV_PROJ,
                                     nullptr, 1, j.s);
+            if (st) return st;
+            st = enqueue_matvec(g, 0, L, g->work[0].x, g->d_E, true, nullptr, nullptr, INV_RESID,
+                                nullptr, 1, j.s);
             if (st) return st;
             j.outer++;
             j.phase = Job::RESID;

@@ -211,6 +211,7 @@ int hg_create_grid(hg_ctx* c, int d, const int* N, const double* Y, hg_grid** ou
         return st;
     }
     c->ngrids += 1;
+    c->grids.insert(g);
     g->counted = true;
     *out = g;
     return HG_OK;
@@ -238,7 +239,10 @@ int hg_destroy_grid(hg_grid* g) {
     if (g->ev_tick) cudaEventDestroy(g->ev_tick);
     for (int i = 0; i < 2 * hgrt::MAX_PROF_CHUNK; ++i)
         if (g->prof_ev[i]) cudaEventDestroy(g->prof_ev[i]);
-    if (g->counted) c->ngrids -= 1;
+    if (g->counted) {
+        c->ngrids -= 1;
+        c->grids.erase(g);
+    }
     delete g;
     return HG_OK;
 }
@@ -327,11 +331,16 @@ int hg_set_coeffs_phase(hg_grid* g, const uint8_t* phase, int n_phases, const do
     std::vector<float> tb32(tb.size());
     for (size_t i = 0; i < tb.size(); ++i) tb32[i] = (float)tb[i];
     HG_CU(cudaStreamSynchronize(c->stream));
-    free_coeffs(g);
-    int st;
-    if ((st = dev_alloc(c, (void**)&g->d_phase, (size_t)M))) return st;
-    if ((st = dev_alloc(c, &g->d_table[0], tb.size() * sizeof(double)))) return st;
-    if ((st = dev_alloc(c, &g->d_table[1], tb32.size() * sizeof(float)))) return st;
+    // same shape as the current phase coefficients: overwrite in place (no
+    // cudaFree/cudaMalloc, which would synchronise the device)
+    const bool reuse = g->coeff_mode == 0 && g->n_phases == n_phases && g->d_phase;
+    if (!reuse) {
+        free_coeffs(g);
+        int st;
+        if ((st = dev_alloc(c, (void**)&g->d_phase, (size_t)M))) return st;
+        if ((st = dev_alloc(c, &g->d_table[0], tb.size() * sizeof(double)))) return st;
+        if ((st = dev_alloc(c, &g->d_table[1], tb32.size() * sizeof(float)))) return st;
+    }
     HG_CU(cudaMemcpyAsync(g->d_phase, phase, (size_t)M,
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     HG_CU(cudaMemcpyAsync(g->d_table[0], tb.data(), tb.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));

@@ -18,7 +18,8 @@ enum {
     ST_ZERO_RHS = 2,
     ST_MAXITER = 3,
     ST_BREAKDOWN = 4,
-    ST_IDLE = 5        // not part of this solve (load not requested)
+    ST_IDLE = 5,       // not part of this solve (load not requested)
+    ST_STAGNATED = 6   // inner FP32 solve stopped improving (refinement goes on)
 };
 
 // Per-system CG scalars kept on the device (written by the last CTA of a
@@ -38,6 +39,9 @@ struct Scalars {
     int total_iters; // accumulated over refinement steps
     float alpha_f;   // alpha and beta rounded to FP32 for the FP32 kernels
     float beta_f;
+    double best_rr;  // stagnation test (inner FP32 solves): best (r, r) so far
+    int stall;       // iterations since best_rr last fell by 4x
+    int stall_max;   // > 0: stop (ST_STAGNATED) after this many such iterations
 };
 
 struct GridDev {
@@ -77,7 +81,7 @@ struct RowCfg { int RB; int LB; int threads; int smem; long long nbx; int nby; i
 struct StrCfg { int Cl; int threads; int smem; int ct; };
 
 enum RowFwdMode { FWD_CG = 0, FWD_APPLY = 1 };
-enum RowInvMode { INV_CG = 0, INV_RHS = 1, INV_OUT = 2, INV_RESID = 3 };
+enum RowInvMode { INV_CG = 0, INV_RHS = 1, INV_OUT = 2, INV_RESID = 3, INV_PROJ = 4 };
 enum StrMode { STR_FWD = 0, STR_INV = 1, STR_GAMMA = 2, STR_FWD_SCALE = 3 };
 
 struct RowFwdArgs {

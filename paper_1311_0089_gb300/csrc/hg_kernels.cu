@@ -13,7 +13,7 @@ __global__ void k_init_scalars(Scalars* sc, int L, int s0, int s1, int s2, doubl
     if (l >= L) return;
     Scalars s;
     s.rr = 0; s.pt = 0; s.alpha = 0; s.beta = 0; s.bnorm = 0; s.aen = 0; s.relres = 1.0;
-    s.alpha_f = 0.f; s.beta_f = 0.f;
+    s.alpha_f = 0.f; s.beta_f = 0.f; s.best_rr = 0.0; s.stall = 0; s.stall_max = 0;
     s.tol = tol; s.iters = 0; s.max_iter = max_iter; s.total_iters = 0;
     s.status = (l == 0) ? s0 : (l == 1) ? s1 : s2;
     sc[l] = s;
@@ -50,8 +50,16 @@ __global__ void __launch_bounds__(256) k_inner_init(GridDev g, int L, const doub
     if (threadIdx.x == 0) {
         for (int l = 0; l < L; ++l) {
             Scalars s;
+            // inner target: reduce the current FP64 residual just enough to reach
+            // the outer tolerance (half of it), never looser than 0.5 nor tighter
+            // than inner_tol
+            const double need = 0.5 * outer[l].tol / fmax(outer[l].relres, 1e-300);
+            const double itol = fmin(0.5, fmax(inner_tol, need));
             s.rr = tot[l] * g.invM; s.pt = 0; s.alpha = 0; s.beta = 0; s.alpha_f = 0.f; s.beta_f = 0.f;
-            s.bnorm = sqrt(s.rr); s.aen = 0; s.relres = 1.0; s.tol = inner_tol;
+            // an inner FP32 solve that stops improving ends; the FP64
+            // refinement decides whether another inner solve is needed
+            s.best_rr = s.rr; s.stall = 0; s.stall_max = 64;
+            s.bnorm = sqrt(s.rr); s.aen = 0; s.relres = 1.0; s.tol = itol;
             s.iters = 0; s.max_iter = inner_max; s.total_iters = 0;
             s.status = act[l] ? (s.rr > 0.0 ? ST_ACTIVE : ST_CONVERGED) : ST_IDLE;
             inner[l] = s;

@@ -720,6 +720,8 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
                         const T rnew = -q;
                         Rt[o] = rnew;
                         tacc[li] += rnew * rnew;
+                    } else if (a.mode == INV_PROJ) {
+                        Xt[o] = q;             // x <- Gamma x
                     } else {
                         Ot[o] = q;
                     }
@@ -728,7 +730,7 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
         }
     }
 
-    if (a.mode == INV_OUT) return;
+    if (a.mode == INV_OUT || a.mode == INV_PROJ) return;
     double acc[MAXL];
     block_sum_t<T, MAXL>(tacc, acc);
     const long long nbx = gridDim.x;
@@ -752,6 +754,14 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
                 if (!isfinite(rr)) s.status = ST_BREAKDOWN;
                 else if (rel <= s.tol) s.status = ST_CONVERGED;
                 else if (s.iters >= s.max_iter) s.status = ST_MAXITER;
+                if (s.stall_max > 0 && s.status == ST_ACTIVE) {
+                    if (rr < 0.25 * s.best_rr) {
+                        s.best_rr = rr;
+                        s.stall = 0;
+                    } else if (++s.stall >= s.stall_max) {
+                        s.status = ST_STAGNATED;
+                    }
+                }
                 s.beta = rr / s.rr;
                 s.beta_f = (float)s.beta;
                 s.rr = rr;

@@ -11,6 +11,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <unordered_map>
 
@@ -28,6 +29,7 @@ struct hg_ctx {
     std::map<void*, size_t> alloc_sizes;
     std::atomic<long long> launches{0};
     std::atomic<int> ngrids{0};         // live grids (hg_destroy refuses while > 0)
+    std::set<hg_grid*> grids;           // live grids (guarded by mu)
     int max_smem = 48 * 1024;
     std::recursive_mutex mu;            // serialises device work issued by callers
     hgrt::Scheduler* sched = nullptr;   // request scheduler (hg_submit / hg_poll)
@@ -131,6 +133,9 @@ struct Job {
 int job_begin(Job& j);
 int job_advance(Job& j, bool* done);
 void grid_free_work(hg_grid* g);
+// Frees the solver state of every grid of ctx that no ticket holds (except
+// `keep`); returns the bytes released.  Caller holds ctx->mu.
+size_t ctx_reclaim(hg_ctx* ctx, hg_grid* keep);
 int solve_impl(hg_grid* g, const hg_solve_opts* o, double* AH_out, hg_result* info);
 
 // scheduler (hg_sched.cpp)

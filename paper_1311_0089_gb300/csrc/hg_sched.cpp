@@ -60,12 +60,10 @@ struct Scheduler {
 };
 
 static void complete(Scheduler* S, Ticket* t, int status) {
-    // the ticket's work is finished or abandoned: make sure nothing is in flight
+    // the ticket's work is finished or abandoned: make sure nothing is in flight.
+    // Its device buffers stay allocated (reused by the next request on this
+    // grid; reclaimed by admission when the budget is short).
     if (t->job.s) cudaStreamSynchronize(t->job.s);
-    {
-        std::lock_guard<std::recursive_mutex> lk(S->ctx->mu);
-        grid_free_work(t->g);
-    }
     std::lock_guard<std::mutex> lk(S->m);
     t->status = status;
     t->res.status = status;
@@ -104,6 +102,12 @@ static void worker(Scheduler* S) {
                 t->job.ev1 = t->g->ev1;
                 t->job.tick = t->g->ev_tick;
                 st = job_begin(t->job);
+                if (st == HG_ERR_NO_MEMORY) {
+                    // over the budget: release idle grids' solver state and retry once
+                    cudaStreamSynchronize(t->job.s);
+                    grid_free_work(t->g);
+                    if (ctx_reclaim(S->ctx, t->g) > 0) st = job_begin(t->job);
+                }
             }
             if (st == HG_ERR_NO_MEMORY) {
                 bool none_running;

@@ -262,3 +262,52 @@ def test_time_pass_in_graph(hg, ctx):
     with pytest.raises(hg.HGError):
         g.solve(hg.default_opts(time_pass=g.num_passes()))
     g.close()
+
+
+def test_scheduler_admission_by_memory_budget(hg):
+    # A context whose budget holds the solver state of one 135x135 grid at a
+    # time: the second request waits for the first, then reuses its memory.
+    ms = [W.circles_2d(n=135, count=6, r_lo=5, r_hi=12, contrast=c, seed=int(c)) for c in (20.0, 40.0)]
+    probe = hg.Context(0, use_torch_stream=False)
+    g = probe.grid(ms[0].N)
+    g.set_coeffs_phase(ms[0].phase, ms[0].table)
+    want = [None, None]
+    for k in range(2):
+        g.set_coeffs_phase(ms[k].phase, ms[k].table)
+        want[k] = g.solve(hg.default_opts(tol=1e-9, prec=hg.HG_MIXED))["AH"]
+    g.close()
+    probe.close()
+    budget = 7 << 20           # one grid's FP64 + FP32 state at 135^2 is ~4.7 MiB
+    ctx = hg.Context(0, mem_budget=budget, use_torch_stream=False)
+    gs = []
+    for m in ms:
+        gg = ctx.grid(m.N)
+        gg.set_coeffs_phase(m.phase, m.table)
+        gs.append(gg)
+    ts = [ctx.submit(gg, hg.default_opts(tol=1e-9, prec=hg.HG_MIXED)) for gg in gs]
+    out = [ctx.poll(t, timeout_us=-1) for t in ts]
+    for k in range(2):
+        assert out[k]["status"] == 0
+        np.testing.assert_allclose(out[k]["AH"], want[k], rtol=1e-12)
+    big = ctx.grid((405, 405))
+    big.set_coeffs_phase(np.zeros((405, 405), np.uint8), np.eye(2)[None])
+    t = ctx.submit(big, hg.default_opts())
+    r = ctx.poll(t, timeout_us=-1)
+    assert r["status"] == -4            # can never fit the budget
+    ctx.close()
+
+
+def test_cancel_queued_ticket(hg):
+    ctx = hg.Context(0, use_torch_stream=False)
+    ms = W.circles_2d(n=81, count=4, r_lo=4, r_hi=9, contrast=30.0, seed=1)
+    gs = []
+    for _ in range(3):
+        g = ctx.grid(ms.N)
+        g.set_coeffs_phase(ms.phase, ms.table)
+        gs.append(g)
+    ts = [ctx.submit(g, hg.default_opts(tol=1e-10)) for g in gs]
+    ctx.cancel(ts[2])
+    outs = [ctx.poll(t, timeout_us=-1) for t in ts]
+    assert outs[0]["status"] == 0 and outs[1]["status"] == 0
+    assert outs[2]["status"] in (0, -9)
+    ctx.close()
