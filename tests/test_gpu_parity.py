@@ -311,3 +311,67 @@ def test_cancel_queued_ticket(hg):
     assert outs[0]["status"] == 0 and outs[1]["status"] == 0
     assert outs[2]["status"] in (0, -9)
     ctx.close()
+
+
+# ------------------------------------------------------------ full-size workloads
+def test_full_size_729_against_oracle_golden(hg, ctx):
+    """The 729x729 workload in the configuration bench.py times (tol 1e-5,
+    mixed and FP64) against the oracle's A_H at tol 1e-12."""
+    gold = json.load(open(os.path.join(HERE, "golden", "circles_729_AH.json")))
+    ref = np.array(gold["AH"])
+    ms = W.circles_2d()
+    g = ctx.grid(ms.N)
+    g.set_coeffs_phase(ms.phase, ms.table)
+    mixed = g.solve(hg.default_opts(tol=1e-5, prec=hg.HG_MIXED, inner_tol=5e-6))
+    fp64 = g.solve(hg.default_opts(tol=1e-5, prec=hg.HG_FP64))
+    tight = g.solve(hg.default_opts(tol=1e-12, prec=hg.HG_FP64))
+    assert rel_max(mixed["AH"], ref) < 1e-6
+    assert rel_max(fp64["AH"], ref) < 1e-6
+    assert rel_max(tight["AH"], ref) < 1e-8
+    assert abs(tight["iters"][0] - gold["iters"][0]) <= 2
+    g.close()
+
+
+def test_full_size_135_cubed_sampled_and_properties(hg, ctx):
+    """The 135^3 workload: one operator application against the oracle, and
+    A_H symmetry, Voigt/Reuss bounds and energy = flux at full size."""
+    ms = W.spheres_3d()
+    N, d = ms.N, 3
+    g = ctx.grid(N)
+    g.set_coeffs_phase(ms.phase, ms.table)
+    A = ms.full_field()
+    u = np.random.default_rng(5).standard_normal((d,) + N)
+    np.testing.assert_allclose(g.apply(u, with_A=True), O.apply_K(A, u, N), atol=1e-9)
+    res = g.solve(hg.default_opts(tol=1e-6, prec=hg.HG_MIXED, inner_tol=5e-7))
+    assert res["status"] == 0
+    AH = res["AH"]
+    np.testing.assert_allclose(AH, AH.T, atol=1e-9 * np.max(np.abs(AH)))
+    np.testing.assert_allclose(res["AH_flux"], AH, rtol=1e-4, atol=1e-6 * np.max(np.abs(AH)))
+    f = ms.phase.mean()
+    voigt = (1 - f) * ms.table[0] + f * ms.table[1]
+    reuss = np.linalg.inv((1 - f) * np.linalg.inv(ms.table[0]) + f * np.linalg.inv(ms.table[1]))
+    assert np.min(np.linalg.eigvalsh(voigt - AH)) > -1e-8 * np.max(np.abs(AH))
+    assert np.min(np.linalg.eigvalsh(AH - reuss)) > -1e-8 * np.max(np.abs(AH))
+    g.close()
+
+
+def test_mixed_high_contrast_accuracy(hg, ctx):
+    """Contrast ~5e3: the mixed path (FP32 CG, FP64 refinement with the
+    projection onto E_N) meets 1e-6 in A_H at tol 1e-5."""
+    probs = W.batch_2d(count=40)
+    ms = max((p for p in probs if p.N[0] <= 135), key=lambda p: p.meta["contrast"])
+    g = ctx.grid(ms.N)
+    g.set_coeffs_phase(ms.phase, ms.table)
+    ref = g.solve(hg.default_opts(tol=1e-11))["AH"]
+    mixed = g.solve(hg.default_opts(tol=1e-5, prec=hg.HG_MIXED, inner_tol=5e-6))
+    assert ms.meta["contrast"] > 1e3
+    assert rel_max(mixed["AH"], ref) < 1e-6
+    g.close()
+    # and against the oracle itself on one small batched problem
+    small = next(p for p in probs if p.N[0] == 45)
+    g = ctx.grid(small.N)
+    g.set_coeffs_phase(small.phase, small.table)
+    mixed = g.solve(hg.default_opts(tol=1e-8, prec=hg.HG_MIXED))
+    oref = O.solve_AH(small.full_field(), small.N, tol=1e-12)["AH"]
+    assert rel_max(mixed["AH"], oref) < 1e-6
+    g.close()
