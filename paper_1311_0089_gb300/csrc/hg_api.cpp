@@ -420,7 +420,7 @@ int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_p
 
 // q = G A (E + u) followed by the epilogue `inv_mode` (INV_RHS / INV_RESID /
 // INV_OUT); u may be null.
-int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, const double* E, bool withA,
+int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, bool withA,
                    const double* A0dev, const double* A0host, int inv_mode, void* out,
                    int check_status, cudaStream_t s) {
     const GridDev& gd = g->gd;
@@ -429,7 +429,11 @@ int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, const double* E, 
     RowFwdArgs fa;
     memset(&fa, 0, sizeof(fa));
     fa.mode = FWD_APPLY; fa.L = L; fa.co = coeffs_for(g, prec, withA);
-    fa.u = u; fa.E = E; fa.A0 = A0dev; fa.S = w.S; fa.sc = w.sc;
+    fa.u = u; fa.A0 = A0dev; fa.S = w.S; fa.sc = w.sc;
+    if (unit_loads) {          // E_l = e_l (Eq. grad_field_split with E = e_j)
+        fa.has_E = 1;
+        for (int l = 0; l < L; ++l) { fa.Ed[l * gd.d + l] = 1.0; fa.Ef[l * gd.d + l] = 1.0f; }
+    }
     fa.partial = g->partial; fa.counter = g->counters + 2; fa.check_status = check_status;
     HG_CU(launch_row_fwd(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], fa, s));
     g->ctx->launches++;
@@ -598,7 +602,7 @@ int job_begin(Job& j) {
     HG_CU(launch_init_scalars(g->work[0].sc, L, init_st, j.o.tol, j.prec ? j.o.max_outer : j.o.max_iter, j.s));
     ctx->launches++;
     // b = -G A E  ->  r = p = b, x = 0  (Eq. final_system), in FP64
-    if ((st = enqueue_matvec(g, 0, L, nullptr, g->d_E, true, nullptr, nullptr, INV_RHS, nullptr, 1, j.s))) return st;
+    if ((st = enqueue_matvec(g, 0, L, nullptr, true, true, nullptr, nullptr, INV_RHS, nullptr, 1, j.s))) return st;
     if (j.prec == 0) {
         j.phase = Job::PLAIN;
         return job_launch_chunk(j, 0);
@@ -630,10 +634,10 @@ int job_advance(Job& j, bool* done) {
             HG_CU(launch_outer_update(gd, L, (double*)g->work[0].x, (const float*)g->work[1].x,
                                       g->work[0].sc, g->work[1].sc, j.s));
             g->ctx->launches++;
-            int st = enqueue_matvec(g, 0, L, g->work[0].x, nullptr, false, nullptr, nullptr, INV_PROJ,
+            int st = enqueue_matvec(g, 0, L, g->work[0].x, false, false, nullptr, nullptr, INV_PROJ,
                                     nullptr, 1, j.s);
             if (st) return st;
-            st = enqueue_matvec(g, 0, L, g->work[0].x, g->d_E, true, nullptr, nullptr, INV_RESID,
+            st = enqueue_matvec(g, 0, L, g->work[0].x, true, true, nullptr, nullptr, INV_RESID,
                                 nullptr, 1, j.s);
             if (st) return st;
             j.outer++;

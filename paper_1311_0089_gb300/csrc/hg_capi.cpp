@@ -406,7 +406,7 @@ int hg_apply(hg_grid* g, const double* u, double* out, int with_A, const double*
         HG_CU(cudaMemcpyAsync(g->d_A0, A0, sizeof(double) * g->gd.d * g->gd.d, cudaMemcpyHostToDevice, s));
         A0dev = g->d_A0;
     }
-    if ((st = enqueue_matvec(g, pr, 1, g->work[pr].x, nullptr, with_A != 0, A0dev, A0, INV_OUT,
+    if ((st = enqueue_matvec(g, pr, 1, g->work[pr].x, false, with_A != 0, A0dev, A0, INV_OUT,
                              g->work[pr].r, 0, s))) return st;
     if (pr == 1) { HG_CU(launch_convert(g->work[1].r, 1, g->work[0].r, 0, (long long)n, s)); c->launches++; }
     HG_CU(cudaMemcpyAsync(out, g->work[0].r, n * sizeof(double),

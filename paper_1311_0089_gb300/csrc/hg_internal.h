@@ -91,7 +91,9 @@ struct RowFwdArgs {
     void* p;                    // FWD_CG: in/out search direction [L][d][M]
     const void* r;              // FWD_CG: residual
     const void* u;              // FWD_APPLY: input field [L][d][M] or null (= 0)
-    const double* E;            // FWD_APPLY: loads [L][d] or null (= 0)
+    int has_E;                  // FWD_APPLY: add the loads E (by value, both precisions)
+    double Ed[MAXL * MAXD];     //   [L][d]
+    float Ef[MAXL * MAXD];
     const double* A0;           // FWD_APPLY: d x d reference medium applied after A, or null
     void* S;                    // out: half spectra [L][d][rows][H]
     Scalars* sc;                // per system

@@ -65,28 +65,54 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     __syncthreads();
 }
 
-// Block sum of per-thread partials held in T: warp sums in T (32 terms), FP64
-// across the warps of the block (and, through publish/final_sums, across the
-// grid).  Result valid in thread 0.
+// Block sum of per-thread partials held in T: warp sums in T (32 terms), then
+// the warp sums of the block accumulated exactly as an unevaluated pair
+// hi + lo (Knuth's TwoSum, error-free in T), and FP64 across the CTAs of the
+// grid (final_sums).  The pair is packed into the CTA's FP64 slot, so an
+// FP32 pass issues no FP64 instruction outside its last CTA.  Valid in thread 0.
+__device__ __forceinline__ double pack_pair(float hi, float lo) {
+    return __longlong_as_double(((long long)__float_as_int(lo) << 32) | (unsigned)__float_as_int(hi));
+}
+__device__ __forceinline__ double unpack_pair(double v) {
+    const long long b = __double_as_longlong(v);
+    return (double)__int_as_float((int)(b & 0xffffffffll)) + (double)__int_as_float((int)(b >> 32));
+}
+template <typename T> struct SlotCodec;
+template <> struct SlotCodec<float> {
+    __device__ __forceinline__ static double pack(float hi, float lo) { return pack_pair(hi, lo); }
+    __device__ __forceinline__ static double unpack(double v) { return unpack_pair(v); }
+};
+template <> struct SlotCodec<double> {
+    __device__ __forceinline__ static double pack(double hi, double lo) { return hi + lo; }
+    __device__ __forceinline__ static double unpack(double v) { return v; }
+};
+
 template <typename T, int NV>
 __device__ __forceinline__ void block_sum_t(const T (&v)[NV], double (&out)[NV]) {
-    __shared__ double red[NV][32];
+    __shared__ T red[NV][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
         T x = v[i];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-        if (lane == 0) red[i][wid] = (double)x;
+        if (lane == 0) red[i][wid] = x;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            double sum = 0.0;
-            for (int w = 0; w < nw; ++w) sum += red[i][w];
-            out[i] = sum;
+            T hi = T(0), lo = T(0);
+            for (int w = 0; w < nw; ++w) {
+                const T b = red[i][w];
+                const T s = hi + b;                 // TwoSum(hi, b)
+                const T bb = s - hi;
+                const T err = (hi - (s - bb)) + (b - bb);
+                hi = s;
+                lo += err;
+            }
+            out[i] = SlotCodec<T>::pack(hi, lo);
         }
     }
     __syncthreads();
@@ -110,7 +136,7 @@ __device__ __forceinline__ bool publish(const double* vals, const int* slots, in
 
 // In the last CTA: sums slot s over `nb` CTAs in a fixed order; result in
 // out[s] (valid in every thread).
-template <int NV>
+template <int NV, typename T = double>
 __device__ __forceinline__ void final_sums(const double* partial, long long stride, long long nb,
                                            int nslots, double (&out)[NV]) {
     __shared__ double res[NV];
@@ -121,7 +147,7 @@ __device__ __forceinline__ void final_sums(const double* partial, long long stri
     for (long long b = threadIdx.x; b < nb; b += blockDim.x) {
 #pragma unroll
         for (int s = 0; s < NV; ++s)
-            if (s < nslots) v[s] += __ldcg(&partial[s * stride + b]);
+            if (s < nslots) v[s] += SlotCodec<T>::unpack(__ldcg(&partial[s * stride + b]));
     }
     block_sum<NV>(v);
     if (threadIdx.x == 0) {
@@ -230,6 +256,9 @@ __device__ __forceinline__ void fft_str(Cx<T>* buf, int Cl, int lgCl, int n, con
     else fft_pencils<T, INV, MAXB>(buf, D * Cl, n, pl, twg);
 }
 
+__device__ __forceinline__ float load_of(const RowFwdArgs& a, int i, float) { return a.Ef[i]; }
+__device__ __forceinline__ double load_of(const RowFwdArgs& a, int i, double) { return a.Ed[i]; }
+
 // CG scalars in the kernel's precision (FP32 copies are written beside the
 // FP64 values by the reducing CTA).
 __device__ __forceinline__ float beta_of(const Scalars& s, float) { return s.beta_f; }
@@ -324,7 +353,8 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
 #pragma unroll
     for (int li = 0; li < D; ++li)
 #pragma unroll
-        for (int al = 0; al < D; ++al) Ev[li][al] = (!cg && a.E && li < nl) ? (T)a.E[(l0 + li) * D + al] : T(0);
+        for (int al = 0; al < D; ++al)
+            Ev[li][al] = (a.has_E && li < nl) ? load_of(a, (l0 + li) * D + al, T()) : T(0);
     const uint8_t* phb = a.co.phase ? a.co.phase + kb : nullptr;
     CoeffsDev co = a.co;     // phase map / packed field shifted to the tile
     co.phase = phb;
@@ -448,7 +478,7 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
     const bool last = publish(acc, slots, nl, a.partial, nbx, blockIdx.x, a.counter, nblocks);
     if (!last) return;
     double tot[MAXL];
-    final_sums<MAXL>(a.partial, nbx, nbx, a.L, tot);
+    final_sums<MAXL, T>(a.partial, nbx, nbx, a.L, tot);
     if (threadIdx.x == 0) {
         for (int l = 0; l < a.L; ++l) {
             Scalars& s = a.sc[l];
@@ -521,15 +551,15 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_strided(GridDev g, AxisP
     } else if (a.mode == STR_GAMMA) {
         // q_hat = xi (xi . t_hat) / (xi . A0 xi) / |N| with t = A0 A u (Eq. Gamma_hat,
         // G = Gamma A0); A0 = I unless has_A0.  Computed in T.
-        const long long i = i0 + lane;
+        const int i = (int)i0 + lane;     // < inner < 2^31
         T xi_rest[D];        // the components of xi fixed by this lane
         xi_rest[0] = T(0);
         if (lane_ok) {
             if (D == 2) {
                 xi_rest[1] = (T)i * inv_y(g, 1, T());
             } else {
-                const int k2 = (int)(i % g.H);
-                const int k1 = (int)(i / g.H);
+                const int k2 = i % g.H;
+                const int k1 = i / g.H;
                 xi_rest[1] = (T)freq_of(k1, g.N[1]) * inv_y(g, 1, T());
                 xi_rest[D - 1] = (T)k2 * inv_y(g, D - 1, T());
             }
@@ -740,7 +770,7 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
     const bool last = publish(acc, slots, nl, a.partial, nbx, blockIdx.x, a.counter, nblocks);
     if (!last) return;
     double tot[MAXL];
-    final_sums<MAXL>(a.partial, nbx, nbx, a.L, tot);
+    final_sums<MAXL, T>(a.partial, nbx, nbx, a.L, tot);
     if (threadIdx.x == 0) {
         for (int l = 0; l < a.L; ++l) {
             Scalars& s = a.sc[l];

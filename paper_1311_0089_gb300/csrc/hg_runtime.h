@@ -108,7 +108,7 @@ int enqueue_forward_strided(hg_grid* g, int prec, int L, int check_status, int g
                             const double* A0, cudaStream_t s);
 int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_pass = -1,
                          cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);
-int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, const double* E, bool withA,
+int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, bool withA,
                    const double* A0dev, const double* A0host, int inv_mode, void* out,
                    int check_status, cudaStream_t s);
 int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nkern, int prof_pass = -1);
