@@ -326,7 +326,7 @@ CoeffsDev coeffs_for(const hg_grid* g, int prec, bool withA) {
 // pass enqueueing (every CG iteration / operator application)
 // ----------------------------------------------------------------------------
 int enqueue_forward_strided(hg_grid* g, int prec, int L, int check_status, int gamma_mode,
-                            const double* A0, cudaStream_t s) {
+                            const double* A0, cudaStream_t s, Scalars* status_sc) {
     // 3D: axis 1 forward, axis 0 (fwd + Gamma + inv | fwd+scale), axis 1 inverse
     const GridDev& gd = g->gd;
     Work& w = g->work[prec];
@@ -335,7 +335,7 @@ int enqueue_forward_strided(hg_grid* g, int prec, int L, int check_status, int g
     memset(&sa, 0, sizeof(sa));
     sa.L = L;
     sa.S = w.S;
-    sa.sc = w.sc;
+    sa.sc = status_sc ? status_sc : w.sc;
     sa.check_status = check_status;
     if (A0) {
         sa.has_A0 = 1;
@@ -422,14 +422,15 @@ int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_p
 // INV_OUT); u may be null.
 int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, bool withA,
                    const double* A0dev, const double* A0host, int inv_mode, void* out,
-                   int check_status, cudaStream_t s) {
+                   int check_status, cudaStream_t s, Scalars* status_sc) {
     const GridDev& gd = g->gd;
     Work& w = g->work[prec];
+    Scalars* sc = status_sc ? status_sc : w.sc;
     const int last = gd.d - 1;
     RowFwdArgs fa;
     memset(&fa, 0, sizeof(fa));
     fa.mode = FWD_APPLY; fa.L = L; fa.co = coeffs_for(g, prec, withA);
-    fa.u = u; fa.A0 = A0dev; fa.S = w.S; fa.sc = w.sc;
+    fa.u = u; fa.A0 = A0dev; fa.S = w.S; fa.sc = sc;
     if (unit_loads) {          // E_l = e_l (Eq. grad_field_split with E = e_j)
         fa.has_E = 1;
         for (int l = 0; l < L; ++l) { fa.Ed[l * gd.d + l] = 1.0; fa.Ef[l * gd.d + l] = 1.0f; }
@@ -437,12 +438,12 @@ int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, 
     fa.partial = g->partial; fa.counter = g->counters + 2; fa.check_status = check_status;
     HG_CU(launch_row_fwd(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], fa, s));
     g->ctx->launches++;
-    int st = enqueue_forward_strided(g, prec, L, check_status, STR_GAMMA, A0host, s);
+    int st = enqueue_forward_strided(g, prec, L, check_status, STR_GAMMA, A0host, s, sc);
     if (st) return st;
     RowInvArgs ia;
     memset(&ia, 0, sizeof(ia));
     ia.mode = inv_mode; ia.L = L; ia.S = w.S; ia.x = w.x; ia.r = w.r; ia.p = w.p; ia.out = out;
-    ia.sc = w.sc; ia.partial = g->partial; ia.counter = g->counters + 3; ia.check_status = check_status;
+    ia.sc = sc; ia.partial = g->partial; ia.counter = g->counters + 3; ia.check_status = check_status;
     HG_CU(launch_row_inv(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], ia, s));
     g->ctx->launches++;
     return HG_OK;
@@ -626,17 +627,25 @@ int job_advance(Job& j, bool* done) {
             if (any_active(h, L) && j.launched <= (long long)mi + 2 * j.chunk)
                 return job_launch_chunk(j, j.cg_prec);
             if (j.phase == Job::PLAIN) return job_finish_enqueue(j);
-            // x64 += x32; x64 <- Gamma_N x64 in FP64 (FP32 roundoff leaves a part
-            // of the correction outside E_N, which the residual below cannot
-            // see but A_H would, to first order; Gamma_N is the orthogonal
-            // projection onto E_N, Lemma FD_projection (iii),(v)); then the
-            // FP64 residual r = -G A (E + x)
+            // FP32 roundoff in q = G A p (relative to |A p|, up to rho |p|)
+            // leaves a part of the FP32 correction delta outside E_N, which the
+            // FP64 residual cannot see but A_H would, to first order.  Gamma_N
+            // is the orthogonal projection onto E_N (Lemma FD_projection
+            // (iii),(v)): delta <- Gamma_N delta in FP32 (error eps32 |delta|,
+            // no contrast factor), x64 += delta, and for tolerances below 1e-8
+            // also x64 <- Gamma_N x64 in FP64.  Then the FP64 residual
+            // r = -G A (E + x).
+            int st = enqueue_matvec(g, 1, L, g->work[1].x, false, false, nullptr, nullptr, INV_PROJ,
+                                    nullptr, 1, j.s, g->work[0].sc);
+            if (st) return st;
             HG_CU(launch_outer_update(gd, L, (double*)g->work[0].x, (const float*)g->work[1].x,
                                       g->work[0].sc, g->work[1].sc, j.s));
             g->ctx->launches++;
-            int st = enqueue_matvec(g, 0, L, g->work[0].x, false, false, nullptr, nullptr, INV_PROJ,
+            if (j.o.tol < 1e-8) {
+                st = enqueue_matvec(g, 0, L, g->work[0].x, false, false, nullptr, nullptr, INV_PROJ,
                                     nullptr, 1, j.s);
-            if (st) return st;
+                if (st) return st;
+            }
             st = enqueue_matvec(g, 0, L, g->work[0].x, true, true, nullptr, nullptr, INV_RESID,
                                 nullptr, 1, j.s);
             if (st) return st;

@@ -105,12 +105,12 @@ int grid_alloc_work(hg_grid* g, int prec);
 int grid_alloc_common(hg_grid* g);
 hgk::CoeffsDev coeffs_for(const hg_grid* g, int prec, bool withA);
 int enqueue_forward_strided(hg_grid* g, int prec, int L, int check_status, int gamma_mode,
-                            const double* A0, cudaStream_t s);
+                            const double* A0, cudaStream_t s, hgk::Scalars* status_sc = nullptr);
 int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_pass = -1,
                          cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);
 int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, bool withA,
                    const double* A0dev, const double* A0host, int inv_mode, void* out,
-                   int check_status, cudaStream_t s);
+                   int check_status, cudaStream_t s, hgk::Scalars* status_sc = nullptr);
 int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nkern, int prof_pass = -1);
 
 // One solve as a resumable state machine: job_begin enqueues the first
