@@ -333,6 +333,7 @@ int enqueue_forward_strided(hg_grid* g, int prec, int L, int check_status, int g
     const int d = gd.d;
     StrArgs sa;
     memset(&sa, 0, sizeof(sa));
+    sa.early_stage = 1;
     sa.L = L;
     sa.S = w.S;
     sa.sc = status_sc ? status_sc : w.sc;
@@ -374,6 +375,7 @@ int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_p
     };
     RowFwdArgs fa;
     memset(&fa, 0, sizeof(fa));
+    fa.early_stage = 1;
     fa.mode = FWD_CG; fa.L = L; fa.co = coeffs_for(g, prec, true);
     fa.p = w.p; fa.r = w.r; fa.S = w.S; fa.sc = w.sc;
     fa.partial = g->partial; fa.counter = g->counters + 0; fa.check_status = 1;
@@ -384,6 +386,7 @@ int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_p
     ++pass;
     StrArgs sa;
     memset(&sa, 0, sizeof(sa));
+    sa.early_stage = 1;
     sa.L = L; sa.S = w.S; sa.sc = w.sc; sa.check_status = 1;
     if (d == 3) {
         sa.mode = STR_FWD; sa.axis = 1; sa.outer = gd.N[0]; sa.n = gd.N[1]; sa.inner = gd.H;
@@ -409,6 +412,7 @@ int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_p
     }
     RowInvArgs ia;
     memset(&ia, 0, sizeof(ia));
+    ia.early_stage = 1;
     ia.mode = INV_CG; ia.L = L; ia.S = w.S; ia.x = w.x; ia.r = w.r; ia.p = w.p;
     ia.sc = w.sc; ia.partial = g->partial; ia.counter = g->counters + 1; ia.check_status = 1;
     HG_CU(mark(true));
@@ -429,6 +433,7 @@ int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, 
     const int last = gd.d - 1;
     RowFwdArgs fa;
     memset(&fa, 0, sizeof(fa));
+    fa.early_stage = 1;
     fa.mode = FWD_APPLY; fa.L = L; fa.co = coeffs_for(g, prec, withA);
     fa.u = u; fa.A0 = A0dev; fa.S = w.S; fa.sc = sc;
     if (unit_loads) {          // E_l = e_l (Eq. grad_field_split with E = e_j)
@@ -442,6 +447,7 @@ int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, 
     if (st) return st;
     RowInvArgs ia;
     memset(&ia, 0, sizeof(ia));
+    ia.early_stage = 1;
     ia.mode = inv_mode; ia.L = L; ia.S = w.S; ia.x = w.x; ia.r = w.r; ia.p = w.p; ia.out = out;
     ia.sc = sc; ia.partial = g->partial; ia.counter = g->counters + 3; ia.check_status = check_status;
     HG_CU(launch_row_inv(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], ia, s));

@@ -435,6 +435,7 @@ int hg_spectrum(hg_grid* g, const double* u, double* S_out, int prec, int on_dev
     Work& w = g->work[pr];
     RowFwdArgs fa;
     memset(&fa, 0, sizeof(fa));
+    fa.early_stage = 1;
     fa.mode = FWD_APPLY; fa.L = 1; fa.co = coeffs_for(g, pr, false);
     fa.u = w.x; fa.S = w.S; fa.sc = w.sc; fa.partial = g->partial; fa.counter = g->counters + 2;
     const int last = gd.d - 1;
@@ -483,6 +484,7 @@ int hg_time_pass(hg_grid* g, int prec, int pass, int reps, double* ms_out, char*
         if (pass == 0) {
             RowFwdArgs fa;
             memset(&fa, 0, sizeof(fa));
+            fa.early_stage = 1;
             fa.mode = FWD_CG; fa.L = L; fa.co = coeffs_for(g, pr, true);
             fa.p = w.p; fa.r = w.r; fa.S = w.S; fa.sc = w.sc;
             fa.partial = g->partial; fa.counter = g->counters + 0; fa.check_status = 0;
@@ -491,6 +493,7 @@ int hg_time_pass(hg_grid* g, int prec, int pass, int reps, double* ms_out, char*
         } else if (pass == np - 1) {
             RowInvArgs ia;
             memset(&ia, 0, sizeof(ia));
+            ia.early_stage = 1;
             ia.mode = INV_CG; ia.L = L; ia.S = w.S; ia.x = w.x; ia.r = w.r; ia.p = w.p;
             ia.sc = w.sc; ia.partial = g->partial; ia.counter = g->counters + 1; ia.check_status = 0;
             if (nm) snprintf(nm, 64, "k_row_inv<%s,%d> (C2R DFT + CG update, axis %d)", pr ? "float" : "double", gd.d, last);
@@ -498,6 +501,7 @@ int hg_time_pass(hg_grid* g, int prec, int pass, int reps, double* ms_out, char*
         } else {
             StrArgs sa;
             memset(&sa, 0, sizeof(sa));
+            sa.early_stage = 1;
             sa.L = L; sa.S = w.S; sa.sc = w.sc; sa.check_status = 0;
             int axis;
             if (gd.d == 2 || pass == 2) {

@@ -100,6 +100,8 @@ struct RowFwdArgs {
     double* partial;            // reduction scratch [L][nbx]
     unsigned* counter;          // one counter, reset by the last CTA
     int check_status;           // skip systems that are not ACTIVE
+    int early_stage;            // 1: twiddle/coefficient staging may precede the wait for
+                                //    the previous kernel (tables written only by copies)
 };
 
 struct StrArgs {
@@ -113,6 +115,8 @@ struct StrArgs {
     int check_status;
     int has_A0;
     double A0[9];
+    int early_stage;            // 1: twiddle/coefficient staging may precede the wait for
+                                //    the previous kernel (tables written only by copies)
 };
 
 struct RowInvArgs {
@@ -127,6 +131,8 @@ struct RowInvArgs {
     double* partial;
     unsigned* counter;
     int check_status;
+    int early_stage;            // 1: twiddle/coefficient staging may precede the wait for
+                                //    the previous kernel (tables written only by copies)
 };
 
 // Launchers (prec: 0 = double, 1 = float).  Return cudaGetLastError().

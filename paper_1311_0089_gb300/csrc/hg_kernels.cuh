@@ -248,6 +248,16 @@ __device__ __forceinline__ Cx<T>* stage_twiddles(Cx<T>* smem_after, const AxisPl
 
 template <int NN> struct PassThreads { static constexpr int v = NN > 0 ? CT_THREADS : MAXT; };
 
+// Programmatic dependent launch: the pass kernels are launched so that their
+// CTAs may start while the previous kernel in the stream finishes.  Work that
+// depends on nothing the previous kernel writes (twiddle and coefficient
+// staging) runs first; grid_dep_wait() then blocks until the previous grid has
+// completed and its memory is visible, before any dependent read.
+// grid_dep_launch() lets the next kernel start launching its CTAs.  Both are
+// no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Strided-pass transform: interleaved layout for the compile-time kernels.
 template <typename T, int D, int NN, bool INV>
 __device__ __forceinline__ void fft_str(Cx<T>* buf, int Cl, int lgCl, int n, const AxisPlanH& pl,
@@ -309,18 +319,20 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
     const int nl = min(LB, a.L - l0);
     const int nreal = RB * nl * D;
     const int ncplx = (nreal + 1) >> 1;
+    if (!a.early_stage) grid_dep_wait();
     const C* tws = stage_twiddles<T, NN>(buf + ncplx * Nl, pl, tw);
 
     __shared__ T s_beta[D];
     __shared__ int s_act[D];
     __shared__ T s_tab[SMEM_PHASES * D * D];
     __shared__ long long s_off[MAX_REAL_ROWS];
+    const T* tab = stage_table<T, D>(a.co, s_tab);
+    if (a.early_stage) grid_dep_wait();
     if (threadIdx.x < nl) {
         const Scalars& s = a.sc[l0 + threadIdx.x];
         s_act[threadIdx.x] = (!a.check_status) || (s.status == ST_ACTIVE);
         s_beta[threadIdx.x] = beta_of(s, T());
     }
-    const T* tab = stage_table<T, D>(a.co, s_tab);
     __shared__ int s_any;
     if (threadIdx.x == 0) {
         // a launch in which no system is ACTIVE (the tail of a graph chunk after
@@ -445,6 +457,7 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
     __syncthreads();
 
     fft_any<T, NN, false>(buf, ncplx, Nl, pl, tw, tws);
+    grid_dep_launch();
 
     // Separate the packed pairs: Z = a + i b  ->  A(k) = (Z(k) + conj Z(-k))/2,
     // B(k) = (Z(k) - conj Z(-k)) / 2i, for k = 0..H-1 (Hermitian half).
@@ -514,10 +527,12 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_strided(GridDev g, AxisP
     const long long i0 = (long long)blockIdx.x * Cl;
     const long long o = blockIdx.y;
     const int l = blockIdx.z;
-    if (a.check_status && a.sc[l].status != ST_ACTIVE) return;
     const int n = NN > 0 ? NN : a.n;
     const int inner = (int)a.inner;
+    if (!a.early_stage) grid_dep_wait();
     const C* tws = stage_twiddles<T, NN>(buf + D * Cl * n, pl, tw);
+    if (a.early_stage) grid_dep_wait();
+    if (a.check_status && a.sc[l].status != ST_ACTIVE) return;
 
     // Cl is a power of two dividing blockDim.x: each thread keeps one lane and
     // walks the (component, position) rows with stride blockDim.x / Cl.
@@ -609,6 +624,7 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_strided(GridDev g, AxisP
         fft_str<T, D, NN, true>(buf, Cl, lgCl, n, pl, tw, tws);
     }
 
+    grid_dep_launch();
     if (lane_ok) {
 #pragma unroll 4
         for (int row = threadIdx.x / Cl; row < D * n; row += rstep) {
@@ -638,12 +654,14 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
     const int nl = min(LB, a.L - l0);
     const int nreal = RB * nl * D;
     const int ncplx = (nreal + 1) >> 1;
+    if (!a.early_stage) grid_dep_wait();
     const C* tws = stage_twiddles<T, NN>(buf + ncplx * Nl, pl, tw);
 
     __shared__ T s_alpha[D];
     __shared__ int s_act[D];
     __shared__ long long s_off[MAX_REAL_ROWS];
     __shared__ int s_any;
+    if (a.early_stage) grid_dep_wait();
     if (threadIdx.x < nl) {
         const Scalars& s = a.sc[l0 + threadIdx.x];
         s_act[threadIdx.x] = (!a.check_status) || (s.status == ST_ACTIVE);
@@ -680,6 +698,7 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
     __syncthreads();
 
     fft_any<T, NN, true>(buf, ncplx, Nl, pl, tw, tws);
+    grid_dep_launch();
 
     const long long b0 = (long long)l0 * D * M + row0 * Nl;
     T* const Xt = a.x ? static_cast<T*>(a.x) + b0 : nullptr;
@@ -828,13 +847,31 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
 #define HG_CT_SIZES_2D(X) X(15) X(27) X(45) X(75) X(81) X(135) X(243) X(375) X(729)
 #define HG_CT_SIZES_3D(X) X(15) X(27) X(45) X(81) X(135)
 
+// Launch with programmatic stream serialization (see grid_dep_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, int threads, int smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <typename T>
 cudaError_t launch_row_fwd_t(const GridDev& g, const AxisPlanH& pl, const void* tw, const RowCfg& cfg,
                              const RowFwdArgs& a, cudaStream_t s) {
+    cudaError_t le = cudaSuccess;
     dim3 grid((unsigned)cfg.nbx, (unsigned)((a.L + cfg.LB - 1) / cfg.LB));
     const Cx<T>* twp = (const Cx<T>*)tw;
-#define HG_CASE2(NV) case NV: k_row_fwd<T, 2, NV><<<grid, CT_THREADS, cfg.smem, s>>>(g, pl, twp, a, cfg.RB, cfg.LB); break;
-#define HG_CASE3(NV) case NV: k_row_fwd<T, 3, NV><<<grid, CT_THREADS, cfg.smem, s>>>(g, pl, twp, a, cfg.RB, cfg.LB); break;
+#define HG_CASE2(NV) case NV: le = launch_pdl(k_row_fwd<T, 2, NV>, grid, CT_THREADS, cfg.smem, s, g, pl, twp, a, cfg.RB, cfg.LB); break;
+#define HG_CASE3(NV) case NV: le = launch_pdl(k_row_fwd<T, 3, NV>, grid, CT_THREADS, cfg.smem, s, g, pl, twp, a, cfg.RB, cfg.LB); break;
     if (g.d == 2) {
         if (cfg.ct) {
             switch (g.Nl) {
@@ -842,7 +879,7 @@ cudaError_t launch_row_fwd_t(const GridDev& g, const AxisPlanH& pl, const void* 
                 default: return cudaErrorInvalidConfiguration;   // no compile-time kernel
             }
         } else {
-            k_row_fwd<T, 2, 0><<<grid, cfg.threads, cfg.smem, s>>>(g, pl, twp, a, cfg.RB, cfg.LB);
+            le = launch_pdl(k_row_fwd<T, 2, 0>, grid, cfg.threads, cfg.smem, s, g, pl, twp, a, cfg.RB, cfg.LB);
         }
     } else {
         if (cfg.ct) {
@@ -851,21 +888,23 @@ cudaError_t launch_row_fwd_t(const GridDev& g, const AxisPlanH& pl, const void* 
                 default: return cudaErrorInvalidConfiguration;   // no compile-time kernel
             }
         } else {
-            k_row_fwd<T, 3, 0><<<grid, cfg.threads, cfg.smem, s>>>(g, pl, twp, a, cfg.RB, cfg.LB);
+            le = launch_pdl(k_row_fwd<T, 3, 0>, grid, cfg.threads, cfg.smem, s, g, pl, twp, a, cfg.RB, cfg.LB);
         }
     }
 #undef HG_CASE2
 #undef HG_CASE3
+    if (le != cudaSuccess) return le;
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_row_inv_t(const GridDev& g, const AxisPlanH& pl, const void* tw, const RowCfg& cfg,
                              const RowInvArgs& a, cudaStream_t s) {
+    cudaError_t le = cudaSuccess;
     dim3 grid((unsigned)cfg.nbx, (unsigned)((a.L + cfg.LB - 1) / cfg.LB));
     const Cx<T>* twp = (const Cx<T>*)tw;
-#define HG_CASE2(NV) case NV: k_row_inv<T, 2, NV><<<grid, CT_THREADS, cfg.smem, s>>>(g, pl, twp, a, cfg.RB, cfg.LB); break;
-#define HG_CASE3(NV) case NV: k_row_inv<T, 3, NV><<<grid, CT_THREADS, cfg.smem, s>>>(g, pl, twp, a, cfg.RB, cfg.LB); break;
+#define HG_CASE2(NV) case NV: le = launch_pdl(k_row_inv<T, 2, NV>, grid, CT_THREADS, cfg.smem, s, g, pl, twp, a, cfg.RB, cfg.LB); break;
+#define HG_CASE3(NV) case NV: le = launch_pdl(k_row_inv<T, 3, NV>, grid, CT_THREADS, cfg.smem, s, g, pl, twp, a, cfg.RB, cfg.LB); break;
     if (g.d == 2) {
         if (cfg.ct) {
             switch (g.Nl) {
@@ -873,7 +912,7 @@ cudaError_t launch_row_inv_t(const GridDev& g, const AxisPlanH& pl, const void* 
                 default: return cudaErrorInvalidConfiguration;   // no compile-time kernel
             }
         } else {
-            k_row_inv<T, 2, 0><<<grid, cfg.threads, cfg.smem, s>>>(g, pl, twp, a, cfg.RB, cfg.LB);
+            le = launch_pdl(k_row_inv<T, 2, 0>, grid, cfg.threads, cfg.smem, s, g, pl, twp, a, cfg.RB, cfg.LB);
         }
     } else {
         if (cfg.ct) {
@@ -882,21 +921,23 @@ cudaError_t launch_row_inv_t(const GridDev& g, const AxisPlanH& pl, const void* 
                 default: return cudaErrorInvalidConfiguration;   // no compile-time kernel
             }
         } else {
-            k_row_inv<T, 3, 0><<<grid, cfg.threads, cfg.smem, s>>>(g, pl, twp, a, cfg.RB, cfg.LB);
+            le = launch_pdl(k_row_inv<T, 3, 0>, grid, cfg.threads, cfg.smem, s, g, pl, twp, a, cfg.RB, cfg.LB);
         }
     }
 #undef HG_CASE2
 #undef HG_CASE3
+    if (le != cudaSuccess) return le;
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_strided_t(const GridDev& g, const AxisPlanH& pl, const void* tw, const StrCfg& cfg,
                              const StrArgs& a, cudaStream_t s) {
+    cudaError_t le = cudaSuccess;
     dim3 grid((unsigned)((a.inner + cfg.Cl - 1) / cfg.Cl), (unsigned)a.outer, (unsigned)a.L);
     const Cx<T>* twp = (const Cx<T>*)tw;
-#define HG_CASE2(NV) case NV: k_strided<T, 2, NV><<<grid, CT_THREADS, cfg.smem, s>>>(g, pl, twp, a, cfg.Cl); break;
-#define HG_CASE3(NV) case NV: k_strided<T, 3, NV><<<grid, CT_THREADS, cfg.smem, s>>>(g, pl, twp, a, cfg.Cl); break;
+#define HG_CASE2(NV) case NV: le = launch_pdl(k_strided<T, 2, NV>, grid, CT_THREADS, cfg.smem, s, g, pl, twp, a, cfg.Cl); break;
+#define HG_CASE3(NV) case NV: le = launch_pdl(k_strided<T, 3, NV>, grid, CT_THREADS, cfg.smem, s, g, pl, twp, a, cfg.Cl); break;
     if (g.d == 2) {
         if (cfg.ct) {
             switch (a.n) {
@@ -904,7 +945,7 @@ cudaError_t launch_strided_t(const GridDev& g, const AxisPlanH& pl, const void* 
                 default: return cudaErrorInvalidConfiguration;   // no compile-time kernel
             }
         } else {
-            k_strided<T, 2, 0><<<grid, cfg.threads, cfg.smem, s>>>(g, pl, twp, a, cfg.Cl);
+            le = launch_pdl(k_strided<T, 2, 0>, grid, cfg.threads, cfg.smem, s, g, pl, twp, a, cfg.Cl);
         }
     } else {
         if (cfg.ct) {
@@ -913,11 +954,12 @@ cudaError_t launch_strided_t(const GridDev& g, const AxisPlanH& pl, const void* 
                 default: return cudaErrorInvalidConfiguration;   // no compile-time kernel
             }
         } else {
-            k_strided<T, 3, 0><<<grid, cfg.threads, cfg.smem, s>>>(g, pl, twp, a, cfg.Cl);
+            le = launch_pdl(k_strided<T, 3, 0>, grid, cfg.threads, cfg.smem, s, g, pl, twp, a, cfg.Cl);
         }
     }
 #undef HG_CASE2
 #undef HG_CASE3
+    if (le != cudaSuccess) return le;
     return cudaGetLastError();
 }
 
