@@ -71,17 +71,32 @@ typedef enum {
 } hg_precision;
 
 typedef enum {
+    HG_CG = 0,      /* conjugate gradients on G_N A_N e~ = -G_N A_N E
+                       (Eq. final_system, Sec. 5.3 Lemma)                  */
+    HG_MS = 1       /* Moulinec-Suquet fixed point (Neumann series of the
+                       discrete Lippmann-Schwinger equation, Sec. 5.3
+                       comments): e_i = E - Gamma_N (A_N - lambda I) e_{i-1} */
+} hg_method;
+
+typedef enum {
     HG_COEFF_FULL = 0,    /* |N| x d x d doubles, voxel-major, symmetric      */
     HG_COEFF_PACKED = 1   /* d(d+1)/2 x |N| doubles, component-major; the
                              packed order is (11,22[,33],12[,13,23])          */
 } hg_coeff_layout;
 
 typedef struct {
-    double tol;          /* stop when ||r_i|| / ||b|| <= tol (default 1e-10)     */
-    int max_iter;        /* CG iterations per load (default 10000)              */
+    double tol;          /* HG_CG: stop when ||r_i|| / ||b|| <= tol.  HG_MS: stop
+                            when ||e_i - e_{i-1}|| / ||E|| <= tol (HG_MIXED:
+                            when the next step, ||r|| / lambda with the FP64
+                            residual r, is).  Default 1e-10                    */
+    int max_iter;        /* iterations per load (default 10000)                 */
     int prec;            /* hg_precision (default HG_FP64)                      */
-    double lambda_ref;   /* A0 = lambda I; the system does not depend on it
-                            (Lemma FD_projection (v)); kept for the record     */
+    double lambda_ref;   /* A0 = lambda I.  HG_CG does not depend on it (Lemma
+                            FD_projection (v)).  HG_MS: the reference medium;
+                            <= 0 (default 0) takes (c_A + C_A) / 2, the extreme
+                            eigenvalues of A_N over all voxels; a lambda <=
+                            C_A / 2, for which the series need not converge,
+                            returns HG_ERR_ARG                                 */
     unsigned loads_mask; /* bit j set: solve load E = e_j (default all)        */
     double inner_tol;    /* HG_MIXED: relative tolerance of each FP32 inner solve
                             (default 1e-4)                                      */
@@ -93,6 +108,10 @@ typedef struct {
                             forward pass, last = last-axis inverse pass, as in
                             hg_time_pass); results in hg_result.pass_*.
                             -1 (default): no timing.  check_every <= 64.      */
+    int method;          /* hg_method (default HG_CG).  HG_MS needs the bounds
+                            c_A, C_A: the first HG_MS solve after new
+                            coefficients computes them on the device and
+                            waits for them on the host once                   */
 } hg_solve_opts;
 
 typedef struct {
@@ -100,7 +119,7 @@ typedef struct {
     int d;
     double AH[9];           /* d x d row-major energy form                     */
     double AH_flux[9];      /* d x d mean-flux form <A e_j>_i (check)          */
-    int iters[3];           /* CG iterations per load (HG_MIXED: inner FP32
+    int iters[3];           /* iterations per load (HG_MIXED: inner FP32
                                iterations summed over refinement steps)        */
     int outer[3];           /* HG_MIXED: FP64 residual evaluations per load    */
     double rel_res[3];      /* final ||r|| / ||b|| (FP64 true residual for
@@ -111,6 +130,9 @@ typedef struct {
     double pass_ms_total;   /* time_pass >= 0: summed duration of the timed pass
                                over the iterations in which a system was active */
     int pass_launches;      /* number of such launches                         */
+    double lambda_ref;      /* HG_MS: the lambda used (0 for HG_CG)            */
+    double c_A, C_A;        /* HG_MS: smallest and largest eigenvalue of A_N
+                               over the voxels (0 for HG_CG)                   */
 } hg_result;
 
 /* Fill opts with the defaults listed above. */

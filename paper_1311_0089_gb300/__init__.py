@@ -24,6 +24,8 @@ HG_OK = 0
 HG_PENDING = 1
 HG_FP64 = 0
 HG_MIXED = 1
+HG_CG = 0
+HG_MS = 1
 HG_COEFF_FULL = 0
 HG_COEFF_PACKED = 1
 STATUS = {
@@ -46,7 +48,8 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("prec", ctypes.c_int),
                 ("lambda_ref", ctypes.c_double), ("loads_mask", ctypes.c_uint),
                 ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
-                ("max_outer", ctypes.c_int), ("time_pass", ctypes.c_int)]
+                ("max_outer", ctypes.c_int), ("time_pass", ctypes.c_int),
+                ("method", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -55,7 +58,8 @@ class Result(ctypes.Structure):
                 ("outer", ctypes.c_int * 3), ("rel_res", ctypes.c_double * 3),
                 ("device_ms", ctypes.c_double), ("wall_ms", ctypes.c_double),
                 ("launches", ctypes.c_longlong), ("pass_ms_total", ctypes.c_double),
-                ("pass_launches", ctypes.c_int)]
+                ("pass_launches", ctypes.c_int), ("lambda_ref", ctypes.c_double),
+                ("c_A", ctypes.c_double), ("C_A", ctypes.c_double)]
 
     def to_dict(self) -> dict:
         d = self.d
@@ -71,6 +75,9 @@ class Result(ctypes.Structure):
             "launches": self.launches,
             "pass_ms_total": self.pass_ms_total,
             "pass_launches": self.pass_launches,
+            "lambda_ref": self.lambda_ref,
+            "c_A": self.c_A,
+            "C_A": self.C_A,
         }
 
 

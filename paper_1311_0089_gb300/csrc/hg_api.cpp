@@ -562,7 +562,7 @@ static int job_start_inner(Job& j) {
     const GridDev& gd = g->gd;
     HG_CU(launch_inner_init(gd, gd.d, (const double*)g->work[0].r, (float*)g->work[1].r,
                             (float*)g->work[1].p, (float*)g->work[1].x, g->work[0].sc, g->work[1].sc,
-                            j.o.inner_tol, j.o.max_iter, g->partial, g->counters + 4, j.s));
+                            j.o.inner_tol, j.o.max_iter, j.stall_max, g->partial, g->counters + 4, j.s));
     g->ctx->launches++;
     j.launched = 0;
     j.prof_prev_iters = 0;
@@ -581,6 +581,43 @@ static int job_finish_enqueue(Job& j) {
     HG_CU(cudaMemcpyAsync(g->h_AH, g->d_AH, sizeof(double) * 2 * gd.d * gd.d, cudaMemcpyDeviceToHost, j.s));
     j.phase = Job::FINAL;
     return job_tick_copy(j, 0);
+}
+
+// Moulinec-Suquet (Sec. 5.3 comments): e_i = E - Gamma_N (A_N - lambda I)
+// e_{i-1} with Gamma_N = (1 / lambda) G_N for A0 = lambda I.  Writing e_i = E +
+// x_i with x_i in E_N (G_N E = 0, G_N x = x on E_N, Lemma FD_projection) gives
+// x_i = x_{i-1} + r_{i-1} / lambda, r = -G_N A_N (E + x): the CG iteration with
+// alpha fixed to 1 / lambda and beta = 0.  The series converges for the
+// spectrum [c_A, C_A] of A_N when lambda > C_A / 2, with contraction
+// q = max |1 - c / lambda| over c in {c_A, C_A}, least, (rho - 1) / (rho + 1),
+// at lambda = (c_A + C_A) / 2.
+static int job_method_setup(Job& j) {
+    hg_grid* g = j.g;
+    j.fixed_alpha = 0.0;
+    j.lambda = 0.0;
+    j.stall_max = 64;
+    if (j.o.method != HG_MS) return HG_OK;
+    if (!g->bounds_ok) {
+        double* db = g->d_AH + 24;
+        HG_CU(launch_coeff_bounds(g->gd, coeffs_for(g, 0, true), db, j.s));
+        g->ctx->launches++;
+        double hb[2] = {0.0, 0.0};
+        HG_CU(cudaMemcpyAsync(hb, db, sizeof(hb), cudaMemcpyDeviceToHost, j.s));
+        HG_CU(cudaStreamSynchronize(j.s));
+        g->c_A = hb[0];
+        g->C_A = hb[1];
+        g->bounds_ok = true;
+    }
+    const double lam = j.o.lambda_ref > 0.0 ? j.o.lambda_ref : 0.5 * (g->c_A + g->C_A);
+    if (!(lam > 0.5 * g->C_A) || !(g->c_A > 0.0)) return HG_ERR_ARG;
+    const double q = std::max(std::fabs(1.0 - g->c_A / lam), std::fabs(1.0 - g->C_A / lam));
+    // an inner FP32 solve is stagnating when (r, r) has not dropped 4x in
+    // twice the iterations the contraction needs for that (q^2 per step)
+    const double per4 = q > 0.0 ? std::log(4.0) / (-2.0 * std::log(q)) : 1.0;
+    j.stall_max = (int)std::min(1e9, 64.0 + 2.0 * std::ceil(per4));
+    j.lambda = lam;
+    j.fixed_alpha = 1.0 / lam;
+    return HG_OK;
 }
 
 int job_begin(Job& j) {
@@ -603,10 +640,12 @@ int job_begin(Job& j) {
     if ((st = grid_alloc_common(g))) return st;
     if ((st = grid_alloc_work(g, 0))) return st;
     if (j.prec == 1 && (st = grid_alloc_work(g, 1))) return st;
+    if ((st = job_method_setup(j))) return st;
     HG_CU(cudaEventRecord(j.ev0, j.s));
     int init_st[MAXL];
     for (int l = 0; l < MAXL; ++l) init_st[l] = (l < L && ((j.o.loads_mask >> l) & 1u)) ? ST_ACTIVE : ST_IDLE;
-    HG_CU(launch_init_scalars(g->work[0].sc, L, init_st, j.o.tol, j.prec ? j.o.max_outer : j.o.max_iter, j.s));
+    HG_CU(launch_init_scalars(g->work[0].sc, L, init_st, j.o.tol, j.prec ? j.o.max_outer : j.o.max_iter,
+                              j.fixed_alpha, j.s));
     ctx->launches++;
     // b = -G A E  ->  r = p = b, x = 0  (Eq. final_system), in FP64
     if ((st = enqueue_matvec(g, 0, L, nullptr, true, true, nullptr, nullptr, INV_RHS, nullptr, 1, j.s))) return st;
@@ -688,6 +727,11 @@ int job_advance(Job& j, bool* done) {
             r.launches = g->ctx->launches.load() - j.launches0;
             r.pass_ms_total = j.prof_ms;
             r.pass_launches = j.prof_n;
+            if (j.o.method == HG_MS) {
+                r.lambda_ref = j.lambda;
+                r.c_A = g->c_A;
+                r.C_A = g->C_A;
+            }
             g->last_prec = j.prec;
             j.result = result;
             j.phase = Job::DONE;

@@ -84,12 +84,13 @@ void hg_default_opts(hg_solve_opts* o) {
     o->tol = 1e-10;
     o->max_iter = 10000;
     o->prec = HG_FP64;
-    o->lambda_ref = 1.0;
+    o->lambda_ref = 0.0;
     o->loads_mask = 0x7u;
     o->inner_tol = 1e-4;
     o->check_every = 8;
     o->max_outer = 30;
     o->time_pass = -1;
+    o->method = HG_CG;
 }
 
 const char* hg_strerror(int s) {
@@ -298,6 +299,7 @@ int hg_set_coeffs(hg_grid* g, const double* A, int layout, int on_device) {
     HG_CU(cudaMemcpyAsync(g->d_field[1], pk32.data(), pk32.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     HG_CU(cudaStreamSynchronize(c->stream));
     g->coeff_mode = 1;
+    g->bounds_ok = false;
     return HG_OK;
 }
 
@@ -347,6 +349,7 @@ int hg_set_coeffs_phase(hg_grid* g, const uint8_t* phase, int n_phases, const do
     HG_CU(cudaMemcpyAsync(g->d_table[1], tb32.data(), tb32.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     HG_CU(cudaStreamSynchronize(c->stream));
     g->coeff_mode = 0;
+    g->bounds_ok = false;
     g->n_phases = n_phases;
     return HG_OK;
 }
@@ -356,7 +359,8 @@ int hg_solve_AH(hg_grid* g, const hg_solve_opts* opts, double* AH_out, hg_result
     hg_solve_opts o;
     if (opts) o = *opts; else hg_default_opts(&o);
     if (!(o.tol > 0.0) || o.max_iter < 1 || (o.prec != HG_FP64 && o.prec != HG_MIXED) ||
-        !(o.inner_tol > 0.0) || o.inner_tol >= 1.0)
+        !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 || (o.method != HG_CG && o.method != HG_MS) ||
+        !std::isfinite(o.lambda_ref))
         return HG_ERR_ARG;
     if (o.time_pass >= hg_num_passes(g) || (o.time_pass >= 0 && o.check_every > hgrt::MAX_PROF_CHUNK))
         return HG_ERR_ARG;

@@ -42,6 +42,8 @@ struct Scalars {
     double best_rr;  // stagnation test (inner FP32 solves): best (r, r) so far
     int stall;       // iterations since best_rr last fell by 4x
     int stall_max;   // > 0: stop (ST_STAGNATED) after this many such iterations
+    double fixed_alpha;  // > 0: Moulinec-Suquet step 1/lambda in place of CG's
+                         // alpha, beta = 0, stop on the step just taken
 };
 
 struct GridDev {
@@ -144,13 +146,20 @@ cudaError_t launch_row_inv(int prec, const GridDev& g, const AxisPlanH& pl, cons
                            const RowCfg& cfg, const RowInvArgs& a, cudaStream_t s);
 
 // Small helpers.
+// fixed_alpha > 0 selects the Moulinec-Suquet update with step fixed_alpha.
 cudaError_t launch_init_scalars(Scalars* sc, int L, const int* status_init, double tol,
-                                int max_iter, cudaStream_t s);
+                                int max_iter, double fixed_alpha, cudaStream_t s);
 // Mixed precision: r32 = (float) r64, p32 = r32, x32 = 0, inner scalars from
-// the outer status; reduction of (r32, r32).
+// the outer status (and its fixed step); reduction of (r32, r32).  An inner
+// solve stops (STAGNATED) after stall_max iterations without a 4x drop of (r, r).
 cudaError_t launch_inner_init(const GridDev& g, int L, const double* r64, float* r32, float* p32,
                               float* x32, const Scalars* outer, Scalars* inner, double inner_tol,
-                              int inner_max, double* partial, unsigned* counter, cudaStream_t s);
+                              int inner_max, int stall_max, double* partial, unsigned* counter,
+                              cudaStream_t s);
+// bounds[0] = min, bounds[1] = max over the voxels of the eigenvalues of A(x_k)
+// (FP64 coefficients co64); both exact up to the eigenvalue formula's rounding
+// and independent of the reduction order.
+cudaError_t launch_coeff_bounds(const GridDev& g, const CoeffsDev& co64, double* bounds, cudaStream_t s);
 // x64 += x32 for systems whose outer status is ACTIVE; inner iterations are
 // added to the outer totals.
 cudaError_t launch_outer_update(const GridDev& g, int L, double* x64, const float* x32,

@@ -8,12 +8,14 @@ namespace hgk {
 // ---------------------------------------------------------------------------
 // helpers: scalars init, mixed-precision refinement, A_H, conversions
 // ---------------------------------------------------------------------------
-__global__ void k_init_scalars(Scalars* sc, int L, int s0, int s1, int s2, double tol, int max_iter) {
+__global__ void k_init_scalars(Scalars* sc, int L, int s0, int s1, int s2, double tol, int max_iter,
+                               double fixed_alpha) {
     const int l = threadIdx.x;
     if (l >= L) return;
     Scalars s;
     s.rr = 0; s.pt = 0; s.alpha = 0; s.beta = 0; s.bnorm = 0; s.aen = 0; s.relres = 1.0;
     s.alpha_f = 0.f; s.beta_f = 0.f; s.best_rr = 0.0; s.stall = 0; s.stall_max = 0;
+    s.fixed_alpha = fixed_alpha;
     s.tol = tol; s.iters = 0; s.max_iter = max_iter; s.total_iters = 0;
     s.status = (l == 0) ? s0 : (l == 1) ? s1 : s2;
     sc[l] = s;
@@ -24,7 +26,7 @@ __global__ void __launch_bounds__(256) k_inner_init(GridDev g, int L, const doub
                                                     float* __restrict__ r32, float* __restrict__ p32,
                                                     float* __restrict__ x32, const Scalars* __restrict__ outer,
                                                     Scalars* inner, double inner_tol, int inner_max,
-                                                    double* partial, unsigned* counter) {
+                                                    int stall_max, double* partial, unsigned* counter) {
     const long long M = g.M;
     const long long n = (long long)L * D * M;
     double acc[MAXL] = {0.0, 0.0, 0.0};
@@ -58,7 +60,8 @@ __global__ void __launch_bounds__(256) k_inner_init(GridDev g, int L, const doub
             s.rr = tot[l] * g.invM; s.pt = 0; s.alpha = 0; s.beta = 0; s.alpha_f = 0.f; s.beta_f = 0.f;
             // an inner FP32 solve that stops improving ends; the FP64
             // refinement decides whether another inner solve is needed
-            s.best_rr = s.rr; s.stall = 0; s.stall_max = 64;
+            s.best_rr = s.rr; s.stall = 0; s.stall_max = stall_max;
+            s.fixed_alpha = outer[l].fixed_alpha;
             s.bnorm = sqrt(s.rr); s.aen = 0; s.relres = 1.0; s.tol = itol;
             s.iters = 0; s.max_iter = inner_max; s.total_iters = 0;
             s.status = act[l] ? (s.rr > 0.0 ? ST_ACTIVE : ST_CONVERGED) : ST_IDLE;
@@ -139,6 +142,76 @@ __global__ void __launch_bounds__(256) k_energy(GridDev g, int L, CoeffsDev co, 
     }
 }
 
+// Eigenvalues of a symmetric D x D matrix by cyclic Jacobi rotations (Golub
+// and Van Loan, Matrix Computations, Sec. 8.5): each rotation in the (p, q)
+// plane zeroes a_pq; the diagonal converges to the eigenvalues with absolute
+// error of order eps ||A||, also for nearly equal eigenvalues.
+template <int D>
+__device__ __forceinline__ void sym_eig_jacobi(double (&a)[D][D], double (&ev)[D]) {
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        double off = 0.0, dia = 0.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            dia += fabs(a[i][i]);
+#pragma unroll
+            for (int j = i + 1; j < D; ++j) off += fabs(a[i][j]);
+        }
+        if (off <= 1e-18 * dia) break;
+#pragma unroll
+        for (int p = 0; p < D - 1; ++p) {
+#pragma unroll
+            for (int q = p + 1; q < D; ++q) {
+                const double apq = a[p][q];
+                if (apq == 0.0) continue;
+                // tan of the rotation angle: the smaller root of t^2 + 2 theta t - 1 = 0
+                const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0);
+                const double sn = t * c;
+                a[p][p] -= t * apq;
+                a[q][q] += t * apq;
+                a[p][q] = a[q][p] = 0.0;
+#pragma unroll
+                for (int r = 0; r < D; ++r) {
+                    if (r == p || r == q) continue;
+                    const double arp = a[r][p], arq = a[r][q];
+                    a[r][p] = a[p][r] = c * arp - sn * arq;
+                    a[r][q] = a[q][r] = sn * arp + c * arq;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) ev[i] = a[i][i];
+}
+
+// min and max eigenvalue of A(x_k) over all voxels.  Eigenvalues of SPD
+// matrices are positive, so their FP64 bit patterns order like the values
+// and the grid-wide min/max are integer atomics (order-independent).
+template <int D>
+__global__ void __launch_bounds__(256) k_coeff_bounds(GridDev g, CoeffsDev co,
+                                                      unsigned long long* bounds) {
+    const long long M = g.M;
+    double lo = INFINITY, hi = 0.0;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < M;
+         k += (long long)gridDim.x * blockDim.x) {
+        double am[D][D], ev[D];
+        load_coeffs<double, D>(co, k, M, am, static_cast<const double*>(co.table));
+        sym_eig_jacobi<D>(am, ev);
+#pragma unroll
+        for (int i = 0; i < D; ++i) { lo = fmin(lo, ev[i]); hi = fmax(hi, ev[i]); }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&bounds[0], (unsigned long long)__double_as_longlong(fmax(lo, 0.0)));
+        atomicMax(&bounds[1], (unsigned long long)__double_as_longlong(fmax(hi, 0.0)));
+    }
+}
+
 template <typename S, typename Dd>
 __global__ void k_convert(const S* __restrict__ src, Dd* __restrict__ dst, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -209,9 +282,9 @@ cudaError_t launch_row_inv(int prec, const GridDev& g, const AxisPlanH& pl, cons
 }
 
 cudaError_t launch_init_scalars(Scalars* sc, int L, const int* st, double tol, int max_iter,
-                                cudaStream_t s) {
+                                double fixed_alpha, cudaStream_t s) {
     k_init_scalars<<<1, 32, 0, s>>>(sc, L, st[0], L > 1 ? st[1] : ST_IDLE, L > 2 ? st[2] : ST_IDLE,
-                                    tol, max_iter);
+                                    tol, max_iter, fixed_alpha);
     return cudaGetLastError();
 }
 
@@ -225,12 +298,15 @@ static unsigned elem_grid(long long n) {
 
 cudaError_t launch_inner_init(const GridDev& g, int L, const double* r64, float* r32, float* p32,
                               float* x32, const Scalars* outer, Scalars* inner, double inner_tol,
-                              int inner_max, double* partial, unsigned* counter, cudaStream_t s) {
+                              int inner_max, int stall_max, double* partial, unsigned* counter,
+                              cudaStream_t s) {
     unsigned nb = elem_grid((long long)L * g.d * g.M);
     if (g.d == 2)
-        k_inner_init<2><<<nb, 256, 0, s>>>(g, L, r64, r32, p32, x32, outer, inner, inner_tol, inner_max, partial, counter);
+        k_inner_init<2><<<nb, 256, 0, s>>>(g, L, r64, r32, p32, x32, outer, inner, inner_tol, inner_max,
+                                           stall_max, partial, counter);
     else
-        k_inner_init<3><<<nb, 256, 0, s>>>(g, L, r64, r32, p32, x32, outer, inner, inner_tol, inner_max, partial, counter);
+        k_inner_init<3><<<nb, 256, 0, s>>>(g, L, r64, r32, p32, x32, outer, inner, inner_tol, inner_max,
+                                           stall_max, partial, counter);
     return cudaGetLastError();
 }
 
@@ -248,6 +324,17 @@ cudaError_t launch_energy(const GridDev& g, int L, const CoeffsDev& co64, const 
     unsigned nb = elem_grid(g.M);
     if (g.d == 2) k_energy<2><<<nb, 256, 0, s>>>(g, L, co64, x, loadmask, partial, counter, out);
     else          k_energy<3><<<nb, 256, 0, s>>>(g, L, co64, x, loadmask, partial, counter, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coeff_bounds(const GridDev& g, const CoeffsDev& co64, double* bounds, cudaStream_t s) {
+    unsigned long long* b = reinterpret_cast<unsigned long long*>(bounds);
+    cudaError_t e = cudaMemsetAsync(b, 0xff, sizeof(unsigned long long), s);   // min: above every value
+    if (e == cudaSuccess) e = cudaMemsetAsync(b + 1, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    unsigned nb = elem_grid(g.M);
+    if (g.d == 2) k_coeff_bounds<2><<<nb, 256, 0, s>>>(g, co64, b);
+    else          k_coeff_bounds<3><<<nb, 256, 0, s>>>(g, co64, b);
     return cudaGetLastError();
 }
 

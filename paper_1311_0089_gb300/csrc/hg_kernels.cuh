@@ -499,11 +499,18 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
             if (a.mode == FWD_CG) {
                 if (a.check_status && s.status != ST_ACTIVE) continue;
                 s.pt = val;
-                if (!(val > 0.0) || !isfinite(val)) {
+                if (s.fixed_alpha > 0.0 && s.rr == 0.0) {
+                    // Moulinec-Suquet reached the fixed point exactly: the step
+                    // from r = 0 is zero
+                    s.status = ST_CONVERGED;
+                    s.alpha = 0.0;
+                } else if (!(val > 0.0) || !isfinite(val)) {
                     s.status = ST_BREAKDOWN;
                     s.alpha = 0.0;
                 } else {
-                    s.alpha = s.rr / val;
+                    // CG: alpha = (r, r) / (p, A p); Moulinec-Suquet: the step
+                    // of the reference medium, 1 / lambda
+                    s.alpha = s.fixed_alpha > 0.0 ? s.fixed_alpha : s.rr / val;
                 }
                 s.alpha_f = (float)s.alpha;
             } else {
@@ -800,8 +807,12 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
                 s.total_iters += 1;
                 const double rel = sqrt(rr) / s.bnorm;
                 s.relres = rel;
+                // Moulinec-Suquet stops on the step just taken, x_{i+1} - x_i =
+                // r_i / lambda, i.e. on the residual before this update (the
+                // tolerance was rescaled by lambda / ||b|| at the right-hand side)
+                const double crit = s.fixed_alpha > 0.0 ? sqrt(s.rr) / s.bnorm : rel;
                 if (!isfinite(rr)) s.status = ST_BREAKDOWN;
-                else if (rel <= s.tol) s.status = ST_CONVERGED;
+                else if (crit <= s.tol) s.status = ST_CONVERGED;
                 else if (s.iters >= s.max_iter) s.status = ST_MAXITER;
                 if (s.stall_max > 0 && s.status == ST_ACTIVE) {
                     if (rr < 0.25 * s.best_rr) {
@@ -811,7 +822,7 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
                         s.status = ST_STAGNATED;
                     }
                 }
-                s.beta = rr / s.rr;
+                s.beta = s.fixed_alpha > 0.0 ? 0.0 : rr / s.rr;   // MS: p = r
                 s.beta_f = (float)s.beta;
                 s.rr = rr;
             } else if (a.mode == INV_RHS) {
@@ -828,6 +839,11 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
                 if (!(s.bnorm > ZERO_RHS * s.aen)) {
                     s.status = ST_ZERO_RHS;
                     s.relres = 0.0;
+                } else if (s.fixed_alpha > 0.0) {
+                    // Moulinec-Suquet: ||e_{i+1} - e_i|| = ||r_i|| / lambda with
+                    // ||E|| = 1 for a unit load, so ||e_{i+1} - e_i|| / ||E||
+                    // <= tol  <=>  ||r_i|| / ||b|| <= tol lambda / ||b||
+                    s.tol = s.tol / (s.fixed_alpha * s.bnorm);
                 }
             } else {  // INV_RESID
                 s.relres = sqrt(rr) / s.bnorm;

@@ -70,12 +70,15 @@ struct hg_grid {
     uint8_t* d_phase = nullptr;
     void* d_table[2] = {nullptr, nullptr};
     void* d_field[2] = {nullptr, nullptr};
+    // eigenvalue bounds c_A, C_A of the current coefficients (Moulinec-Suquet)
+    bool bounds_ok = false;
+    double c_A = 0.0, C_A = 0.0;
     // solver state
     hgrt::Work work[2];
     double* partial = nullptr;
     long long partial_slots = 0;
     unsigned* counters = nullptr;
-    double* d_AH = nullptr;
+    double* d_AH = nullptr;        // 32 doubles: [0, 18) A_H forms, [24, 26) bounds
     double* d_E = nullptr;
     double* d_A0 = nullptr;
     hgk::Scalars* h_sc = nullptr;  // pinned: scalars of the last tick
@@ -126,6 +129,9 @@ struct Job {
     long long launched = 0, launches0 = 0;
     double t0 = 0.0;
     hg_result res{};
+    double fixed_alpha = 0.0;   // Moulinec-Suquet: 1 / lambda (0: CG)
+    double lambda = 0.0;
+    int stall_max = 64;         // inner FP32 solves: iterations without a 4x drop
     int prof_prev_iters = 0;    // time_pass: iterations done before the chunk in flight
     double prof_ms = 0.0;
     int prof_n = 0;
