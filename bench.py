@@ -50,9 +50,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tol", type=float, default=TOL)
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "batched", "serving"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "batched", "serving", "ms"],
                     help="c2: 729x729 (default, the headline); c3: 135^3 3D; batched: 256 2D "
-                         "problems through the scheduler; serving: Poisson request stream")
+                         "problems through the scheduler; serving: Poisson request stream; "
+                         "ms: Moulinec-Suquet fixed point against CG on the 729x729 geometry "
+                         "over contrasts 10, 100, 1000")
     ap.add_argument("--duration", type=float, default=20.0, help="serving: arrival window (s)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--passes-once", action="store_true",
@@ -689,6 +691,83 @@ def run_serving(args):
     return 0
 
 
+# ----------------------------------------------------------------------------
+# ms: Moulinec-Suquet fixed point against CG on the 729x729 geometry
+# ----------------------------------------------------------------------------
+def run_ms(args):
+    import torch
+    import paper_1311_0089_gb300 as hg
+    import workloads as W
+    torch.cuda.set_device(0)
+    hg.load()
+    base = W.circles_2d()
+    ctx = hg.Context(0)
+    g = ctx.grid(base.N)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    M = int(np.prod(base.N))
+    o_ms = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, method=hg.HG_MS, max_iter=200000,
+                           inner_tol=max(0.5 * args.tol, 1e-6))
+    o_cg = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=max(0.5 * args.tol, 1e-6))
+    o_ref = hg.default_opts(tol=1e-10)
+
+    def timed(o, n):
+        ts, out = [], None
+        for _ in range(n):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = g.solve(o)
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts), out
+
+    rows = []
+    sampler = ClockSampler(0)
+    headline = None
+    for rho in (10.0, 100.0, 1000.0):
+        g.set_coeffs_phase(base.phase, W.isotropic_table([1.0, rho], 2))
+        ref = g.solve(o_ref)["AH"]
+        for _ in range(max(1, args.warmup)):
+            g.solve(o_ms)
+            g.solve(o_cg)
+        n = args.steps if rho == 100.0 else max(1, min(3, args.steps))
+        if rho == 100.0:
+            sampler.start()
+        t_ms, r_ms = timed(o_ms, n)
+        if rho == 100.0:
+            clocks = sampler.stop()
+            headline = (t_ms, r_ms)
+        t_cg, r_cg = timed(o_cg, n)
+        rows.append({"contrast": rho, "lambda": r_ms["lambda_ref"],
+                     "ms_iters": r_ms["iters"], "cg_iters": r_cg["iters"],
+                     "ms_outer": r_ms["outer"], "cg_outer": r_cg["outer"],
+                     "ms_ms_per_solve": t_ms * 1e3, "cg_ms_per_solve": t_cg * 1e3,
+                     "ms_AH_max_rel_err_vs_fp64": ah_err(r_ms["AH"], ref),
+                     "cg_AH_max_rel_err_vs_fp64": ah_err(r_cg["AH"], ref)})
+    rhos = np.log([r["contrast"] for r in rows])
+    slope = lambda key: float(np.polyfit(rhos, np.log([sum(r[key]) for r in rows]), 1)[0])
+    t_ms, r_ms = headline
+    vox = M * sum(r_ms["iters"])
+    line = {
+        "metric": "Moulinec-Suquet voxel-iterations/sec (optimal lambda) vs CG on the 729x729 workload",
+        "value": vox / t_ms, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "729x729, 40 seeded circles r~U[10,30], phases 1*I / rho*I, loads e1,e2; "
+                               "MS: e_i = E - Gamma(A - lambda I) e_{i-1}, lambda = (c_A + C_A)/2, "
+                               "FP32 inner + FP64 refinement, stop when the next step is below %g; "
+                               "CG: relative residual %g" % (args.tol, args.tol),
+                   "headline_contrast": 100.0, "l2": "flushed between steps (512 MiB write)"},
+        "solves_per_s": 1.0 / t_ms,
+        "ms_vs_cg": rows,
+        "iteration_exponent_vs_contrast": {"ms": slope("ms_iters"), "cg": slope("cg_iters")},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    g.close()
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.passes_once:
@@ -697,6 +776,8 @@ def main():
         return run_batched(args)
     if args.impl == "ours" and args.workload == "serving":
         return run_serving(args)
+    if args.impl == "ours" and args.workload == "ms":
+        return run_ms(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

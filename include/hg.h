@@ -103,8 +103,9 @@ typedef struct {
     int check_every;     /* iterations between host reads of the convergence
                             flags (default 8); each chunk is one CUDA graph    */
     int max_outer;       /* HG_MIXED: refinement steps (default 30)            */
-    int time_pass;       /* >= 0: time this pass of every CG iteration with CUDA
-                            events inside the captured graphs (0 = first-axis
+    int time_pass;       /* >= 0: time this pass with CUDA events inside the
+                            captured graphs, in the first iteration of every
+                            chunk of check_every iterations (0 = first-axis
                             forward pass, last = last-axis inverse pass, as in
                             hg_time_pass); results in hg_result.pass_*.
                             -1 (default): no timing.  check_every <= 64.      */
@@ -128,7 +129,8 @@ typedef struct {
     double wall_ms;         /* host wall time of the call                      */
     long long launches;     /* kernels launched by this solve                  */
     double pass_ms_total;   /* time_pass >= 0: summed duration of the timed pass
-                               over the iterations in which a system was active */
+                               over the timed iterations in which a system was
+                               active                                          */
     int pass_launches;      /* number of such launches                         */
     double lambda_ref;      /* HG_MS: the lambda used (0 for HG_CG)            */
     double c_A, C_A;        /* HG_MS: smallest and largest eigenvalue of A_N

@@ -471,14 +471,17 @@ int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nke
     const long long before = g->ctx->launches.load();
     int st = HG_OK;
     HG_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    // time_pass: the pass is bracketed in the first iteration of the chunk only,
+    // so that the event nodes (which break the programmatic launch overlap
+    // around it) perturb one iteration in `chunk`
     if (prof_pass >= 0) {
-        for (int i = 0; i < 2 * chunk; ++i)
+        for (int i = 0; i < 2; ++i)
             if (!g->prof_ev[i] && cudaEventCreate(&g->prof_ev[i]) != cudaSuccess) st = HG_ERR_CUDA;
     }
     for (int i = 0; i < chunk && st == HG_OK; ++i)
-        st = prof_pass >= 0 ? enqueue_cg_iteration(g, prec, g->gd.d, s, prof_pass, g->prof_ev[2 * i],
-                                                   g->prof_ev[2 * i + 1])
-                            : enqueue_cg_iteration(g, prec, g->gd.d, s);
+        st = (prof_pass >= 0 && i == 0)
+                 ? enqueue_cg_iteration(g, prec, g->gd.d, s, prof_pass, g->prof_ev[0], g->prof_ev[1])
+                 : enqueue_cg_iteration(g, prec, g->gd.d, s);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &graph);
     const long long nk = g->ctx->launches.load() - before;
@@ -510,17 +513,16 @@ static int map_status(int s) {
 // ----------------------------------------------------------------------------
 // Enqueue one graph chunk of CG iterations of precision `prec`, then the copy
 // of that precision's scalars to pinned host memory and the tick event.
-// time_pass: add the durations of the timed pass over the iterations of the
-// chunk that just completed in which at least one system was active.
+// time_pass: add the duration of the timed pass in the first iteration of the
+// chunk that just completed, if a system was active in it.
 static void job_collect_pass_times(Job& j) {
     if (j.o.time_pass < 0) return;
     const Scalars* h = j.g->h_sc;
     int it = 0;
     for (int l = 0; l < j.g->gd.d; ++l) it = std::max(it, h[l].iters);
-    const int k = std::min(j.chunk, std::max(0, it - j.prof_prev_iters));
-    for (int i = 0; i < k; ++i) {
+    if (it > j.prof_prev_iters) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, j.g->prof_ev[2 * i], j.g->prof_ev[2 * i + 1]) == cudaSuccess) {
+        if (cudaEventElapsedTime(&ms, j.g->prof_ev[0], j.g->prof_ev[1]) == cudaSuccess) {
             j.prof_ms += ms;
             j.prof_n += 1;
         } else {
@@ -620,6 +622,43 @@ static int job_method_setup(Job& j) {
     return HG_OK;
 }
 
+// Right-hand side b = -G A E (Eq. final_system): r = p = b, x = 0.  The mixed
+// path computes b in FP32: its first inner FP32 solve would see no more of an
+// FP64 b than its FP32 rounding, and the FP64 refinement recomputes the
+// residual from E + x.  An FP32 b too small to decide the zero right-hand-side
+// reading (ST_RHS_RECHECK) makes job_advance start over with the FP64 one.
+static int job_start_rhs(Job& j, bool fp32) {
+    hg_grid* g = j.g;
+    const GridDev& gd = g->gd;
+    const int L = gd.d;
+    int init_st[MAXL];
+    for (int l = 0; l < MAXL; ++l) init_st[l] = (l < L && ((j.o.loads_mask >> l) & 1u)) ? ST_ACTIVE : ST_IDLE;
+    HG_CU(launch_init_scalars(g->work[0].sc, L, init_st, j.o.tol, j.prec ? j.o.max_outer : j.o.max_iter,
+                              j.fixed_alpha, j.s));
+    g->ctx->launches++;
+    j.launched = 0;
+    j.prof_prev_iters = 0;
+    int st;
+    if (!fp32) {
+        if ((st = enqueue_matvec(g, 0, L, nullptr, true, true, nullptr, nullptr, INV_RHS, nullptr, 1, j.s)))
+            return st;
+        if (j.prec == 0) {
+            j.phase = Job::PLAIN;
+            return job_launch_chunk(j, 0);
+        }
+        return job_start_inner(j);
+    }
+    HG_CU(cudaMemsetAsync(g->work[0].x, 0, sizeof(double) * (size_t)L * gd.d * gd.M, j.s));
+    if ((st = enqueue_matvec(g, 1, L, nullptr, true, true, nullptr, nullptr, INV_RHS, nullptr, 1, j.s,
+                             g->work[0].sc)))
+        return st;
+    HG_CU(launch_inner_init(gd, L, nullptr, nullptr, nullptr, nullptr, g->work[0].sc, g->work[1].sc,
+                            j.o.inner_tol, j.o.max_iter, j.stall_max, g->partial, g->counters + 4, j.s));
+    g->ctx->launches++;
+    j.phase = Job::INNER;
+    return job_launch_chunk(j, 1);
+}
+
 int job_begin(Job& j) {
     hg_grid* g = j.g;
     hg_ctx* ctx = g->ctx;
@@ -642,18 +681,7 @@ int job_begin(Job& j) {
     if (j.prec == 1 && (st = grid_alloc_work(g, 1))) return st;
     if ((st = job_method_setup(j))) return st;
     HG_CU(cudaEventRecord(j.ev0, j.s));
-    int init_st[MAXL];
-    for (int l = 0; l < MAXL; ++l) init_st[l] = (l < L && ((j.o.loads_mask >> l) & 1u)) ? ST_ACTIVE : ST_IDLE;
-    HG_CU(launch_init_scalars(g->work[0].sc, L, init_st, j.o.tol, j.prec ? j.o.max_outer : j.o.max_iter,
-                              j.fixed_alpha, j.s));
-    ctx->launches++;
-    // b = -G A E  ->  r = p = b, x = 0  (Eq. final_system), in FP64
-    if ((st = enqueue_matvec(g, 0, L, nullptr, true, true, nullptr, nullptr, INV_RHS, nullptr, 1, j.s))) return st;
-    if (j.prec == 0) {
-        j.phase = Job::PLAIN;
-        return job_launch_chunk(j, 0);
-    }
-    return job_start_inner(j);
+    return job_start_rhs(j, j.prec == 1);
 }
 
 // Called once the job's tick event has completed.  Enqueues the next step or
@@ -667,6 +695,8 @@ int job_advance(Job& j, bool* done) {
     switch (j.phase) {
         case Job::PLAIN:
         case Job::INNER: {
+            for (int l = 0; l < L; ++l)
+                if (h[l].status == ST_RHS_RECHECK) return job_start_rhs(j, false);
             job_collect_pass_times(j);
             const int mi = j.o.max_iter;
             if (any_active(h, L) && j.launched <= (long long)mi + 2 * j.chunk)

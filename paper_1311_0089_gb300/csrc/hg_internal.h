@@ -19,7 +19,9 @@ enum {
     ST_MAXITER = 3,
     ST_BREAKDOWN = 4,
     ST_IDLE = 5,       // not part of this solve (load not requested)
-    ST_STAGNATED = 6   // inner FP32 solve stopped improving (refinement goes on)
+    ST_STAGNATED = 6,  // inner FP32 solve stopped improving (refinement goes on)
+    ST_RHS_RECHECK = 7 // FP32 right-hand side too small to tell from zero: the
+                       // solve recomputes it in FP64
 };
 
 // Per-system CG scalars kept on the device (written by the last CTA of a
@@ -152,6 +154,9 @@ cudaError_t launch_init_scalars(Scalars* sc, int L, const int* status_init, doub
 // Mixed precision: r32 = (float) r64, p32 = r32, x32 = 0, inner scalars from
 // the outer status (and its fixed step); reduction of (r32, r32).  An inner
 // solve stops (STAGNATED) after stall_max iterations without a 4x drop of (r, r).
+// r64 = null: r32 = p32 = b and x32 = 0 were written by the FP32 right-hand
+// side (INV_RHS) and the outer scalars hold (b, b); only the inner scalars are
+// set (one block).
 cudaError_t launch_inner_init(const GridDev& g, int L, const double* r64, float* r32, float* p32,
                               float* x32, const Scalars* outer, Scalars* inner, double inner_tol,
                               int inner_max, int stall_max, double* partial, unsigned* counter,

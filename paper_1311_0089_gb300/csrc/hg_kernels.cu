@@ -32,23 +32,27 @@ __global__ void __launch_bounds__(256) k_inner_init(GridDev g, int L, const doub
     double acc[MAXL] = {0.0, 0.0, 0.0};
     bool act[MAXL];
     for (int l = 0; l < MAXL; ++l) act[l] = (l < L) && outer[l].status == ST_ACTIVE;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int l = (int)(idx / (D * M));
-        if (!act[l]) continue;
-        const float v = (float)r64[idx];
-        r32[idx] = v;
-        p32[idx] = v;
-        x32[idx] = 0.f;
-        const double dv = (double)v;
-        if (l == 0) acc[0] += dv * dv; else if (l == 1) acc[1] += dv * dv; else acc[2] += dv * dv;
-    }
-    block_sum<MAXL>(acc);
-    int slots[MAXL] = {0, 1, 2};
-    const bool last = publish(acc, slots, L, partial, gridDim.x, blockIdx.x, counter, gridDim.x);
-    if (!last) return;
     double tot[MAXL];
-    final_sums<MAXL>(partial, gridDim.x, gridDim.x, L, tot);
+    if (r64) {
+        for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+             idx += (long long)gridDim.x * blockDim.x) {
+            const int l = (int)(idx / (D * M));
+            if (!act[l]) continue;
+            const float v = (float)r64[idx];
+            r32[idx] = v;
+            p32[idx] = v;
+            x32[idx] = 0.f;
+            const double dv = (double)v;
+            if (l == 0) acc[0] += dv * dv; else if (l == 1) acc[1] += dv * dv; else acc[2] += dv * dv;
+        }
+        block_sum<MAXL>(acc);
+        int slots[MAXL] = {0, 1, 2};
+        const bool last = publish(acc, slots, L, partial, gridDim.x, blockIdx.x, counter, gridDim.x);
+        if (!last) return;
+        final_sums<MAXL>(partial, gridDim.x, gridDim.x, L, tot);
+    } else {
+        for (int l = 0; l < MAXL; ++l) tot[l] = l < L ? outer[l].rr : 0.0;   // (b, b), normalised
+    }
     if (threadIdx.x == 0) {
         for (int l = 0; l < L; ++l) {
             Scalars s;
@@ -57,17 +61,18 @@ __global__ void __launch_bounds__(256) k_inner_init(GridDev g, int L, const doub
             // than inner_tol
             const double need = 0.5 * outer[l].tol / fmax(outer[l].relres, 1e-300);
             const double itol = fmin(0.5, fmax(inner_tol, need));
-            s.rr = tot[l] * g.invM; s.pt = 0; s.alpha = 0; s.beta = 0; s.alpha_f = 0.f; s.beta_f = 0.f;
+            s.rr = r64 ? tot[l] * g.invM : tot[l]; s.pt = 0; s.alpha = 0; s.beta = 0; s.alpha_f = 0.f; s.beta_f = 0.f;
             // an inner FP32 solve that stops improving ends; the FP64
             // refinement decides whether another inner solve is needed
             s.best_rr = s.rr; s.stall = 0; s.stall_max = stall_max;
             s.fixed_alpha = outer[l].fixed_alpha;
             s.bnorm = sqrt(s.rr); s.aen = 0; s.relres = 1.0; s.tol = itol;
             s.iters = 0; s.max_iter = inner_max; s.total_iters = 0;
-            s.status = act[l] ? (s.rr > 0.0 ? ST_ACTIVE : ST_CONVERGED) : ST_IDLE;
+            s.status = act[l] ? (s.rr > 0.0 ? ST_ACTIVE : ST_CONVERGED)
+                              : (outer[l].status == ST_RHS_RECHECK ? ST_RHS_RECHECK : ST_IDLE);
             inner[l] = s;
         }
-        *counter = 0u;
+        if (r64) *counter = 0u;
     }
 }
 
@@ -300,7 +305,7 @@ cudaError_t launch_inner_init(const GridDev& g, int L, const double* r64, float*
                               float* x32, const Scalars* outer, Scalars* inner, double inner_tol,
                               int inner_max, int stall_max, double* partial, unsigned* counter,
                               cudaStream_t s) {
-    unsigned nb = elem_grid((long long)L * g.d * g.M);
+    unsigned nb = r64 ? elem_grid((long long)L * g.d * g.M) : 1u;
     if (g.d == 2)
         k_inner_init<2><<<nb, 256, 0, s>>>(g, L, r64, r32, p32, x32, outer, inner, inner_tol, inner_max,
                                            stall_max, partial, counter);

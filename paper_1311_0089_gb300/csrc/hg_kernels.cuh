@@ -32,6 +32,9 @@ namespace hgk {
 constexpr int MAXB = 2;     // runtime kernels: butterflies per thread per stage
 constexpr int MAXT = 512;   // runtime kernels: threads per CTA (upper bound)
 constexpr double ZERO_RHS = 1e-13;
+// An FP32 right-hand side carries roundoff of about 1e-7 ||A E||; below this
+// ratio it cannot decide the zero test, and the FP64 one is taken.
+constexpr double RHS32_RECHECK = 1e-4;
 
 template <typename T> using Cx = typename cplx_t<T>::type;
 
@@ -836,7 +839,9 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
                 // along every direction G keeps (G kills constants, Lemma
                 // FD_projection (iv)); ||b|| <= ||A E|| since G is an
                 // orthogonal projection, so a ratio at roundoff level is zero.
-                if (!(s.bnorm > ZERO_RHS * s.aen)) {
+                if (sizeof(T) == 4 && !(s.bnorm > RHS32_RECHECK * s.aen)) {
+                    s.status = ST_RHS_RECHECK;
+                } else if (!(s.bnorm > ZERO_RHS * s.aen)) {
                     s.status = ST_ZERO_RHS;
                     s.relres = 0.0;
                 } else if (s.fixed_alpha > 0.0) {
