@@ -431,7 +431,8 @@ def run_ours(args):
         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
         "peak_kind": peak_kind, "traffic": profiled_traffic("fp32_" + keys[dom_pass] + ("" if d == 2 else "_3d")),
         "bytes_per_launch": dom["bytes"], "ms_per_launch": dom_avg_ms, "launches_timed": dom_n,
-        "timing": "CUDA events around every launch of this pass inside the captured graphs of the timed solves",
+        "timing": "CUDA events around this pass in the first iteration of every graph chunk (8 iterations) "
+                  "inside the captured graphs of the timed solves, on the stream the kernels run on",
         "note": ("working set of one solve (~45 MB FP32) is L2-resident between passes" if d == 2
                  else "working set (about 1 GB) exceeds L2"),
         "passes_fp32": passes,

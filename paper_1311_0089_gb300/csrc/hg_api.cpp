@@ -162,7 +162,7 @@ bool choose_str_cfg(int prec, int n, int d, int minR, size_t csize, int max_smem
         for (int Cl = 1; Cl <= 16; Cl *= 2) {   // powers of two (lane = tid & (Cl-1))
             if (d * Cl > npmax || (Cl > 1 && Cl > inner)) break;
             if (Cl > prefer_lanes && ((inner + Cl - 1) / Cl) * outer * L < 4 * 152) break;
-            if (Cl > 2 * prefer_lanes) break;
+            if (Cl > 2 * prefer_lanes || Cl > ct_max_lanes(d)) break;
             best = Cl;
         }
         if (!best) return false;

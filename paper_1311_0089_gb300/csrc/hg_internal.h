@@ -183,7 +183,10 @@ cudaError_t configure_kernels(int max_smem);
 // of such a kernel may stage (mirrors CtCaps in fft_device.cuh).
 bool ct_length(int d, int n);
 int ct_npmax(int prec, int n);
-enum { CT_THREADS_HOST = 256 };
+enum { CT_THREADS_HOST = 256 };   // = CT_THREADS
+// Most lanes of a compile-time strided tile (the device bounds its per-thread
+// loads by it; the host never chooses more).
+__host__ __device__ constexpr int ct_max_lanes(int d) { return d == 2 ? 2 : 4; }
 
 // per-precision launchers (hg_kernels_f32.cu, hg_kernels_f64.cu)
 cudaError_t launch_row_fwd_f32(const GridDev&, const AxisPlanH&, const void*, const RowCfg&, const RowFwdArgs&, cudaStream_t);

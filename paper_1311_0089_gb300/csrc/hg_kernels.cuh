@@ -288,6 +288,9 @@ __device__ __forceinline__ double div_proj(double f, double den) { return f * re
 
 // Largest number of real rows a row-pass CTA stages (RB * LB * D).
 constexpr int MAX_REAL_ROWS = 64;
+// Most lanes (pencils per component) of a compile-time strided tile: 2 in
+// 2D, 4 in 3D (ct_max_lanes in hg_internal.h, shared with the host's choice).
+static_assert(CT_THREADS == CT_THREADS_HOST, "host launch geometry and device tiling disagree");
 
 // Offset of the half-spectrum row of real row rr (-1: none) for a row tile:
 // real row rr = (rowi * nl + li) * D + al holds component al of load l0 + li
@@ -557,13 +560,38 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_strided(GridDev g, AxisP
     };
     C* Sb = static_cast<C*>(a.S) + (long long)l * D * g.Ms + o * (long long)n * inner + i0 + lane;
     const long long cstride = g.Ms;
+    if constexpr (NN > 0) {
+        // Every load of the thread is issued before the first shared-memory
+        // store (a store through a generic pointer would otherwise keep the
+        // next global load behind it): one memory latency per tile instead of
+        // one per few rows.  At most ct_max_lanes(D) lanes, so KL bounds the rows
+        // (a bound above the rows actually held costs registers and time).
+        constexpr int KL = (D * NN * ct_max_lanes(D) + CT_THREADS - 1) / CT_THREADS;
+        C v[KL];
+#pragma unroll
+        for (int k = 0; k < KL; ++k) {
+            const int row = threadIdx.x / Cl + k * rstep;
+            const int al = row / n;
+            const int m = row - al * n;
+            v[k] = (lane_ok && row < D * n) ? Sb[al * cstride + m * inner] : czero<T>();
+        }
+#pragma unroll
+        for (int k = 0; k < KL; ++k) {
+            const int row = threadIdx.x / Cl + k * rstep;
+            if (row < D * n) {
+                const int al = row / n;
+                buf[sidx(al, row - al * n)] = v[k];
+            }
+        }
+    } else {
 #pragma unroll 4
-    for (int row = threadIdx.x / Cl; row < D * n; row += rstep) {
-        const int al = row / n;
-        const int m = row - al * n;
-        C v = czero<T>();
-        if (lane_ok) v = Sb[al * cstride + m * inner];
-        buf[sidx(al, m)] = v;
+        for (int row = threadIdx.x / Cl; row < D * n; row += rstep) {
+            const int al = row / n;
+            const int m = row - al * n;
+            C v = czero<T>();
+            if (lane_ok) v = Sb[al * cstride + m * inner];
+            buf[sidx(al, m)] = v;
+        }
     }
     __syncthreads();
 
@@ -690,20 +718,38 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
     // Rebuild two real rows a, b as one complex row Z = a + i b from their
     // Hermitian half spectra: X(k) for k >= H is conj X(Nl - k).
     const C* __restrict__ S = static_cast<const C*>(a.S);
-    for (int e = threadIdx.x; e < ncplx * Nl; e += blockDim.x) {
-        const int c = e / Nl;
-        const int kk = e - c * Nl;
-        const bool up = kk >= H;
-        const int ks = up ? Nl - kk : kk;
-        const long long o0 = s_off[2 * c];
-        const long long o1 = (2 * c + 1 < nreal) ? s_off[2 * c + 1] : -1;
-        C v0 = o0 >= 0 ? S[o0 + ks] : czero<T>();
-        C v1 = o1 >= 0 ? S[o1 + ks] : czero<T>();
-        if (up) { v0.y = -v0.y; v1.y = -v1.y; }
-        C z;
-        z.x = v0.x - v1.y;
-        z.y = v0.y + v1.x;
-        buf[c * Nl + kk] = z;
+    // KB elements per thread are loaded before any is stored (see k_strided)
+    constexpr int KB = (sizeof(T) == 4 && D == 3) ? 8 : 4;
+    for (int e0 = threadIdx.x; e0 < ncplx * Nl; e0 += KB * blockDim.x) {
+        C v0[KB], v1[KB];
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v0[u] = czero<T>();
+            v1[u] = czero<T>();
+            if (e < ncplx * Nl) {
+                const int c = e / Nl;
+                const int kk = e - c * Nl;
+                const int ks = kk >= H ? Nl - kk : kk;
+                const long long o0 = s_off[2 * c];
+                const long long o1 = (2 * c + 1 < nreal) ? s_off[2 * c + 1] : -1;
+                if (o0 >= 0) v0[u] = S[o0 + ks];
+                if (o1 >= 0) v1[u] = S[o1 + ks];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < ncplx * Nl) {
+                const int c = e / Nl;
+                const int kk = e - c * Nl;
+                if (kk >= H) { v0[u].y = -v0[u].y; v1[u].y = -v1[u].y; }
+                C z;
+                z.x = v0[u].x - v1[u].y;
+                z.y = v0[u].y + v1[u].x;
+                buf[c * Nl + kk] = z;
+            }
+        }
     }
     __syncthreads();
 
