@@ -619,9 +619,16 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_strided(GridDev g, AxisP
         }
         const T invY0 = inv_y(g, 0, T());
         const T invM = inv_m(g, T());
-        for (int m = threadIdx.x / Cl; m < n && lane_ok; m += rstep) {
+        // the row's frequency in T, stepped with the row (integers below 2^24
+        // are exact in FP32): one integer-to-float conversion per thread, not
+        // one per frequency (conversions run on the slow FP64 pipe)
+        const int m_first = threadIdx.x / Cl;
+        const int half = (n - 1) >> 1;
+        const T stepf = (T)rstep, nf = (T)n;
+        T mf = (T)m_first;
+        for (int m = m_first; m < n && lane_ok; m += rstep, mf += stepf) {
             T xi[D];
-            xi[0] = (T)freq_of(m, n) * invY0;
+            xi[0] = (m <= half ? mf : mf - nf) * invY0;
 #pragma unroll
             for (int al = 1; al < D; ++al) xi[al] = xi_rest[al];
             C th[D];
