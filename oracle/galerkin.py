@@ -19,6 +19,8 @@ Galerkin method for homogenization of periodic media" (arXiv:1311.0089):
                                G_N A_N e~ = -G_N A_N E for A0 = lambda I
   * Sec. 5.3 (Lemma on CG)     CG on the non-symmetric G_N A_N from e~_0 in E_N
   * Sec. 5.3                   Moulinec-Suquet fixed point (Neumann series)
+  * Sec. 5.1 (Eq. Helmholtz_discrete) R^{dN} = U_N (+) E_N (+) J_N; the dual
+                               (flux) problem on J_N that Sec. 6 announces
   * Sec. 3 (Eq. forms_def1)    energy a(e,e) -> homogenized matrix A_H
                                (A_H itself is not defined in the paper; the
                                energy reading is stated in the project notes)
@@ -40,6 +42,7 @@ __all__ = [
     "idft_naive", "gamma_hat", "apply_gamma", "apply_G", "apply_A", "apply_K",
     "inner", "ZERO_RHS", "cg", "homogenized_energy", "homogenized_flux", "solve_AH",
     "dense_gamma_matrix", "solve_lsd_dense", "moulinec_suquet",
+    "apply_gamma_J", "invert_coeffs", "cg_dual", "solve_AH_dual", "solve_dual_dense",
 ]
 
 
@@ -356,3 +359,108 @@ def moulinec_suquet(A: np.ndarray, E: np.ndarray, N, Y=None, lam: float = 1.0,
         if step <= tol:
             break
     return {"e": e, "iters": it, "step": step}
+
+
+# ---------------------------------------------------------------------------
+# dual (flux) formulation on J_N (Eq. Helmholtz_discrete; announced in Sec. 6)
+# ---------------------------------------------------------------------------
+def apply_gamma_J(u: np.ndarray, N, Y=None) -> np.ndarray:
+    """Orthogonal projection onto J_N (zero-mean divergence-free grid fields).
+
+    Eq. Helmholtz_discrete splits R^{dN} into the mutually orthogonal U_N
+    (constants), E_N and J_N, so the projection onto J_N is the identity minus
+    the projection onto U_N (the grid mean) minus Gamma_N (the orthogonal
+    projection onto E_N for A0 = I, Lemma FD_projection)."""
+    N = check_grid(N)
+    d = len(N)
+    mean = u.reshape(d, -1).mean(axis=1).reshape((d,) + (1,) * d)
+    return u - mean - apply_gamma(u, N, Y)
+
+
+def invert_coeffs(A: np.ndarray) -> np.ndarray:
+    """A(x_k)^-1 per voxel, (d, d, *N) -> (d, d, *N)."""
+    d = A.shape[0]
+    m = np.moveaxis(A.reshape(d, d, -1), 2, 0)
+    inv = np.linalg.inv(m)
+    return np.moveaxis(inv, 0, 2).reshape(A.shape)
+
+
+def cg_dual(A: np.ndarray, S: np.ndarray, N, Y=None, tol: float = 1e-10,
+            maxiter: int = 10000) -> Dict:
+    """Dual GaNi problem: the flux s = S + s~ with s~ in J_N and
+    (A_N^-1 s, t) = 0 for all t in J_N, i.e. G_J A_N^-1 s~ = -G_J A_N^-1 S
+    with G_J the projection onto J_N.  G_J A_N^-1 is symmetric positive
+    definite on J_N, so the CG steps of `cg` apply unchanged (same stopping
+    rule and zero right-hand-side rule)."""
+    N = check_grid(N)
+    d = len(N)
+    Ainv = invert_coeffs(A)
+    K = lambda u: apply_gamma_J(apply_A(Ainv, u), N, Y)
+    Svec = np.asarray(S, dtype=np.float64).reshape((d,) + (1,) * d) * np.ones((d,) + N)
+    b = -K(Svec)
+    x = np.zeros((d,) + N)
+    r = b.copy()
+    p = r.copy()
+    rr = inner(r, r)
+    bnorm = np.sqrt(rr)
+    AS = apply_A(Ainv, Svec)
+    if bnorm <= ZERO_RHS * np.sqrt(inner(AS, AS)):
+        bnorm = 0.0
+    if bnorm == 0.0:
+        return {"x": x, "iters": 0, "rel_res": 0.0}
+    it = 0
+    rel = 1.0
+    while it < maxiter and rel > tol:
+        q = K(p)
+        alpha = rr / inner(p, q)
+        x = x + alpha * p
+        r = r - alpha * q
+        it += 1
+        rr_new = inner(r, r)
+        rel = np.sqrt(rr_new) / bnorm
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return {"x": x, "iters": it, "rel_res": rel}
+
+
+def solve_AH_dual(A: np.ndarray, N, Y=None, tol: float = 1e-10, maxiter: int = 10000) -> Dict:
+    """Unit flux loads S = e_j: the homogenized compliance
+    C_H[i][j] = (A_N^-1 s_j, s_i) (energy form) and <A_N^-1 s_j>_i (mean
+    field, flux form), and A_H = C_H^-1 from each."""
+    N = check_grid(N)
+    d = len(N)
+    Ainv = invert_coeffs(A)
+    ss, iters, xs = [], [], []
+    for j in range(d):
+        S = np.zeros(d)
+        S[j] = 1.0
+        out = cg_dual(A, S, N, Y, tol, maxiter)
+        iters.append(out["iters"])
+        xs.append(out["x"])
+        ss.append(S.reshape((d,) + (1,) * d) + out["x"])
+    CH = homogenized_energy(Ainv, ss)
+    CH_flux = homogenized_flux(Ainv, ss)
+    return {"CH": CH, "CH_flux": CH_flux, "AH": np.linalg.inv(CH), "AH_flux": np.linalg.inv(CH_flux),
+            "iters": iters, "x": xs}
+
+
+def solve_dual_dense(A: np.ndarray, S: np.ndarray, N, Y=None) -> np.ndarray:
+    """Dense route to s~ for tiny grids: with P_J the projection onto J_N
+    assembled from the dense DFT matrices (identity minus mean minus dense
+    Gamma_N), solve [P_J A^-1 P_J + (I - P_J)] s~ = -P_J A^-1 S by LU (the
+    second term makes the matrix regular off J_N without touching J_N)."""
+    N = check_grid(N)
+    d = len(N)
+    M = int(np.prod(N))
+    Gam = dense_gamma_matrix(N, Y, None)
+    Pu = np.kron(np.eye(d), np.full((M, M), 1.0 / M))
+    PJ = np.eye(d * M) - Pu - Gam
+    Ai = invert_coeffs(A).reshape(d, d, M)
+    Ad = np.zeros((d * M, d * M))
+    idx = np.arange(M)
+    for a in range(d):
+        for b in range(d):
+            Ad[a * M + idx, b * M + idx] = Ai[a, b]
+    sysm = PJ @ Ad @ PJ + (np.eye(d * M) - PJ)
+    rhs = -PJ @ (Ad @ np.repeat(np.asarray(S, dtype=np.float64), M))
+    return np.linalg.solve(sysm, rhs).reshape((d,) + N)
