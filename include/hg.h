@@ -79,6 +79,16 @@ typedef enum {
 } hg_method;
 
 typedef enum {
+    HG_PRIMAL = 0,  /* fields: e = E + e~, e~ in E_N (curl-free), loads E = e_j */
+    HG_DUAL = 1     /* fluxes: s = S + s~, s~ in J_N (divergence-free), unit
+                       flux loads S = e_j, coefficients A_N^-1; the Helmholtz
+                       decomposition R^{dN} = U_N + E_N + J_N of Sec. 5.1
+                       (Eq. Helmholtz_discrete) and the dual problem that
+                       Sec. 6 announces.  Gives the compliance C_H and
+                       A_H = C_H^-1, equal to the primal A_H for GaNi        */
+} hg_formulation;
+
+typedef enum {
     HG_COEFF_FULL = 0,    /* |N| x d x d doubles, voxel-major, symmetric      */
     HG_COEFF_PACKED = 1   /* d(d+1)/2 x |N| doubles, component-major; the
                              packed order is (11,22[,33],12[,13,23])          */
@@ -113,12 +123,15 @@ typedef struct {
                             c_A, C_A: the first HG_MS solve after new
                             coefficients computes them on the device and
                             waits for them on the host once                   */
+    int formulation;     /* hg_formulation (default HG_PRIMAL); HG_DUAL needs
+                            every load in loads_mask and the reference
+                            medium A0 = I                                      */
 } hg_solve_opts;
 
 typedef struct {
     int status;             /* hg_status of the solve                          */
     int d;
-    double AH[9];           /* d x d row-major energy form                     */
+    double AH[9];           /* d x d row-major energy form (HG_DUAL: C_H^-1)   */
     double AH_flux[9];      /* d x d mean-flux form <A e_j>_i (check)          */
     int iters[3];           /* iterations per load (HG_MIXED: inner FP32
                                iterations summed over refinement steps)        */
@@ -133,8 +146,12 @@ typedef struct {
                                active                                          */
     int pass_launches;      /* number of such launches                         */
     double lambda_ref;      /* HG_MS: the lambda used (0 for HG_CG)            */
-    double c_A, C_A;        /* HG_MS: smallest and largest eigenvalue of A_N
-                               over the voxels (0 for HG_CG)                   */
+    double c_A, C_A;        /* HG_MS: smallest and largest eigenvalue of the
+                               coefficients the method iterates with (A_N, or
+                               A_N^-1 for HG_DUAL) over the voxels             */
+    double CH[9];           /* HG_DUAL: compliance C_H[i][j] = (A_N^-1 s_j, s_i)
+                               (energy form); AH = C_H^-1, AH_flux = the inverse
+                               of the mean-field form <A_N^-1 s_j>_i           */
 } hg_result;
 
 /* Fill opts with the defaults listed above. */
@@ -171,7 +188,8 @@ int hg_set_coeffs_phase(hg_grid* grid, const uint8_t* phase, int n_phases,
  * NULL (d*d doubles, row-major); info may be NULL. */
 int hg_solve_AH(hg_grid* grid, const hg_solve_opts* opts, double* AH_out, hg_result* info);
 
-/* Copy e~_load of the last solve (d x |N| doubles, component-major). */
+/* Copy e~_load of the last solve (d x |N| doubles, component-major); after an
+ * HG_DUAL solve, the flux fluctuation s~_load. */
 int hg_get_field(hg_grid* grid, int load, double* e_out, int on_device);
 
 /* Asynchronous solve through the context's scheduler (continuous batching:

@@ -26,6 +26,8 @@ HG_FP64 = 0
 HG_MIXED = 1
 HG_CG = 0
 HG_MS = 1
+HG_PRIMAL = 0
+HG_DUAL = 1
 HG_COEFF_FULL = 0
 HG_COEFF_PACKED = 1
 STATUS = {
@@ -49,7 +51,7 @@ class SolveOpts(ctypes.Structure):
                 ("lambda_ref", ctypes.c_double), ("loads_mask", ctypes.c_uint),
                 ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("time_pass", ctypes.c_int),
-                ("method", ctypes.c_int)]
+                ("method", ctypes.c_int), ("formulation", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -59,7 +61,7 @@ class Result(ctypes.Structure):
                 ("device_ms", ctypes.c_double), ("wall_ms", ctypes.c_double),
                 ("launches", ctypes.c_longlong), ("pass_ms_total", ctypes.c_double),
                 ("pass_launches", ctypes.c_int), ("lambda_ref", ctypes.c_double),
-                ("c_A", ctypes.c_double), ("C_A", ctypes.c_double)]
+                ("c_A", ctypes.c_double), ("C_A", ctypes.c_double), ("CH", ctypes.c_double * 9)]
 
     def to_dict(self) -> dict:
         d = self.d
@@ -78,6 +80,7 @@ class Result(ctypes.Structure):
             "lambda_ref": self.lambda_ref,
             "c_A": self.c_A,
             "C_A": self.C_A,
+            "CH": np.array(self.CH[: d * d]).reshape(d, d),
         }
 
 

@@ -315,8 +315,8 @@ int grid_alloc_common(hg_grid* g) {
 CoeffsDev coeffs_for(const hg_grid* g, int prec, bool withA) {
     CoeffsDev c;
     c.phase = g->d_phase;
-    c.table = g->d_table[prec];
-    c.field = g->d_field[prec];
+    c.table = g->form ? g->d_table_inv[prec] : g->d_table[prec];
+    c.field = g->form ? g->d_field_inv[prec] : g->d_field[prec];
     c.mode = !withA ? 2 : (g->coeff_mode == 0 ? 0 : 1);
     c.n_phases = g->n_phases;
     return c;
@@ -338,6 +338,7 @@ int enqueue_forward_strided(hg_grid* g, int prec, int L, int check_status, int g
     sa.S = w.S;
     sa.sc = status_sc ? status_sc : w.sc;
     sa.check_status = check_status;
+    sa.dual = g->form;
     if (A0) {
         sa.has_A0 = 1;
         for (int i = 0; i < d * d; ++i) sa.A0[i] = A0[i];
@@ -387,7 +388,7 @@ int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_p
     StrArgs sa;
     memset(&sa, 0, sizeof(sa));
     sa.early_stage = 1;
-    sa.L = L; sa.S = w.S; sa.sc = w.sc; sa.check_status = 1;
+    sa.L = L; sa.S = w.S; sa.sc = w.sc; sa.check_status = 1; sa.dual = g->form;
     if (d == 3) {
         sa.mode = STR_FWD; sa.axis = 1; sa.outer = gd.N[0]; sa.n = gd.N[1]; sa.inner = gd.H;
         HG_CU(mark(true));
@@ -458,7 +459,7 @@ int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, 
 // A CUDA graph of `chunk` CG iterations, cached per precision.
 int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nkern, int prof_pass) {
     GraphCache& gc = g->graphs[prec];
-    if (gc.exec && gc.chunk == chunk && gc.prof_pass == prof_pass) {
+    if (gc.exec && gc.chunk == chunk && gc.prof_pass == prof_pass && gc.form == g->form) {
         *out = gc.exec;
         *nkern = gc.nkern;
         return HG_OK;
@@ -493,6 +494,7 @@ int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nke
     if (e != cudaSuccess) { set_last_cuda_error(e, "cudaGraphInstantiate"); gc.exec = nullptr; return HG_ERR_CUDA; }
     gc.chunk = chunk;
     gc.prof_pass = prof_pass;
+    gc.form = g->form;
     gc.nkern = (int)nk;
     *out = gc.exec;
     *nkern = gc.nkern;
@@ -585,6 +587,55 @@ static int job_finish_enqueue(Job& j) {
     return job_tick_copy(j, 0);
 }
 
+// A(x_k)^-1 for the dual formulation, made once per coefficient set: phase
+// tables are inverted on the host (adjugate over determinant, at most 256
+// small matrices), packed fields on the device.
+static void invert_small(const double* a, double* r, int d) {
+    if (d == 2) {
+        const double det = a[0] * a[3] - a[1] * a[2];
+        r[0] = a[3] / det; r[1] = -a[1] / det; r[2] = -a[2] / det; r[3] = a[0] / det;
+        return;
+    }
+    const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+    const double c10 = a[2] * a[7] - a[1] * a[8], c11 = a[0] * a[8] - a[2] * a[6], c12 = a[1] * a[6] - a[0] * a[7];
+    const double c20 = a[1] * a[5] - a[2] * a[4], c21 = a[2] * a[3] - a[0] * a[5], c22 = a[0] * a[4] - a[1] * a[3];
+    const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    // inverse = transpose of the cofactor matrix / det
+    r[0] = c00 / det; r[1] = c10 / det; r[2] = c20 / det;
+    r[3] = c01 / det; r[4] = c11 / det; r[5] = c21 / det;
+    r[6] = c02 / det; r[7] = c12 / det; r[8] = c22 / det;
+}
+
+static int grid_ensure_inverse(hg_grid* g, cudaStream_t s) {
+    if (g->inv_ok) return HG_OK;
+    hg_ctx* c = g->ctx;
+    const int d = g->gd.d;
+    int st;
+    if (g->coeff_mode == 0) {
+        const size_t n = (size_t)g->n_phases * d * d;
+        std::vector<double> tb(n), inv(n);
+        std::vector<float> inv32(n);
+        HG_CU(cudaMemcpyAsync(tb.data(), g->d_table[0], n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        HG_CU(cudaStreamSynchronize(s));
+        for (int p = 0; p < g->n_phases; ++p) invert_small(&tb[(size_t)p * d * d], &inv[(size_t)p * d * d], d);
+        for (size_t i = 0; i < n; ++i) inv32[i] = (float)inv[i];
+        if (!g->d_table_inv[0] && (st = dev_alloc(c, &g->d_table_inv[0], n * sizeof(double)))) return st;
+        if (!g->d_table_inv[1] && (st = dev_alloc(c, &g->d_table_inv[1], n * sizeof(float)))) return st;
+        HG_CU(cudaMemcpyAsync(g->d_table_inv[0], inv.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+        HG_CU(cudaMemcpyAsync(g->d_table_inv[1], inv32.data(), n * sizeof(float), cudaMemcpyHostToDevice, s));
+        HG_CU(cudaStreamSynchronize(s));   // the host buffers go out of scope
+    } else {
+        const size_t n = (size_t)(d * (d + 1) / 2) * g->gd.M;
+        if (!g->d_field_inv[0] && (st = dev_alloc(c, &g->d_field_inv[0], n * sizeof(double)))) return st;
+        if (!g->d_field_inv[1] && (st = dev_alloc(c, &g->d_field_inv[1], n * sizeof(float)))) return st;
+        HG_CU(launch_invert_field(d, g->gd.M, (const double*)g->d_field[0], (double*)g->d_field_inv[0],
+                                  (float*)g->d_field_inv[1], s));
+        c->launches++;
+    }
+    g->inv_ok = true;
+    return HG_OK;
+}
+
 // Moulinec-Suquet (Sec. 5.3 comments): e_i = E - Gamma_N (A_N - lambda I)
 // e_{i-1} with Gamma_N = (1 / lambda) G_N for A0 = lambda I.  Writing e_i = E +
 // x_i with x_i in E_N (G_N E = 0, G_N x = x on E_N, Lemma FD_projection) gives
@@ -599,20 +650,22 @@ static int job_method_setup(Job& j) {
     j.lambda = 0.0;
     j.stall_max = 64;
     if (j.o.method != HG_MS) return HG_OK;
-    if (!g->bounds_ok) {
+    const int f = g->form;
+    if (!g->bounds_ok[f]) {
         double* db = g->d_AH + 24;
         HG_CU(launch_coeff_bounds(g->gd, coeffs_for(g, 0, true), db, j.s));
         g->ctx->launches++;
         double hb[2] = {0.0, 0.0};
         HG_CU(cudaMemcpyAsync(hb, db, sizeof(hb), cudaMemcpyDeviceToHost, j.s));
         HG_CU(cudaStreamSynchronize(j.s));
-        g->c_A = hb[0];
-        g->C_A = hb[1];
-        g->bounds_ok = true;
+        g->c_A[f] = hb[0];
+        g->C_A[f] = hb[1];
+        g->bounds_ok[f] = true;
     }
-    const double lam = j.o.lambda_ref > 0.0 ? j.o.lambda_ref : 0.5 * (g->c_A + g->C_A);
-    if (!(lam > 0.5 * g->C_A) || !(g->c_A > 0.0)) return HG_ERR_ARG;
-    const double q = std::max(std::fabs(1.0 - g->c_A / lam), std::fabs(1.0 - g->C_A / lam));
+    const double cA = g->c_A[f], CA = g->C_A[f];
+    const double lam = j.o.lambda_ref > 0.0 ? j.o.lambda_ref : 0.5 * (cA + CA);
+    if (!(lam > 0.5 * CA) || !(cA > 0.0)) return HG_ERR_ARG;
+    const double q = std::max(std::fabs(1.0 - cA / lam), std::fabs(1.0 - CA / lam));
     // an inner FP32 solve is stagnating when (r, r) has not dropped 4x in
     // twice the iterations the contraction needs for that (q^2 per step)
     const double per4 = q > 0.0 ? std::log(4.0) / (-2.0 * std::log(q)) : 1.0;
@@ -679,6 +732,11 @@ int job_begin(Job& j) {
     if ((st = grid_alloc_common(g))) return st;
     if ((st = grid_alloc_work(g, 0))) return st;
     if (j.prec == 1 && (st = grid_alloc_work(g, 1))) return st;
+    g->form = j.o.formulation == HG_DUAL ? 1 : 0;
+    if (g->form) {
+        if ((j.o.loads_mask & ((1u << L) - 1u)) != ((1u << L) - 1u)) return HG_ERR_ARG;
+        if ((st = grid_ensure_inverse(g, j.s))) return st;
+    }
     if ((st = job_method_setup(j))) return st;
     HG_CU(cudaEventRecord(j.ev0, j.s));
     return job_start_rhs(j, j.prec == 1);
@@ -739,6 +797,13 @@ int job_advance(Job& j, bool* done) {
             memset(&r, 0, sizeof(r));
             r.d = gd.d;
             for (int i = 0; i < gd.d * gd.d; ++i) { r.AH[i] = g->h_AH[i]; r.AH_flux[i] = g->h_AH[gd.d * gd.d + i]; }
+            if (g->form) {
+                // the energy of the flux loads is the compliance: A_H = C_H^-1
+                double ch[9], chf[9];
+                for (int i = 0; i < gd.d * gd.d; ++i) { ch[i] = r.AH[i]; chf[i] = r.AH_flux[i]; r.CH[i] = ch[i]; }
+                invert_small(ch, r.AH, gd.d);
+                invert_small(chf, r.AH_flux, gd.d);
+            }
             for (int l = 0; l < L; ++l) {
                 const Scalars& sc = h[l];
                 int ms = map_status(sc.status);
@@ -759,8 +824,8 @@ int job_advance(Job& j, bool* done) {
             r.pass_launches = j.prof_n;
             if (j.o.method == HG_MS) {
                 r.lambda_ref = j.lambda;
-                r.c_A = g->c_A;
-                r.C_A = g->C_A;
+                r.c_A = g->c_A[g->form];
+                r.C_A = g->C_A[g->form];
             }
             g->last_prec = j.prec;
             j.result = result;

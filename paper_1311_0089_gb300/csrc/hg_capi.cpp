@@ -60,6 +60,15 @@ int check_size(int n) {
     return m == 1 ? HG_OK : HG_ERR_UNSUPPORTED_SIZE;
 }
 
+void free_inverse_coeffs(hg_grid* g) {
+    for (int p = 0; p < 2; ++p) {
+        dev_free(g->ctx, g->d_table_inv[p]);
+        dev_free(g->ctx, g->d_field_inv[p]);
+        g->d_table_inv[p] = g->d_field_inv[p] = nullptr;
+    }
+    g->inv_ok = false;
+}
+
 void free_coeffs(hg_grid* g) {
     dev_free(g->ctx, g->d_phase);
     g->d_phase = nullptr;
@@ -68,6 +77,7 @@ void free_coeffs(hg_grid* g) {
         dev_free(g->ctx, g->d_field[p]);
         g->d_table[p] = g->d_field[p] = nullptr;
     }
+    free_inverse_coeffs(g);
     g->coeff_mode = -1;
 }
 
@@ -91,6 +101,7 @@ void hg_default_opts(hg_solve_opts* o) {
     o->max_outer = 30;
     o->time_pass = -1;
     o->method = HG_CG;
+    o->formulation = HG_PRIMAL;
 }
 
 const char* hg_strerror(int s) {
@@ -299,7 +310,7 @@ int hg_set_coeffs(hg_grid* g, const double* A, int layout, int on_device) {
     HG_CU(cudaMemcpyAsync(g->d_field[1], pk32.data(), pk32.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     HG_CU(cudaStreamSynchronize(c->stream));
     g->coeff_mode = 1;
-    g->bounds_ok = false;
+    g->bounds_ok[0] = g->bounds_ok[1] = false;
     return HG_OK;
 }
 
@@ -349,7 +360,8 @@ int hg_set_coeffs_phase(hg_grid* g, const uint8_t* phase, int n_phases, const do
     HG_CU(cudaMemcpyAsync(g->d_table[1], tb32.data(), tb32.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     HG_CU(cudaStreamSynchronize(c->stream));
     g->coeff_mode = 0;
-    g->bounds_ok = false;
+    g->bounds_ok[0] = g->bounds_ok[1] = false;
+    g->inv_ok = false;   // a reused phase table keeps its buffers; the inverse is redone
     g->n_phases = n_phases;
     return HG_OK;
 }
@@ -360,7 +372,7 @@ int hg_solve_AH(hg_grid* g, const hg_solve_opts* opts, double* AH_out, hg_result
     if (opts) o = *opts; else hg_default_opts(&o);
     if (!(o.tol > 0.0) || o.max_iter < 1 || (o.prec != HG_FP64 && o.prec != HG_MIXED) ||
         !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 || (o.method != HG_CG && o.method != HG_MS) ||
-        !std::isfinite(o.lambda_ref))
+        !std::isfinite(o.lambda_ref) || (o.formulation != HG_PRIMAL && o.formulation != HG_DUAL))
         return HG_ERR_ARG;
     if (o.time_pass >= hg_num_passes(g) || (o.time_pass >= 0 && o.check_every > hgrt::MAX_PROF_CHUNK))
         return HG_ERR_ARG;
@@ -395,6 +407,7 @@ int hg_apply(hg_grid* g, const double* u, double* out, int with_A, const double*
     hg_ctx* c = g->ctx;
     DeviceGuard dg(c->device);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
+    g->form = 0;   // primal operator
     cudaStream_t s = c->stream;
     const int pr = prec == HG_MIXED ? 1 : 0;
     int st;
@@ -425,6 +438,7 @@ int hg_spectrum(hg_grid* g, const double* u, double* S_out, int prec, int on_dev
     hg_ctx* c = g->ctx;
     DeviceGuard dg(c->device);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
+    g->form = 0;   // primal operator
     cudaStream_t s = c->stream;
     const int pr = prec == HG_MIXED ? 1 : 0;
     int st;
@@ -464,9 +478,11 @@ int hg_time_pass(hg_grid* g, int prec, int pass, int reps, double* ms_out, char*
     const int np = hg_num_passes(g);
     if (pass < 0 || pass >= np) return HG_ERR_ARG;
     if (g->coeff_mode < 0) return HG_ERR_NO_COEFFS;
+    if (g->borrowed.load() > 0) return HG_ERR_BUSY;
     hg_ctx* c = g->ctx;
     DeviceGuard dg(c->device);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
+    g->form = 0;   // primal operator
     cudaStream_t s = c->stream;
     const int pr = prec == HG_MIXED ? 1 : 0;
     int st;

@@ -121,6 +121,7 @@ struct StrArgs {
     double A0[9];
     int early_stage;            // 1: twiddle/coefficient staging may precede the wait for
                                 //    the previous kernel (tables written only by copies)
+    int dual;                   // STR_GAMMA projects onto J_N (identity - mean - Gamma)
 };
 
 struct RowInvArgs {
@@ -164,6 +165,10 @@ cudaError_t launch_inner_init(const GridDev& g, int L, const double* r64, float*
 // bounds[0] = min, bounds[1] = max over the voxels of the eigenvalues of A(x_k)
 // (FP64 coefficients co64); both exact up to the eigenvalue formula's rounding
 // and independent of the reduction order.
+// A(x_k)^-1 of a packed symmetric FP64 field (component-major, order
+// 11,22[,33],12[,13,23]) into the same layout, FP64 and FP32.
+cudaError_t launch_invert_field(int d, long long M, const double* in, double* out64, float* out32,
+                                cudaStream_t s);
 cudaError_t launch_coeff_bounds(const GridDev& g, const CoeffsDev& co64, double* bounds, cudaStream_t s);
 // x64 += x32 for systems whose outer status is ACTIVE; inner iterations are
 // added to the outer totals.

@@ -217,6 +217,30 @@ __global__ void __launch_bounds__(256) k_coeff_bounds(GridDev g, CoeffsDev co,
     }
 }
 
+// Inverse of a symmetric positive definite matrix as its adjugate over its
+// determinant (cofactor expansion), per voxel of a packed field.
+template <int D>
+__global__ void __launch_bounds__(256) k_invert_field(long long M, const double* __restrict__ in,
+                                                      double* __restrict__ out64, float* __restrict__ out32) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < M;
+         k += (long long)gridDim.x * blockDim.x) {
+        if (D == 2) {
+            const double a = in[k], b = in[M + k], c = in[2 * M + k];   // a11, a22, a12
+            const double det = a * b - c * c;
+            const double r[3] = {b / det, a / det, -c / det};
+            for (int q = 0; q < 3; ++q) { out64[q * M + k] = r[q]; out32[q * M + k] = (float)r[q]; }
+        } else {
+            const double a = in[k], b = in[M + k], c = in[2 * M + k];            // a11, a22, a33
+            const double d = in[3 * M + k], e = in[4 * M + k], f = in[5 * M + k];  // a12, a13, a23
+            const double c11 = b * c - f * f, c22 = a * c - e * e, c33 = a * b - d * d;
+            const double c12 = e * f - d * c, c13 = d * f - b * e, c23 = d * e - a * f;
+            const double det = a * c11 + d * c12 + e * c13;
+            const double r[6] = {c11 / det, c22 / det, c33 / det, c12 / det, c13 / det, c23 / det};
+            for (int q = 0; q < 6; ++q) { out64[q * M + k] = r[q]; out32[q * M + k] = (float)r[q]; }
+        }
+    }
+}
+
 template <typename S, typename Dd>
 __global__ void k_convert(const S* __restrict__ src, Dd* __restrict__ dst, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -329,6 +353,14 @@ cudaError_t launch_energy(const GridDev& g, int L, const CoeffsDev& co64, const 
     unsigned nb = elem_grid(g.M);
     if (g.d == 2) k_energy<2><<<nb, 256, 0, s>>>(g, L, co64, x, loadmask, partial, counter, out);
     else          k_energy<3><<<nb, 256, 0, s>>>(g, L, co64, x, loadmask, partial, counter, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_invert_field(int d, long long M, const double* in, double* out64, float* out32,
+                                cudaStream_t s) {
+    const unsigned nb = elem_grid(M);
+    if (d == 2) k_invert_field<2><<<nb, 256, 0, s>>>(M, in, out64, out32);
+    else        k_invert_field<3><<<nb, 256, 0, s>>>(M, in, out64, out32);
     return cudaGetLastError();
 }
 

@@ -667,8 +667,22 @@ __global__ void __launch_bounds__(PassThreads<NN>::v, StridedMinBlocks<T, D, NN>
                 s.x = num.x * f;
                 s.y = num.y * f;
             }
+            if (a.dual) {
+                // onto J_N: t_hat - xi (xi . t_hat) / |xi|^2 away from k = 0, and
+                // nothing of the mean (Eq. Helmholtz_discrete)
 #pragma unroll
-            for (int al = 0; al < D; ++al) buf[sidx(al, m)] = cscale(s, xi[al]);
+                for (int al = 0; al < D; ++al) {
+                    C q = czero<T>();
+                    if (den > T(0)) {
+                        q.x = th[al].x * invM - s.x * xi[al];
+                        q.y = th[al].y * invM - s.y * xi[al];
+                    }
+                    buf[sidx(al, m)] = q;
+                }
+            } else {
+#pragma unroll
+                for (int al = 0; al < D; ++al) buf[sidx(al, m)] = cscale(s, xi[al]);
+            }
         }
         __syncthreads();
         fft_str<T, D, NN, true>(buf, Cl, lgCl, n, pl, tw, tws);

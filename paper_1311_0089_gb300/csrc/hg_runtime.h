@@ -53,6 +53,7 @@ struct GraphCache {
     int chunk = 0;
     int nkern = 0;
     int prof_pass = -1;   // pass bracketed by event records (-1: none)
+    int form = 0;         // formulation captured (coefficients and projection)
 };
 
 }  // namespace hgrt
@@ -70,9 +71,17 @@ struct hg_grid {
     uint8_t* d_phase = nullptr;
     void* d_table[2] = {nullptr, nullptr};
     void* d_field[2] = {nullptr, nullptr};
-    // eigenvalue bounds c_A, C_A of the current coefficients (Moulinec-Suquet)
-    bool bounds_ok = false;
-    double c_A = 0.0, C_A = 0.0;
+    // inverse coefficients A^-1 for the dual formulation (made on first use)
+    void* d_table_inv[2] = {nullptr, nullptr};
+    void* d_field_inv[2] = {nullptr, nullptr};
+    bool inv_ok = false;
+    // formulation the next enqueued work uses: 0 primal, 1 dual (coefficients
+    // A^-1 and the projection onto J_N); set by every entry point that enqueues
+    int form = 0;
+    // eigenvalue bounds c_A, C_A of the coefficients of each formulation
+    // (Moulinec-Suquet)
+    bool bounds_ok[2] = {false, false};
+    double c_A[2] = {0.0, 0.0}, C_A[2] = {0.0, 0.0};
     // solver state
     hgrt::Work work[2];
     double* partial = nullptr;

@@ -213,7 +213,7 @@ int sched_submit(Scheduler* S, hg_grid* g, const hg_solve_opts* opts, uint64_t* 
     if (opts) o = *opts; else hg_default_opts(&o);
     if (!(o.tol > 0.0) || o.max_iter < 1 || (o.prec != HG_FP64 && o.prec != HG_MIXED) ||
         !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 || (o.method != HG_CG && o.method != HG_MS) ||
-        !std::isfinite(o.lambda_ref))
+        !std::isfinite(o.lambda_ref) || (o.formulation != HG_PRIMAL && o.formulation != HG_DUAL))
         return HG_ERR_ARG;
     o.time_pass = -1;   // per-pass timing is a blocking-solve diagnostic
     if (g->coeff_mode < 0) return HG_ERR_NO_COEFFS;
