@@ -43,6 +43,7 @@ __all__ = [
     "inner", "ZERO_RHS", "cg", "homogenized_energy", "homogenized_flux", "solve_AH",
     "dense_gamma_matrix", "solve_lsd_dense", "moulinec_suquet",
     "apply_gamma_J", "invert_coeffs", "cg_dual", "solve_AH_dual", "solve_dual_dense",
+    "cg_ref", "solve_AH_ref",
 ]
 
 
@@ -314,19 +315,21 @@ def dense_gamma_matrix(N, Y=None, A0=None) -> np.ndarray:
     return out.real
 
 
-def solve_lsd_dense(A: np.ndarray, E: np.ndarray, N, Y=None, lam: float = 1.0) -> np.ndarray:
-    """Solve [I + Gamma_N (A_N - lam I)] e = E by LU (Eq. LSD); returns e (d, *N)."""
+def solve_lsd_dense(A: np.ndarray, E: np.ndarray, N, Y=None, lam: float = 1.0,
+                    A0: Optional[np.ndarray] = None) -> np.ndarray:
+    """Solve [I + Gamma_N (A_N - A0)] e = E by LU (Eq. LSD) with A0 = lam I, or
+    the given SPD A0; returns e (d, *N)."""
     N = check_grid(N)
     d = len(N)
     M = int(np.prod(N))
-    Gam = dense_gamma_matrix(N, Y, lam * np.eye(d))
+    A0m = lam * np.eye(d) if A0 is None else np.asarray(A0, dtype=np.float64)
+    Gam = dense_gamma_matrix(N, Y, A0m)
     Ad = np.zeros((d * M, d * M))
     Af = A.reshape(d, d, M)
     idx = np.arange(M)
     for a in range(d):
         for b in range(d):
-            Ad[a * M + idx, b * M + idx] = Af[a, b]
-    Ad -= lam * np.eye(d * M)
+            Ad[a * M + idx, b * M + idx] = Af[a, b] - A0m[a, b]
     sysm = np.eye(d * M) + Gam @ Ad
     rhs = np.repeat(np.asarray(E, dtype=np.float64), M)
     e = np.linalg.solve(sysm, rhs)
@@ -464,3 +467,67 @@ def solve_dual_dense(A: np.ndarray, S: np.ndarray, N, Y=None) -> np.ndarray:
     sysm = PJ @ Ad @ PJ + (np.eye(d * M) - PJ)
     rhs = -PJ @ (Ad @ np.repeat(np.asarray(S, dtype=np.float64), M))
     return np.linalg.solve(sysm, rhs).reshape((d,) + N)
+
+
+# ---------------------------------------------------------------------------
+# CG with a general reference medium A0 (Lemma FD_projection (ii)-(iii))
+# ---------------------------------------------------------------------------
+def cg_ref(A: np.ndarray, E: np.ndarray, N, A0: np.ndarray, Y=None, tol: float = 1e-10,
+           maxiter: int = 10000) -> Dict:
+    """The discrete Lippmann-Schwinger equation (Eq. LSD) with a general SPD
+    reference medium A0, on the fluctuation x = e - E in E_N:
+
+        Gamma_N A_N x = -Gamma_N A_N E,   Gamma_N = F^-1 Gamma_hat(A0) F,
+
+    (Gamma_N A0 x = x on E_N, since G_N = Gamma_N A0 projects onto E_N, Lemma
+    FD_projection (iii)).  By Lemma FD_projection (ii) Gamma_N is symmetric,
+    so K = Gamma_N A_N satisfies (A0 K x, y) = (A_N x, y) for x, y in E_N:
+    K is symmetric positive definite in the scalar product (u, v)_A0 =
+    (A0 u, v), and CG runs in that product.  Stops on ||r||_A0 / ||b||_A0.
+    For A0 = lam I the iterates are those of `cg`."""
+    N = check_grid(N)
+    d = len(N)
+    A0 = np.asarray(A0, dtype=np.float64)
+    K = lambda u: apply_gamma(apply_A(A, u), N, Y, A0)
+    ip = lambda u, v: inner(np.einsum("ab,b...->a...", A0, u), v)
+    Evec = np.asarray(E, dtype=np.float64).reshape((d,) + (1,) * d) * np.ones((d,) + N)
+    b = -K(Evec)
+    x = np.zeros((d,) + N)
+    r = b.copy()
+    p = r.copy()
+    rr = ip(r, r)
+    bnorm = np.sqrt(rr)
+    # zero right-hand side: ||b||_A0 <= sqrt(lmax) ||b|| <= sqrt(lmax)/lmin ||A E||
+    ev = np.linalg.eigvalsh(A0)
+    AE = apply_A(A, Evec)
+    if bnorm <= ZERO_RHS * np.sqrt(ev[-1]) / ev[0] * np.sqrt(inner(AE, AE)):
+        return {"x": x, "iters": 0, "rel_res": 0.0}
+    it, rel = 0, 1.0
+    while it < maxiter and rel > tol:
+        q = K(p)
+        alpha = rr / ip(p, q)
+        x = x + alpha * p
+        r = r - alpha * q
+        it += 1
+        rr_new = ip(r, r)
+        rel = np.sqrt(rr_new) / bnorm
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return {"x": x, "iters": it, "rel_res": rel}
+
+
+def solve_AH_ref(A: np.ndarray, N, A0: np.ndarray, Y=None, tol: float = 1e-10,
+                 maxiter: int = 10000) -> Dict:
+    """`solve_AH` with the general reference medium A0 (same A_H: the GaNi
+    solution does not depend on A0)."""
+    N = check_grid(N)
+    d = len(N)
+    es, iters, xs = [], [], []
+    for j in range(d):
+        E = np.zeros(d)
+        E[j] = 1.0
+        out = cg_ref(A, E, N, A0, Y, tol, maxiter)
+        iters.append(out["iters"])
+        xs.append(out["x"])
+        es.append(E.reshape((d,) + (1,) * d) + out["x"])
+    return {"AH": homogenized_energy(A, es), "AH_flux": homogenized_flux(A, es), "iters": iters, "x": xs}
