@@ -126,6 +126,17 @@ typedef struct {
     int formulation;     /* hg_formulation (default HG_PRIMAL); HG_DUAL needs
                             every load in loads_mask and the reference
                             medium A0 = I                                      */
+    double A0[9];        /* HG_CG, HG_PRIMAL: a general SPD reference medium
+                            (d x d row-major) for Eq. LSD.  The iteration runs
+                            on Gamma_N(A0) A_N e~ = -Gamma_N(A0) A_N E in the
+                            scalar product (A0 u, v), in which that operator
+                            is symmetric positive definite on E_N (Lemma
+                            FD_projection (ii)-(iii)); the solution, hence
+                            A_H, does not depend on A0, the iteration count
+                            does (an anisotropic A0 close to the medium's
+                            anisotropy can save many iterations).  A0[0] = 0
+                            (default): A0 = lambda_ref I.  Not SPD:
+                            HG_ERR_NOT_SPD; with HG_MS or HG_DUAL: HG_ERR_ARG */
 } hg_solve_opts;
 
 typedef struct {
@@ -136,7 +147,8 @@ typedef struct {
     int iters[3];           /* iterations per load (HG_MIXED: inner FP32
                                iterations summed over refinement steps)        */
     int outer[3];           /* HG_MIXED: FP64 residual evaluations per load    */
-    double rel_res[3];      /* final ||r|| / ||b|| (FP64 true residual for
+    double rel_res[3];      /* final ||r|| / ||b|| in the scalar product of the
+                               iteration (FP64 true residual for
                                HG_MIXED, recursive residual for HG_FP64)       */
     double device_ms;       /* time of the solve on the context stream         */
     double wall_ms;         /* host wall time of the call                      */

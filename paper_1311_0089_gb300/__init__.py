@@ -51,7 +51,8 @@ class SolveOpts(ctypes.Structure):
                 ("lambda_ref", ctypes.c_double), ("loads_mask", ctypes.c_uint),
                 ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("time_pass", ctypes.c_int),
-                ("method", ctypes.c_int), ("formulation", ctypes.c_int)]
+                ("method", ctypes.c_int), ("formulation", ctypes.c_int),
+                ("A0", ctypes.c_double * 9)]
 
 
 class Result(ctypes.Structure):
@@ -141,6 +142,9 @@ def default_opts(**kw) -> SolveOpts:
     for k, v in kw.items():
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
+        if k == "A0":   # d x d reference medium, row-major
+            flat = [float(x) for x in np.asarray(v, dtype=np.float64).ravel()]
+            v = (ctypes.c_double * 9)(*(flat + [0.0] * (9 - len(flat))))
         setattr(o, k, v)
     return o
 

@@ -312,6 +312,14 @@ int grid_alloc_common(hg_grid* g) {
     return HG_OK;
 }
 
+Weight grid_weight(const hg_grid* g) {
+    Weight w;
+    memset(&w, 0, sizeof(w));
+    w.has = g->has_ref;
+    for (int i = 0; i < 9; ++i) { w.w[i] = g->ref[i]; w.wf[i] = (float)g->ref[i]; }
+    return w;
+}
+
 CoeffsDev coeffs_for(const hg_grid* g, int prec, bool withA) {
     CoeffsDev c;
     c.phase = g->d_phase;
@@ -389,6 +397,10 @@ int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_p
     memset(&sa, 0, sizeof(sa));
     sa.early_stage = 1;
     sa.L = L; sa.S = w.S; sa.sc = w.sc; sa.check_status = 1; sa.dual = g->form;
+    if (g->has_ref) {   // Gamma_hat of the reference medium (its denominator xi . A0 xi)
+        sa.has_A0 = 1;
+        for (int i = 0; i < d * d; ++i) sa.A0[i] = g->ref[i];
+    }
     if (d == 3) {
         sa.mode = STR_FWD; sa.axis = 1; sa.outer = gd.N[0]; sa.n = gd.N[1]; sa.inner = gd.H;
         HG_CU(mark(true));
@@ -415,6 +427,7 @@ int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_p
     memset(&ia, 0, sizeof(ia));
     ia.early_stage = 1;
     ia.mode = INV_CG; ia.L = L; ia.S = w.S; ia.x = w.x; ia.r = w.r; ia.p = w.p;
+    ia.W = grid_weight(g);
     ia.sc = w.sc; ia.partial = g->partial; ia.counter = g->counters + 1; ia.check_status = 1;
     HG_CU(mark(true));
     HG_CU(launch_row_inv(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], ia, s));
@@ -429,6 +442,10 @@ int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, 
                    const double* A0dev, const double* A0host, int inv_mode, void* out,
                    int check_status, cudaStream_t s, Scalars* status_sc) {
     const GridDev& gd = g->gd;
+    // the right-hand side and the residual of the iteration use its reference
+    // medium; projections (INV_PROJ) stay orthogonal
+    const bool iter_op = inv_mode == INV_RHS || inv_mode == INV_RESID;
+    if (iter_op && g->has_ref && !A0host) A0host = g->ref;
     Work& w = g->work[prec];
     Scalars* sc = status_sc ? status_sc : w.sc;
     const int last = gd.d - 1;
@@ -450,6 +467,7 @@ int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, 
     memset(&ia, 0, sizeof(ia));
     ia.early_stage = 1;
     ia.mode = inv_mode; ia.L = L; ia.S = w.S; ia.x = w.x; ia.r = w.r; ia.p = w.p; ia.out = out;
+    if (iter_op) ia.W = grid_weight(g);
     ia.sc = sc; ia.partial = g->partial; ia.counter = g->counters + 3; ia.check_status = check_status;
     HG_CU(launch_row_inv(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], ia, s));
     g->ctx->launches++;
@@ -459,7 +477,8 @@ int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, 
 // A CUDA graph of `chunk` CG iterations, cached per precision.
 int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nkern, int prof_pass) {
     GraphCache& gc = g->graphs[prec];
-    if (gc.exec && gc.chunk == chunk && gc.prof_pass == prof_pass && gc.form == g->form) {
+    if (gc.exec && gc.chunk == chunk && gc.prof_pass == prof_pass && gc.form == g->form &&
+        gc.has_ref == g->has_ref && (!g->has_ref || memcmp(gc.ref, g->ref, sizeof(gc.ref)) == 0)) {
         *out = gc.exec;
         *nkern = gc.nkern;
         return HG_OK;
@@ -495,6 +514,8 @@ int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nke
     gc.chunk = chunk;
     gc.prof_pass = prof_pass;
     gc.form = g->form;
+    gc.has_ref = g->has_ref;
+    memcpy(gc.ref, g->ref, sizeof(gc.ref));
     gc.nkern = (int)nk;
     *out = gc.exec;
     *nkern = gc.nkern;
@@ -566,7 +587,8 @@ static int job_start_inner(Job& j) {
     const GridDev& gd = g->gd;
     HG_CU(launch_inner_init(gd, gd.d, (const double*)g->work[0].r, (float*)g->work[1].r,
                             (float*)g->work[1].p, (float*)g->work[1].x, g->work[0].sc, g->work[1].sc,
-                            j.o.inner_tol, j.o.max_iter, j.stall_max, g->partial, g->counters + 4, j.s));
+                            j.o.inner_tol, j.o.max_iter, j.stall_max, grid_weight(g), g->partial,
+                            g->counters + 4, j.s));
     g->ctx->launches++;
     j.launched = 0;
     j.prof_prev_iters = 0;
@@ -585,6 +607,38 @@ static int job_finish_enqueue(Job& j) {
     HG_CU(cudaMemcpyAsync(g->h_AH, g->d_AH, sizeof(double) * 2 * gd.d * gd.d, cudaMemcpyDeviceToHost, j.s));
     j.phase = Job::FINAL;
     return job_tick_copy(j, 0);
+}
+
+// Eigenvalues of a symmetric d x d matrix (row-major) by cyclic Jacobi
+// rotations (Golub and Van Loan, Sec. 8.5).
+static void sym_eig_host(const double* m, int d, double* ev) {
+    double a[3][3];
+    for (int i = 0; i < d; ++i)
+        for (int k = 0; k < d; ++k) a[i][k] = m[i * d + k];
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < d; ++p)
+            for (int q = p + 1; q < d; ++q) off += std::fabs(a[p][q]);
+        if (off == 0.0) break;
+        for (int p = 0; p < d - 1; ++p)
+            for (int q = p + 1; q < d; ++q) {
+                const double apq = a[p][q];
+                if (apq == 0.0) continue;
+                const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                a[p][p] -= t * apq;
+                a[q][q] += t * apq;
+                a[p][q] = a[q][p] = 0.0;
+                for (int r = 0; r < d; ++r) {
+                    if (r == p || r == q) continue;
+                    const double arp = a[r][p], arq = a[r][q];
+                    a[r][p] = a[p][r] = c * arp - sn * arq;
+                    a[r][q] = a[q][r] = sn * arp + c * arq;
+                }
+            }
+    }
+    for (int i = 0; i < d; ++i) ev[i] = a[i][i];
 }
 
 // A(x_k)^-1 for the dual formulation, made once per coefficient set: phase
@@ -687,7 +741,7 @@ static int job_start_rhs(Job& j, bool fp32) {
     int init_st[MAXL];
     for (int l = 0; l < MAXL; ++l) init_st[l] = (l < L && ((j.o.loads_mask >> l) & 1u)) ? ST_ACTIVE : ST_IDLE;
     HG_CU(launch_init_scalars(g->work[0].sc, L, init_st, j.o.tol, j.prec ? j.o.max_outer : j.o.max_iter,
-                              j.fixed_alpha, j.s));
+                              j.fixed_alpha, j.zscale, j.s));
     g->ctx->launches++;
     j.launched = 0;
     j.prof_prev_iters = 0;
@@ -706,7 +760,8 @@ static int job_start_rhs(Job& j, bool fp32) {
                              g->work[0].sc)))
         return st;
     HG_CU(launch_inner_init(gd, L, nullptr, nullptr, nullptr, nullptr, g->work[0].sc, g->work[1].sc,
-                            j.o.inner_tol, j.o.max_iter, j.stall_max, g->partial, g->counters + 4, j.s));
+                            j.o.inner_tol, j.o.max_iter, j.stall_max, grid_weight(g), g->partial,
+                            g->counters + 4, j.s));
     g->ctx->launches++;
     j.phase = Job::INNER;
     return job_launch_chunk(j, 1);
@@ -733,6 +788,16 @@ int job_begin(Job& j) {
     if ((st = grid_alloc_work(g, 0))) return st;
     if (j.prec == 1 && (st = grid_alloc_work(g, 1))) return st;
     g->form = j.o.formulation == HG_DUAL ? 1 : 0;
+    g->has_ref = j.o.A0[0] != 0.0 ? 1 : 0;
+    j.zscale = 1.0;
+    for (int i = 0; i < 9; ++i) g->ref[i] = g->has_ref && i < gd.d * gd.d ? j.o.A0[i] : 0.0;
+    if (g->has_ref) {
+        // ||b||_A0 <= sqrt(lmax(A0)) / lmin(A0) ||A E|| (reading of the zero test)
+        double ev[3];
+        sym_eig_host(g->ref, gd.d, ev);
+        const double lmin = *std::min_element(ev, ev + gd.d), lmax = *std::max_element(ev, ev + gd.d);
+        j.zscale = std::sqrt(lmax) / lmin;
+    }
     if (g->form) {
         if ((j.o.loads_mask & ((1u << L) - 1u)) != ((1u << L) - 1u)) return HG_ERR_ARG;
         if ((st = grid_ensure_inverse(g, j.s))) return st;

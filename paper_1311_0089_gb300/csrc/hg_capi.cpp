@@ -87,6 +87,22 @@ struct DeviceGuard {
 
 }  // namespace
 
+namespace hgrt {
+// Options of hg_solve_AH and hg_submit.  Normalises loads_mask to the grid.
+int validate_solve_opts(const hg_grid* g, hg_solve_opts* o) {
+    if (!(o->tol > 0.0) || o->max_iter < 1 || (o->prec != HG_FP64 && o->prec != HG_MIXED) ||
+        !(o->inner_tol > 0.0) || o->inner_tol >= 1.0 || (o->method != HG_CG && o->method != HG_MS) ||
+        !std::isfinite(o->lambda_ref) || (o->formulation != HG_PRIMAL && o->formulation != HG_DUAL))
+        return HG_ERR_ARG;
+    if (o->A0[0] != 0.0) {
+        if (o->method != HG_CG || o->formulation != HG_PRIMAL) return HG_ERR_ARG;
+        if (!is_spd(o->A0, g->gd.d)) return HG_ERR_NOT_SPD;
+    }
+    o->loads_mask &= (1u << g->gd.d) - 1u;
+    return HG_OK;
+}
+}  // namespace hgrt
+
 extern "C" {
 
 void hg_default_opts(hg_solve_opts* o) {
@@ -102,6 +118,7 @@ void hg_default_opts(hg_solve_opts* o) {
     o->time_pass = -1;
     o->method = HG_CG;
     o->formulation = HG_PRIMAL;
+    for (int i = 0; i < 9; ++i) o->A0[i] = 0.0;
 }
 
 const char* hg_strerror(int s) {
@@ -370,13 +387,10 @@ int hg_solve_AH(hg_grid* g, const hg_solve_opts* opts, double* AH_out, hg_result
     if (!g) return HG_ERR_ARG;
     hg_solve_opts o;
     if (opts) o = *opts; else hg_default_opts(&o);
-    if (!(o.tol > 0.0) || o.max_iter < 1 || (o.prec != HG_FP64 && o.prec != HG_MIXED) ||
-        !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 || (o.method != HG_CG && o.method != HG_MS) ||
-        !std::isfinite(o.lambda_ref) || (o.formulation != HG_PRIMAL && o.formulation != HG_DUAL))
-        return HG_ERR_ARG;
+    const int vst = validate_solve_opts(g, &o);
+    if (vst) return vst;
     if (o.time_pass >= hg_num_passes(g) || (o.time_pass >= 0 && o.check_every > hgrt::MAX_PROF_CHUNK))
         return HG_ERR_ARG;
-    o.loads_mask &= (1u << g->gd.d) - 1u;
     if (g->borrowed.load() > 0) return HG_ERR_BUSY;
     hg_ctx* c = g->ctx;
     DeviceGuard dg(c->device);
@@ -408,6 +422,7 @@ int hg_apply(hg_grid* g, const double* u, double* out, int with_A, const double*
     DeviceGuard dg(c->device);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     g->form = 0;   // primal operator
+    g->has_ref = 0;  // reference medium I
     cudaStream_t s = c->stream;
     const int pr = prec == HG_MIXED ? 1 : 0;
     int st;
@@ -439,6 +454,7 @@ int hg_spectrum(hg_grid* g, const double* u, double* S_out, int prec, int on_dev
     DeviceGuard dg(c->device);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     g->form = 0;   // primal operator
+    g->has_ref = 0;  // reference medium I
     cudaStream_t s = c->stream;
     const int pr = prec == HG_MIXED ? 1 : 0;
     int st;
@@ -483,6 +499,7 @@ int hg_time_pass(hg_grid* g, int prec, int pass, int reps, double* ms_out, char*
     DeviceGuard dg(c->device);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     g->form = 0;   // primal operator
+    g->has_ref = 0;  // reference medium I
     cudaStream_t s = c->stream;
     const int pr = prec == HG_MIXED ? 1 : 0;
     int st;

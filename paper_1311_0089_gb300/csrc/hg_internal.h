@@ -46,6 +46,16 @@ struct Scalars {
     int stall_max;   // > 0: stop (ST_STAGNATED) after this many such iterations
     double fixed_alpha;  // > 0: Moulinec-Suquet step 1/lambda in place of CG's
                          // alpha, beta = 0, stop on the step just taken
+    double zscale;       // zero right-hand-side test: ||b|| <= ZERO_RHS zscale ||A E||
+                         // (sqrt(lmax(A0)) / lmin(A0) for a general reference medium)
+};
+
+// Scalar product of the iteration: (W u, v) with a constant SPD d x d W
+// (the reference medium A0), or the plain one when has = 0.
+struct Weight {
+    int has;
+    double w[9];
+    float wf[9];
 };
 
 struct GridDev {
@@ -138,6 +148,7 @@ struct RowInvArgs {
     int check_status;
     int early_stage;            // 1: twiddle/coefficient staging may precede the wait for
                                 //    the previous kernel (tables written only by copies)
+    Weight W;                   // (r, r) of INV_CG / INV_RHS / INV_RESID in the product (W r, r)
 };
 
 // Launchers (prec: 0 = double, 1 = float).  Return cudaGetLastError().
@@ -151,7 +162,7 @@ cudaError_t launch_row_inv(int prec, const GridDev& g, const AxisPlanH& pl, cons
 // Small helpers.
 // fixed_alpha > 0 selects the Moulinec-Suquet update with step fixed_alpha.
 cudaError_t launch_init_scalars(Scalars* sc, int L, const int* status_init, double tol,
-                                int max_iter, double fixed_alpha, cudaStream_t s);
+                                int max_iter, double fixed_alpha, double zscale, cudaStream_t s);
 // Mixed precision: r32 = (float) r64, p32 = r32, x32 = 0, inner scalars from
 // the outer status (and its fixed step); reduction of (r32, r32).  An inner
 // solve stops (STAGNATED) after stall_max iterations without a 4x drop of (r, r).
@@ -160,8 +171,8 @@ cudaError_t launch_init_scalars(Scalars* sc, int L, const int* status_init, doub
 // set (one block).
 cudaError_t launch_inner_init(const GridDev& g, int L, const double* r64, float* r32, float* p32,
                               float* x32, const Scalars* outer, Scalars* inner, double inner_tol,
-                              int inner_max, int stall_max, double* partial, unsigned* counter,
-                              cudaStream_t s);
+                              int inner_max, int stall_max, const Weight& W, double* partial,
+                              unsigned* counter, cudaStream_t s);
 // bounds[0] = min, bounds[1] = max over the voxels of the eigenvalues of A(x_k)
 // (FP64 coefficients co64); both exact up to the eigenvalue formula's rounding
 // and independent of the reduction order.

@@ -9,13 +9,14 @@ namespace hgk {
 // helpers: scalars init, mixed-precision refinement, A_H, conversions
 // ---------------------------------------------------------------------------
 __global__ void k_init_scalars(Scalars* sc, int L, int s0, int s1, int s2, double tol, int max_iter,
-                               double fixed_alpha) {
+                               double fixed_alpha, double zscale) {
     const int l = threadIdx.x;
     if (l >= L) return;
     Scalars s;
     s.rr = 0; s.pt = 0; s.alpha = 0; s.beta = 0; s.bnorm = 0; s.aen = 0; s.relres = 1.0;
     s.alpha_f = 0.f; s.beta_f = 0.f; s.best_rr = 0.0; s.stall = 0; s.stall_max = 0;
     s.fixed_alpha = fixed_alpha;
+    s.zscale = zscale;
     s.tol = tol; s.iters = 0; s.max_iter = max_iter; s.total_iters = 0;
     s.status = (l == 0) ? s0 : (l == 1) ? s1 : s2;
     sc[l] = s;
@@ -26,24 +27,43 @@ __global__ void __launch_bounds__(256) k_inner_init(GridDev g, int L, const doub
                                                     float* __restrict__ r32, float* __restrict__ p32,
                                                     float* __restrict__ x32, const Scalars* __restrict__ outer,
                                                     Scalars* inner, double inner_tol, int inner_max,
-                                                    int stall_max, double* partial, unsigned* counter) {
+                                                    int stall_max, Weight W, double* partial,
+                                                    unsigned* counter) {
     const long long M = g.M;
-    const long long n = (long long)L * D * M;
+    const long long n = (long long)L * M;
     double acc[MAXL] = {0.0, 0.0, 0.0};
     bool act[MAXL];
     for (int l = 0; l < MAXL; ++l) act[l] = (l < L) && outer[l].status == ST_ACTIVE;
     double tot[MAXL];
     if (r64) {
+        // one voxel of one load per step: the D components together for (W r, r)
         for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
              idx += (long long)gridDim.x * blockDim.x) {
-            const int l = (int)(idx / (D * M));
+            const int l = (int)(idx / M);
             if (!act[l]) continue;
-            const float v = (float)r64[idx];
-            r32[idx] = v;
-            p32[idx] = v;
-            x32[idx] = 0.f;
-            const double dv = (double)v;
-            if (l == 0) acc[0] += dv * dv; else if (l == 1) acc[1] += dv * dv; else acc[2] += dv * dv;
+            const long long k = idx - (long long)l * M;
+            double v[D];
+#pragma unroll
+            for (int al = 0; al < D; ++al) {
+                const long long o = ((long long)l * D + al) * M + k;
+                const float f = (float)r64[o];
+                r32[o] = f;
+                p32[o] = f;
+                x32[o] = 0.f;
+                v[al] = (double)f;
+            }
+            double q = 0.0;
+#pragma unroll
+            for (int al = 0; al < D; ++al) {
+                double wv = v[al];
+                if (W.has) {
+                    wv = 0.0;
+#pragma unroll
+                    for (int be = 0; be < D; ++be) wv += W.w[al * D + be] * v[be];
+                }
+                q += v[al] * wv;
+            }
+            if (l == 0) acc[0] += q; else if (l == 1) acc[1] += q; else acc[2] += q;
         }
         block_sum<MAXL>(acc);
         int slots[MAXL] = {0, 1, 2};
@@ -66,6 +86,7 @@ __global__ void __launch_bounds__(256) k_inner_init(GridDev g, int L, const doub
             // refinement decides whether another inner solve is needed
             s.best_rr = s.rr; s.stall = 0; s.stall_max = stall_max;
             s.fixed_alpha = outer[l].fixed_alpha;
+            s.zscale = outer[l].zscale;
             s.bnorm = sqrt(s.rr); s.aen = 0; s.relres = 1.0; s.tol = itol;
             s.iters = 0; s.max_iter = inner_max; s.total_iters = 0;
             s.status = act[l] ? (s.rr > 0.0 ? ST_ACTIVE : ST_CONVERGED)
@@ -311,9 +332,9 @@ cudaError_t launch_row_inv(int prec, const GridDev& g, const AxisPlanH& pl, cons
 }
 
 cudaError_t launch_init_scalars(Scalars* sc, int L, const int* st, double tol, int max_iter,
-                                double fixed_alpha, cudaStream_t s) {
+                                double fixed_alpha, double zscale, cudaStream_t s) {
     k_init_scalars<<<1, 32, 0, s>>>(sc, L, st[0], L > 1 ? st[1] : ST_IDLE, L > 2 ? st[2] : ST_IDLE,
-                                    tol, max_iter, fixed_alpha);
+                                    tol, max_iter, fixed_alpha, zscale);
     return cudaGetLastError();
 }
 
@@ -327,15 +348,15 @@ static unsigned elem_grid(long long n) {
 
 cudaError_t launch_inner_init(const GridDev& g, int L, const double* r64, float* r32, float* p32,
                               float* x32, const Scalars* outer, Scalars* inner, double inner_tol,
-                              int inner_max, int stall_max, double* partial, unsigned* counter,
-                              cudaStream_t s) {
-    unsigned nb = r64 ? elem_grid((long long)L * g.d * g.M) : 1u;
+                              int inner_max, int stall_max, const Weight& W, double* partial,
+                              unsigned* counter, cudaStream_t s) {
+    unsigned nb = r64 ? elem_grid((long long)L * g.M) : 1u;
     if (g.d == 2)
         k_inner_init<2><<<nb, 256, 0, s>>>(g, L, r64, r32, p32, x32, outer, inner, inner_tol, inner_max,
-                                           stall_max, partial, counter);
+                                           stall_max, W, partial, counter);
     else
         k_inner_init<3><<<nb, 256, 0, s>>>(g, L, r64, r32, p32, x32, outer, inner, inner_tol, inner_max,
-                                           stall_max, partial, counter);
+                                           stall_max, W, partial, counter);
     return cudaGetLastError();
 }
 

@@ -276,6 +276,8 @@ __device__ __forceinline__ void fft_str(Cx<T>* buf, int Cl, int lgCl, int n, con
     else fft_pencils<T, INV, MAXB>(buf, D * Cl, n, pl, twg);
 }
 
+__device__ __forceinline__ float weight_of(const Weight& w, int i, float) { return w.wf[i]; }
+__device__ __forceinline__ double weight_of(const Weight& w, int i, double) { return w.w[i]; }
 __device__ __forceinline__ float load_of(const RowFwdArgs& a, int i, float) { return a.Ef[i]; }
 __device__ __forceinline__ double load_of(const RowFwdArgs& a, int i, double) { return a.Ed[i]; }
 
@@ -798,6 +800,9 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
         alpha_t[li] = li < nl ? s_alpha[li] : T(0);
     }
     T tacc[MAXL] = {T(0), T(0), T(0)};
+    T Wt[D * D];
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) Wt[i] = weight_of(a.W, i, T());
     constexpr int UNR = D == 2 ? 2 : 1;
     const int total = nrow * Nl;
     const bool cgm = a.mode == INV_CG;
@@ -832,32 +837,42 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
             for (int li = 0; li < D; ++li) {
                 if (li >= nl) break;
                 if (!act[li]) continue;
+                T rn[D];
 #pragma unroll
                 for (int al = 0; al < D; ++al) {
                     const int rr = (rowi * nl + li) * D + al;
                     const C z = buf[(rr >> 1) * Nl + i];
                     const T q = (rr & 1) ? z.y : z.x;
                     const size_t o = (size_t)(li * D + al) * Mu + e;
+                    rn[al] = T(0);
                     if (cgm) {
                         Xt[o] = xv[u][li][al] + alpha_t[li] * pv[u][li][al];
-                        const T rnew = rv0[u][li][al] - alpha_t[li] * q;
-                        Rt[o] = rnew;
-                        tacc[li] += rnew * rnew;
+                        rn[al] = rv0[u][li][al] - alpha_t[li] * q;
+                        Rt[o] = rn[al];
                     } else if (a.mode == INV_RHS) {
-                        const T rnew = -q;
-                        Rt[o] = rnew;
-                        Pt[o] = rnew;
+                        rn[al] = -q;
+                        Rt[o] = rn[al];
+                        Pt[o] = rn[al];
                         Xt[o] = T(0);
-                        tacc[li] += rnew * rnew;
                     } else if (a.mode == INV_RESID) {
-                        const T rnew = -q;
-                        Rt[o] = rnew;
-                        tacc[li] += rnew * rnew;
+                        rn[al] = -q;
+                        Rt[o] = rn[al];
                     } else if (a.mode == INV_PROJ) {
                         Xt[o] = q;             // x <- Gamma x
                     } else {
                         Ot[o] = q;
                     }
+                }
+                // (r, r) in the scalar product of the iteration, (W r, r)
+#pragma unroll
+                for (int al = 0; al < D; ++al) {
+                    T wr = rn[al];
+                    if (a.W.has) {
+                        wr = T(0);
+#pragma unroll
+                        for (int be = 0; be < D; ++be) wr += Wt[al * D + be] * rn[be];
+                    }
+                    tacc[li] += rn[al] * wr;
                 }
             }
         }
@@ -912,10 +927,12 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
                 // b = -G A E vanishes in exact arithmetic when A E is constant
                 // along every direction G keeps (G kills constants, Lemma
                 // FD_projection (iv)); ||b|| <= ||A E|| since G is an
-                // orthogonal projection, so a ratio at roundoff level is zero.
-                if (sizeof(T) == 4 && !(s.bnorm > RHS32_RECHECK * s.aen)) {
+                // orthogonal projection (zscale = 1; for a general reference
+                // medium ||b||_A0 <= sqrt(lmax) / lmin ||A E|| = zscale ||A E||),
+                // so a ratio at roundoff level is zero.
+                if (sizeof(T) == 4 && !(s.bnorm > RHS32_RECHECK * s.zscale * s.aen)) {
                     s.status = ST_RHS_RECHECK;
-                } else if (!(s.bnorm > ZERO_RHS * s.aen)) {
+                } else if (!(s.bnorm > ZERO_RHS * s.zscale * s.aen)) {
                     s.status = ST_ZERO_RHS;
                     s.relres = 0.0;
                 } else if (s.fixed_alpha > 0.0) {

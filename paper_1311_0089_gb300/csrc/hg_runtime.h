@@ -54,6 +54,8 @@ struct GraphCache {
     int nkern = 0;
     int prof_pass = -1;   // pass bracketed by event records (-1: none)
     int form = 0;         // formulation captured (coefficients and projection)
+    int has_ref = 0;      // general reference medium captured, and its value
+    double ref[9] = {0};
 };
 
 }  // namespace hgrt
@@ -78,6 +80,10 @@ struct hg_grid {
     // formulation the next enqueued work uses: 0 primal, 1 dual (coefficients
     // A^-1 and the projection onto J_N); set by every entry point that enqueues
     int form = 0;
+    // general reference medium A0 of the next enqueued CG work (0: A0 = I); set
+    // like `form`
+    int has_ref = 0;
+    double ref[9] = {0};
     // eigenvalue bounds c_A, C_A of the coefficients of each formulation
     // (Moulinec-Suquet)
     bool bounds_ok[2] = {false, false};
@@ -139,6 +145,7 @@ struct Job {
     double t0 = 0.0;
     hg_result res{};
     double fixed_alpha = 0.0;   // Moulinec-Suquet: 1 / lambda (0: CG)
+    double zscale = 1.0;        // scale of the zero right-hand-side test
     double lambda = 0.0;
     int stall_max = 64;         // inner FP32 solves: iterations without a 4x drop
     int prof_prev_iters = 0;    // time_pass: iterations done before the chunk in flight
@@ -152,6 +159,8 @@ void grid_free_work(hg_grid* g);
 // `keep`); returns the bytes released.  Caller holds ctx->mu.
 size_t ctx_reclaim(hg_ctx* ctx, hg_grid* keep);
 int solve_impl(hg_grid* g, const hg_solve_opts* o, double* AH_out, hg_result* info);
+int validate_solve_opts(const hg_grid* g, hg_solve_opts* o);
+hgk::Weight grid_weight(const hg_grid* g);   // the scalar product of the iteration
 
 // scheduler (hg_sched.cpp)
 Scheduler* sched_create(hg_ctx* ctx);

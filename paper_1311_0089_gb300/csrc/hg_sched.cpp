@@ -211,13 +211,10 @@ void sched_destroy(Scheduler* S) {
 int sched_submit(Scheduler* S, hg_grid* g, const hg_solve_opts* opts, uint64_t* ticket) {
     hg_solve_opts o;
     if (opts) o = *opts; else hg_default_opts(&o);
-    if (!(o.tol > 0.0) || o.max_iter < 1 || (o.prec != HG_FP64 && o.prec != HG_MIXED) ||
-        !(o.inner_tol > 0.0) || o.inner_tol >= 1.0 || (o.method != HG_CG && o.method != HG_MS) ||
-        !std::isfinite(o.lambda_ref) || (o.formulation != HG_PRIMAL && o.formulation != HG_DUAL))
-        return HG_ERR_ARG;
+    const int vst = validate_solve_opts(g, &o);
+    if (vst) return vst;
     o.time_pass = -1;   // per-pass timing is a blocking-solve diagnostic
     if (g->coeff_mode < 0) return HG_ERR_NO_COEFFS;
-    o.loads_mask &= (1u << g->gd.d) - 1u;
     int expect = 0;
     if (!g->borrowed.compare_exchange_strong(expect, 1)) return HG_ERR_BUSY;
     std::unique_ptr<Ticket> t(new Ticket());
