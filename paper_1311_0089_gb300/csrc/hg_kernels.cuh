@@ -250,12 +250,25 @@ __device__ __forceinline__ Cx<T>* stage_twiddles(Cx<T>* smem_after, const AxisPl
 }
 
 template <int NN> struct PassThreads { static constexpr int v = NN > 0 ? CT_THREADS : MAXT; };
+
+// The tile a pass body works on (the CTA's block index in a plain launch) and
+// the number of tiles in x and y (the grid of a plain launch).
+struct TileIdx {
+    int x, y, z, nx, ny;
+    __device__ static TileIdx of_block() {
+        TileIdx t;
+        t.x = blockIdx.x; t.y = blockIdx.y; t.z = blockIdx.z; t.nx = gridDim.x; t.ny = gridDim.y;
+        return t;
+    }
+};
 // CTAs per SM the compiler must fit: the FP32 3D strided passes of lengths 45,
 // 81 and 135 run 6 (at most 42 registers) where they would take 4 at their
 // natural 54, which keeps more tile loads in flight (10-15% faster on 135^3);
-// other lengths would spill under that bound.
+// other lengths would spill under that bound.  The FP32 2D passes keep 3 (at
+// most 85 registers), the residency their one-wave grids are sized for.
 template <typename T, int D, int NN> struct StridedMinBlocks {
-    static constexpr int v = (D == 3 && sizeof(T) == 4 && (NN == 45 || NN == 81 || NN == 135)) ? 6 : 1;
+    static constexpr int v = (D == 3 && sizeof(T) == 4 && (NN == 45 || NN == 81 || NN == 135)) ? 6
+                             : (D == 2 && sizeof(T) == 4 && NN > 0) ? 3 : 1;
 };
 
 // Programmatic dependent launch: the pass kernels are launched so that their
@@ -319,18 +332,17 @@ __device__ __forceinline__ void row_offsets(long long* s_off, int nreal, int nl,
 // last-axis forward pass (prologue + real-to-complex DFT)
 // ---------------------------------------------------------------------------
 template <typename T, int D, int NN>
-__global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisPlanH pl,
-                                                               const Cx<T>* __restrict__ tw,
-                                                               RowFwdArgs a, int RB, int LB) {
+__device__ __forceinline__ void row_fwd_body(GridDev g, AxisPlanH pl, const Cx<T>* __restrict__ tw,
+                                             RowFwdArgs a, int RB, int LB, TileIdx ti) {
     typedef Cx<T> C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int Nl = NN > 0 ? NN : g.Nl;
     const int H = (Nl + 1) >> 1;
     const long long M = g.M, rows = g.rows;
-    const long long row0 = (long long)blockIdx.x * RB;
+    const long long row0 = (long long)ti.x * RB;
     const int nrow = (int)min((long long)RB, rows - row0);
-    const int l0 = blockIdx.y * LB;
+    const int l0 = ti.y * LB;
     const int nl = min(LB, a.L - l0);
     const int nreal = RB * nl * D;
     const int ncplx = (nreal + 1) >> 1;
@@ -499,11 +511,11 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
     // reductions
     double acc[MAXL];
     block_sum_t<T, MAXL>(tacc, acc);
-    const long long nbx = gridDim.x;
-    const unsigned nblocks = gridDim.x * gridDim.y;
+    const long long nbx = ti.nx;
+    const unsigned nblocks = ti.nx * ti.ny;
     int slots[MAXL];
     for (int li = 0; li < nl; ++li) slots[li] = l0 + li;
-    const bool last = publish(acc, slots, nl, a.partial, nbx, blockIdx.x, a.counter, nblocks);
+    const bool last = publish(acc, slots, nl, a.partial, nbx, ti.x, a.counter, nblocks);
     if (!last) return;
     double tot[MAXL];
     final_sums<MAXL, T>(a.partial, nbx, nbx, a.L, tot);
@@ -536,19 +548,26 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
     }
 }
 
+template <typename T, int D, int NN>
+__global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisPlanH pl,
+                                                               const Cx<T>* __restrict__ tw,
+                                                               RowFwdArgs a, int RB, int LB) {
+    row_fwd_body<T, D, NN>(g, pl, tw, a, RB, LB, TileIdx::of_block());
+}
+
+
 // ---------------------------------------------------------------------------
 // strided-axis pass (complex DFT along one axis; Fourier projection on axis 0)
 // ---------------------------------------------------------------------------
 template <typename T, int D, int NN>
-__global__ void __launch_bounds__(PassThreads<NN>::v, StridedMinBlocks<T, D, NN>::v) k_strided(GridDev g, AxisPlanH pl,
-                                                               const Cx<T>* __restrict__ tw,
-                                                               StrArgs a, int Cl) {
+__device__ __forceinline__ void strided_body(GridDev g, AxisPlanH pl, const Cx<T>* __restrict__ tw,
+                                             StrArgs a, int Cl, TileIdx ti) {
     typedef Cx<T> C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
-    const long long i0 = (long long)blockIdx.x * Cl;
-    const long long o = blockIdx.y;
-    const int l = blockIdx.z;
+    const long long i0 = (long long)ti.x * Cl;
+    const long long o = ti.y;
+    const int l = ti.z;
     const int n = NN > 0 ? NN : a.n;
     const int inner = (int)a.inner;
     if (!a.early_stage) grid_dep_wait();
@@ -703,22 +722,29 @@ __global__ void __launch_bounds__(PassThreads<NN>::v, StridedMinBlocks<T, D, NN>
     }
 }
 
+template <typename T, int D, int NN>
+__global__ void __launch_bounds__(PassThreads<NN>::v, StridedMinBlocks<T, D, NN>::v) k_strided(GridDev g, AxisPlanH pl,
+                                                               const Cx<T>* __restrict__ tw,
+                                                               StrArgs a, int Cl) {
+    strided_body<T, D, NN>(g, pl, tw, a, Cl, TileIdx::of_block());
+}
+
+
 // ---------------------------------------------------------------------------
 // last-axis inverse pass (complex-to-real DFT + CG update)
 // ---------------------------------------------------------------------------
 template <typename T, int D, int NN>
-__global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisPlanH pl,
-                                                               const Cx<T>* __restrict__ tw,
-                                                               RowInvArgs a, int RB, int LB) {
+__device__ __forceinline__ void row_inv_body(GridDev g, AxisPlanH pl, const Cx<T>* __restrict__ tw,
+                                             RowInvArgs a, int RB, int LB, TileIdx ti) {
     typedef Cx<T> C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int Nl = NN > 0 ? NN : g.Nl;
     const int H = (Nl + 1) >> 1;
     const long long M = g.M, rows = g.rows;
-    const long long row0 = (long long)blockIdx.x * RB;
+    const long long row0 = (long long)ti.x * RB;
     const int nrow = (int)min((long long)RB, rows - row0);
-    const int l0 = blockIdx.y * LB;
+    const int l0 = ti.y * LB;
     const int nl = min(LB, a.L - l0);
     const int nreal = RB * nl * D;
     const int ncplx = (nreal + 1) >> 1;
@@ -881,11 +907,11 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
     if (a.mode == INV_OUT || a.mode == INV_PROJ) return;
     double acc[MAXL];
     block_sum_t<T, MAXL>(tacc, acc);
-    const long long nbx = gridDim.x;
-    const unsigned nblocks = gridDim.x * gridDim.y;
+    const long long nbx = ti.nx;
+    const unsigned nblocks = ti.nx * ti.ny;
     int slots[MAXL];
     for (int li = 0; li < nl; ++li) slots[li] = l0 + li;
-    const bool last = publish(acc, slots, nl, a.partial, nbx, blockIdx.x, a.counter, nblocks);
+    const bool last = publish(acc, slots, nl, a.partial, nbx, ti.x, a.counter, nblocks);
     if (!last) return;
     double tot[MAXL];
     final_sums<MAXL, T>(a.partial, nbx, nbx, a.L, tot);
@@ -950,6 +976,14 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
         *a.counter = 0u;
     }
 }
+
+template <typename T, int D, int NN>
+__global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisPlanH pl,
+                                                               const Cx<T>* __restrict__ tw,
+                                                               RowInvArgs a, int RB, int LB) {
+    row_inv_body<T, D, NN>(g, pl, tw, a, RB, LB, TileIdx::of_block());
+}
+
 
 // ---------------------------------------------------------------------------
 // per-precision launch dispatch (hg_kernels_f32.cu / hg_kernels_f64.cu)
