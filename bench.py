@@ -257,6 +257,19 @@ def dist_env():
     return ws, rank, lrank
 
 
+def aggregate_replicas(t_local_s, units_local, dist=None, device=None):
+    """Whole-job figures of N independent replicas (one per GPU, no data-path
+    exchange): the slowest rank's time and the units all ranks processed."""
+    if dist is None or not dist.is_initialized():
+        return t_local_s, float(units_local)
+    import torch
+    t = torch.tensor([float(t_local_s)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -356,15 +369,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     t_total = sum(times) / 1e3
-    tmax = t_total
-    vox_all = vox
-    if dist:
-        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tmax = float(tt.item())
-        vv = torch.tensor([float(vox)], device=dev, dtype=torch.float64)
-        dist.all_reduce(vv, op=dist.ReduceOp.SUM)
-        vox_all = float(vv.item())
+    tmax, vox_all = aggregate_replicas(t_total, vox, dist, dev)
     value = vox_all / tmax
     solves_per_s = ws * args.steps / tmax
     last = results[-1]
