@@ -200,6 +200,17 @@ int hg_set_coeffs_phase(hg_grid* grid, const uint8_t* phase, int n_phases,
  * NULL (d*d doubles, row-major); info may be NULL. */
 int hg_solve_AH(hg_grid* grid, const hg_solve_opts* opts, double* AH_out, hg_result* info);
 
+/* Batched blocking solve of n problems of one grid shape (same d, N and Y; each
+ * grid with its own coefficients): every pass of the iteration is one launch for
+ * all problems (the launch's z index picks the problem), the CG iterations of
+ * the batch are captured check_every at a time in one CUDA graph, and each
+ * problem keeps its own convergence status, so converged problems drop out of
+ * the launches.  results[p] (n entries) is the result of grids[p]; device_ms and
+ * wall_ms are those of the whole batch.  Supports HG_CG, HG_PRIMAL, A0 = I,
+ * HG_FP64 and HG_MIXED, time_pass = -1 (else HG_ERR_ARG).  Returns the first
+ * non-OK status of a problem, or HG_OK. */
+int hg_solve_batch(hg_grid* const* grids, int n, const hg_solve_opts* opts, hg_result* results);
+
 /* Copy e~_load of the last solve (d x |N| doubles, component-major); after an
  * HG_DUAL solve, the flux fluctuation s~_load. */
 int hg_get_field(hg_grid* grid, int load, double* e_out, int on_device);

@@ -108,6 +108,7 @@ SIGNATURES = [
     ("hg_launch_count", ctypes.c_longlong, [_VP]),
     ("hg_time_pass", _I, [_VP, _I, _I, _I, ctypes.POINTER(_D), ctypes.c_char_p]),
     ("hg_num_passes", _I, [_VP]),
+    ("hg_solve_batch", _I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(SolveOpts), ctypes.POINTER(Result)]),
     ("hg_strerror", ctypes.c_char_p, [_I]),
 ]
 
@@ -210,6 +211,18 @@ class Context:
         o = opts if opts is not None else default_opts()
         _check(load().hg_submit(self.h, grid.h, ctypes.byref(o), ctypes.byref(t)), "hg_submit")
         return t.value
+
+    def solve_batch(self, grids: Sequence["Grid"], opts: Optional[SolveOpts] = None,
+                    raise_on_error: bool = True) -> list:
+        """hg_solve_batch: grids of one shape solved together; one result dict each."""
+        n = len(grids)
+        hs = (_VP * n)(*[g.h for g in grids])
+        res = (Result * n)()
+        o = opts if opts is not None else default_opts()
+        st = load().hg_solve_batch(hs, n, ctypes.byref(o), res)
+        if st != HG_OK and raise_on_error:
+            raise HGError(st, "hg_solve_batch")
+        return [r.to_dict() for r in res]
 
     def poll(self, ticket: int, timeout_us: int = 0):
         """Returns None while pending, else the result dict (raises on error)."""

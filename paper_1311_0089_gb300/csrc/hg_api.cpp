@@ -367,32 +367,37 @@ int enqueue_forward_strided(hg_grid* g, int prec, int L, int check_status, int g
     return HG_OK;
 }
 
-// One CG iteration (d + 1 launches).  prof_pass >= 0: event records bracket
-// that pass (0 row_fwd, 1..d-1 strided in launch order, d row_inv).
-int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_pass,
-                         cudaEvent_t ev_before, cudaEvent_t ev_after) {
+// Strided passes of an operator application in launch order (3D: axis 1
+// forward, axis 0, axis 1 inverse; 2D: axis 0), from a template carrying the
+// common fields.
+static void strided_sequence(const hg_grid* g, StrArgs base, int gamma_mode, PassArgs* pa) {
+    const GridDev& gd = g->gd;
+    pa->nstr = 0;
+    if (gd.d == 3) {
+        StrArgs a = base;
+        a.mode = STR_FWD; a.axis = 1; a.outer = gd.N[0]; a.n = gd.N[1]; a.inner = gd.H;
+        pa->sa[pa->nstr++] = a;
+    }
+    StrArgs a = base;
+    a.mode = gamma_mode; a.axis = 0; a.outer = 1; a.n = gd.N[0]; a.inner = gd.Ms / gd.N[0];
+    pa->sa[pa->nstr++] = a;
+    if (gd.d == 3 && gamma_mode == STR_GAMMA) {
+        StrArgs b = base;
+        b.mode = STR_INV; b.axis = 1; b.outer = gd.N[0]; b.n = gd.N[1]; b.inner = gd.H;
+        pa->sa[pa->nstr++] = b;
+    }
+}
+
+void cg_iteration_args(hg_grid* g, int prec, int L, PassArgs* pa) {
     const GridDev& gd = g->gd;
     Work& w = g->work[prec];
-    const int last = gd.d - 1;
     const int d = gd.d;
-    int pass = 0;
-    // inside stream capture only an external event record becomes a real event
-    // record node (a plain record just orders the graph)
-    auto mark = [&](bool before) -> cudaError_t {
-        if (prof_pass != pass) return cudaSuccess;
-        return cudaEventRecordWithFlags(before ? ev_before : ev_after, s, cudaEventRecordExternal);
-    };
-    RowFwdArgs fa;
+    RowFwdArgs& fa = pa->fa;
     memset(&fa, 0, sizeof(fa));
     fa.early_stage = 1;
     fa.mode = FWD_CG; fa.L = L; fa.co = coeffs_for(g, prec, true);
     fa.p = w.p; fa.r = w.r; fa.S = w.S; fa.sc = w.sc;
     fa.partial = g->partial; fa.counter = g->counters + 0; fa.check_status = 1;
-    HG_CU(mark(true));
-    HG_CU(launch_row_fwd(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], fa, s));
-    HG_CU(mark(false));
-    g->ctx->launches++;
-    ++pass;
     StrArgs sa;
     memset(&sa, 0, sizeof(sa));
     sa.early_stage = 1;
@@ -401,55 +406,27 @@ int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_p
         sa.has_A0 = 1;
         for (int i = 0; i < d * d; ++i) sa.A0[i] = g->ref[i];
     }
-    if (d == 3) {
-        sa.mode = STR_FWD; sa.axis = 1; sa.outer = gd.N[0]; sa.n = gd.N[1]; sa.inner = gd.H;
-        HG_CU(mark(true));
-        HG_CU(launch_strided(prec, gd, g->plan[1], g->tw[prec], g->strcfg[prec][1], sa, s));
-        HG_CU(mark(false));
-        g->ctx->launches++;
-        ++pass;
-    }
-    sa.mode = STR_GAMMA; sa.axis = 0; sa.outer = 1; sa.n = gd.N[0]; sa.inner = gd.Ms / gd.N[0];
-    HG_CU(mark(true));
-    HG_CU(launch_strided(prec, gd, g->plan[0], g->tw[prec], g->strcfg[prec][0], sa, s));
-    HG_CU(mark(false));
-    g->ctx->launches++;
-    ++pass;
-    if (d == 3) {
-        sa.mode = STR_INV; sa.axis = 1; sa.outer = gd.N[0]; sa.n = gd.N[1]; sa.inner = gd.H;
-        HG_CU(mark(true));
-        HG_CU(launch_strided(prec, gd, g->plan[1], g->tw[prec], g->strcfg[prec][1], sa, s));
-        HG_CU(mark(false));
-        g->ctx->launches++;
-        ++pass;
-    }
-    RowInvArgs ia;
+    strided_sequence(g, sa, STR_GAMMA, pa);
+    RowInvArgs& ia = pa->ia;
     memset(&ia, 0, sizeof(ia));
     ia.early_stage = 1;
     ia.mode = INV_CG; ia.L = L; ia.S = w.S; ia.x = w.x; ia.r = w.r; ia.p = w.p;
     ia.W = grid_weight(g);
     ia.sc = w.sc; ia.partial = g->partial; ia.counter = g->counters + 1; ia.check_status = 1;
-    HG_CU(mark(true));
-    HG_CU(launch_row_inv(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], ia, s));
-    HG_CU(mark(false));
-    g->ctx->launches++;
-    return HG_OK;
 }
 
-// q = G A (E + u) followed by the epilogue `inv_mode` (INV_RHS / INV_RESID /
-// INV_OUT); u may be null.
-int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, bool withA,
-                   const double* A0dev, const double* A0host, int inv_mode, void* out,
-                   int check_status, cudaStream_t s, Scalars* status_sc) {
+void matvec_args(hg_grid* g, int prec, int L, const void* u, bool unit_loads, bool withA,
+                 const double* A0dev, const double* A0host, int inv_mode, void* out, int check_status,
+                 Scalars* status_sc, PassArgs* pa) {
     const GridDev& gd = g->gd;
+    const int d = gd.d;
     // the right-hand side and the residual of the iteration use its reference
     // medium; projections (INV_PROJ) stay orthogonal
     const bool iter_op = inv_mode == INV_RHS || inv_mode == INV_RESID;
     if (iter_op && g->has_ref && !A0host) A0host = g->ref;
     Work& w = g->work[prec];
     Scalars* sc = status_sc ? status_sc : w.sc;
-    const int last = gd.d - 1;
-    RowFwdArgs fa;
+    RowFwdArgs& fa = pa->fa;
     memset(&fa, 0, sizeof(fa));
     fa.early_stage = 1;
     fa.mode = FWD_APPLY; fa.L = L; fa.co = coeffs_for(g, prec, withA);
@@ -459,19 +436,72 @@ int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, 
         for (int l = 0; l < L; ++l) { fa.Ed[l * gd.d + l] = 1.0; fa.Ef[l * gd.d + l] = 1.0f; }
     }
     fa.partial = g->partial; fa.counter = g->counters + 2; fa.check_status = check_status;
-    HG_CU(launch_row_fwd(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], fa, s));
-    g->ctx->launches++;
-    int st = enqueue_forward_strided(g, prec, L, check_status, STR_GAMMA, A0host, s, sc);
-    if (st) return st;
-    RowInvArgs ia;
+    StrArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.early_stage = 1;
+    sa.L = L; sa.S = w.S; sa.sc = sc; sa.check_status = check_status; sa.dual = g->form;
+    if (A0host) {
+        sa.has_A0 = 1;
+        for (int i = 0; i < d * d; ++i) sa.A0[i] = A0host[i];
+    }
+    strided_sequence(g, sa, STR_GAMMA, pa);
+    RowInvArgs& ia = pa->ia;
     memset(&ia, 0, sizeof(ia));
     ia.early_stage = 1;
     ia.mode = inv_mode; ia.L = L; ia.S = w.S; ia.x = w.x; ia.r = w.r; ia.p = w.p; ia.out = out;
     if (iter_op) ia.W = grid_weight(g);
     ia.sc = sc; ia.partial = g->partial; ia.counter = g->counters + 3; ia.check_status = check_status;
-    HG_CU(launch_row_inv(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], ia, s));
+}
+
+// The launches of pa on g; mark(before, pass) brackets pass `pass`
+// (0 row_fwd, 1..nstr strided, nstr + 1 row_inv) with event records.
+template <typename Mark>
+static int launch_passes(hg_grid* g, int prec, const PassArgs& pa, cudaStream_t s, Mark mark) {
+    const GridDev& gd = g->gd;
+    const int last = gd.d - 1;
+    int pass = 0;
+    HG_CU(mark(true, pass));
+    HG_CU(launch_row_fwd(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], pa.fa, s));
+    HG_CU(mark(false, pass));
+    g->ctx->launches++;
+    ++pass;
+    for (int k = 0; k < pa.nstr; ++k) {
+        const int ax = pa.sa[k].axis;
+        HG_CU(mark(true, pass));
+        HG_CU(launch_strided(prec, gd, g->plan[ax], g->tw[prec], g->strcfg[prec][ax], pa.sa[k], s));
+        HG_CU(mark(false, pass));
+        g->ctx->launches++;
+        ++pass;
+    }
+    HG_CU(mark(true, pass));
+    HG_CU(launch_row_inv(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], pa.ia, s));
+    HG_CU(mark(false, pass));
     g->ctx->launches++;
     return HG_OK;
+}
+
+// One CG iteration (d + 1 launches).  prof_pass >= 0: event records bracket
+// that pass (0 row_fwd, 1..d-1 strided in launch order, d row_inv); inside
+// stream capture only an external event record becomes a real event record
+// node (a plain record just orders the graph).
+int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_pass,
+                         cudaEvent_t ev_before, cudaEvent_t ev_after) {
+    PassArgs pa;
+    cg_iteration_args(g, prec, L, &pa);
+    return launch_passes(g, prec, pa, s, [&](bool before, int pass) -> cudaError_t {
+        if (prof_pass != pass) return cudaSuccess;
+        return cudaEventRecordWithFlags(before ? ev_before : ev_after, s, cudaEventRecordExternal);
+    });
+}
+
+// q = G A (E + u) followed by the epilogue `inv_mode` (INV_RHS / INV_RESID /
+// INV_OUT / INV_PROJ); u may be null.
+int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, bool withA,
+                   const double* A0dev, const double* A0host, int inv_mode, void* out,
+                   int check_status, cudaStream_t s, Scalars* status_sc) {
+    PassArgs pa;
+    matvec_args(g, prec, L, u, unit_loads, withA, A0dev, A0host, inv_mode, out, check_status, status_sc, &pa);
+    return launch_passes(g, prec, pa, s, [](bool, int) { return cudaSuccess; });
 }
 
 // A CUDA graph of `chunk` CG iterations, cached per precision.

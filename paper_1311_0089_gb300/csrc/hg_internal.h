@@ -158,6 +158,15 @@ cudaError_t launch_strided(int prec, const GridDev& g, const AxisPlanH& pl, cons
                            const StrCfg& cfg, const StrArgs& a, cudaStream_t s);
 cudaError_t launch_row_inv(int prec, const GridDev& g, const AxisPlanH& pl, const void* tw,
                            const RowCfg& cfg, const RowInvArgs& a, cudaStream_t s);
+// Batched forms: P problems of the grid shape g, problem p's arguments at items[p]
+// (device memory), L loads each.
+cudaError_t launch_row_fwd_batch(int prec, const GridDev& g, const AxisPlanH& pl, const void* tw,
+                                 const RowCfg& cfg, const RowFwdArgs* items, int P, int L, cudaStream_t s);
+cudaError_t launch_row_inv_batch(int prec, const GridDev& g, const AxisPlanH& pl, const void* tw,
+                                 const RowCfg& cfg, const RowInvArgs* items, int P, int L, cudaStream_t s);
+cudaError_t launch_strided_batch(int prec, const GridDev& g, const AxisPlanH& pl, const void* tw,
+                                 const StrCfg& cfg, const StrArgs* items, int P, int L, int n,
+                                 long long inner, long long outer, cudaStream_t s);
 
 // Small helpers.
 // fixed_alpha > 0 selects the Moulinec-Suquet update with step fixed_alpha.
@@ -180,6 +189,8 @@ cudaError_t launch_inner_init(const GridDev& g, int L, const double* r64, float*
 // 11,22[,33],12[,13,23]) into the same layout, FP64 and FP32.
 cudaError_t launch_invert_field(int d, long long M, const double* in, double* out64, float* out32,
                                 cudaStream_t s);
+// dst[p * MAXL + l] = src[p][l] for p < P (src: device array of P pointers).
+cudaError_t launch_gather_scalars(const Scalars* const* src, Scalars* dst, int P, cudaStream_t s);
 cudaError_t launch_coeff_bounds(const GridDev& g, const CoeffsDev& co64, double* bounds, cudaStream_t s);
 // x64 += x32 for systems whose outer status is ACTIVE; inner iterations are
 // added to the outer totals.
@@ -211,6 +222,12 @@ cudaError_t launch_row_inv_f32(const GridDev&, const AxisPlanH&, const void*, co
 cudaError_t launch_row_inv_f64(const GridDev&, const AxisPlanH&, const void*, const RowCfg&, const RowInvArgs&, cudaStream_t);
 cudaError_t launch_strided_f32(const GridDev&, const AxisPlanH&, const void*, const StrCfg&, const StrArgs&, cudaStream_t);
 cudaError_t launch_strided_f64(const GridDev&, const AxisPlanH&, const void*, const StrCfg&, const StrArgs&, cudaStream_t);
+cudaError_t launch_row_fwd_batch_f32(const GridDev&, const AxisPlanH&, const void*, const RowCfg&, const RowFwdArgs*, int, int, cudaStream_t);
+cudaError_t launch_row_fwd_batch_f64(const GridDev&, const AxisPlanH&, const void*, const RowCfg&, const RowFwdArgs*, int, int, cudaStream_t);
+cudaError_t launch_row_inv_batch_f32(const GridDev&, const AxisPlanH&, const void*, const RowCfg&, const RowInvArgs*, int, int, cudaStream_t);
+cudaError_t launch_row_inv_batch_f64(const GridDev&, const AxisPlanH&, const void*, const RowCfg&, const RowInvArgs*, int, int, cudaStream_t);
+cudaError_t launch_strided_batch_f32(const GridDev&, const AxisPlanH&, const void*, const StrCfg&, const StrArgs*, int, int, int, long long, long long, cudaStream_t);
+cudaError_t launch_strided_batch_f64(const GridDev&, const AxisPlanH&, const void*, const StrCfg&, const StrArgs*, int, int, int, long long, long long, cudaStream_t);
 cudaError_t configure_f32(int max_smem, const double* ctw);
 cudaError_t configure_f64(int max_smem, const double* ctw);
 

@@ -262,6 +262,12 @@ __global__ void __launch_bounds__(256) k_invert_field(long long M, const double*
     }
 }
 
+// dst[p * MAXL + l] = src[p][l]: the scalars of P problems in one buffer.
+__global__ void k_gather_scalars(const Scalars* const* __restrict__ src, Scalars* dst, int P) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P * MAXL) dst[i] = src[i / MAXL][i % MAXL];
+}
+
 template <typename S, typename Dd>
 __global__ void k_convert(const S* __restrict__ src, Dd* __restrict__ dst, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -331,6 +337,25 @@ cudaError_t launch_row_inv(int prec, const GridDev& g, const AxisPlanH& pl, cons
     return prec == 0 ? launch_row_inv_f64(g, pl, tw, cfg, a, s) : launch_row_inv_f32(g, pl, tw, cfg, a, s);
 }
 
+cudaError_t launch_row_fwd_batch(int prec, const GridDev& g, const AxisPlanH& pl, const void* tw,
+                                 const RowCfg& cfg, const RowFwdArgs* items, int P, int L, cudaStream_t s) {
+    return prec == 0 ? launch_row_fwd_batch_f64(g, pl, tw, cfg, items, P, L, s)
+                     : launch_row_fwd_batch_f32(g, pl, tw, cfg, items, P, L, s);
+}
+
+cudaError_t launch_row_inv_batch(int prec, const GridDev& g, const AxisPlanH& pl, const void* tw,
+                                 const RowCfg& cfg, const RowInvArgs* items, int P, int L, cudaStream_t s) {
+    return prec == 0 ? launch_row_inv_batch_f64(g, pl, tw, cfg, items, P, L, s)
+                     : launch_row_inv_batch_f32(g, pl, tw, cfg, items, P, L, s);
+}
+
+cudaError_t launch_strided_batch(int prec, const GridDev& g, const AxisPlanH& pl, const void* tw,
+                                 const StrCfg& cfg, const StrArgs* items, int P, int L, int n,
+                                 long long inner, long long outer, cudaStream_t s) {
+    return prec == 0 ? launch_strided_batch_f64(g, pl, tw, cfg, items, P, L, n, inner, outer, s)
+                     : launch_strided_batch_f32(g, pl, tw, cfg, items, P, L, n, inner, outer, s);
+}
+
 cudaError_t launch_init_scalars(Scalars* sc, int L, const int* st, double tol, int max_iter,
                                 double fixed_alpha, double zscale, cudaStream_t s) {
     k_init_scalars<<<1, 32, 0, s>>>(sc, L, st[0], L > 1 ? st[1] : ST_IDLE, L > 2 ? st[2] : ST_IDLE,
@@ -393,6 +418,12 @@ cudaError_t launch_coeff_bounds(const GridDev& g, const CoeffsDev& co64, double*
     unsigned nb = elem_grid(g.M);
     if (g.d == 2) k_coeff_bounds<2><<<nb, 256, 0, s>>>(g, co64, b);
     else          k_coeff_bounds<3><<<nb, 256, 0, s>>>(g, co64, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_scalars(const Scalars* const* src, Scalars* dst, int P, cudaStream_t s) {
+    const int n = P * MAXL;
+    k_gather_scalars<<<(n + 127) / 128, 128, 0, s>>>(src, dst, P);
     return cudaGetLastError();
 }
 

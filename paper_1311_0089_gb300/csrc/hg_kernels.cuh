@@ -986,6 +986,38 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
 
 
 // ---------------------------------------------------------------------------
+// batched passes: P problems of one grid shape in one launch
+// ---------------------------------------------------------------------------
+// The arguments of problem p (its coefficients, vectors, scalars, reduction
+// slots and tickets) are items[p] in device memory; the grid's z index picks
+// the problem (strided: z = problem * L + load).  Twiddles and launch geometry
+// are those of the shared shape.
+template <typename T, int D, int NN>
+__global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd_b(GridDev g, AxisPlanH pl,
+                                                                 const Cx<T>* __restrict__ tw,
+                                                                 const RowFwdArgs* __restrict__ items,
+                                                                 int RB, int LB) {
+    row_fwd_body<T, D, NN>(g, pl, tw, items[blockIdx.z], RB, LB, TileIdx::of_block());
+}
+
+template <typename T, int D, int NN>
+__global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv_b(GridDev g, AxisPlanH pl,
+                                                                 const Cx<T>* __restrict__ tw,
+                                                                 const RowInvArgs* __restrict__ items,
+                                                                 int RB, int LB) {
+    row_inv_body<T, D, NN>(g, pl, tw, items[blockIdx.z], RB, LB, TileIdx::of_block());
+}
+
+template <typename T, int D, int NN>
+__global__ void __launch_bounds__(PassThreads<NN>::v, StridedMinBlocks<T, D, NN>::v)
+k_strided_b(GridDev g, AxisPlanH pl, const Cx<T>* __restrict__ tw, const StrArgs* __restrict__ items, int Cl,
+            int L) {
+    TileIdx ti = TileIdx::of_block();
+    ti.z = (int)blockIdx.z % L;
+    strided_body<T, D, NN>(g, pl, tw, items[blockIdx.z / L], Cl, ti);
+}
+
+// ---------------------------------------------------------------------------
 // per-precision launch dispatch (hg_kernels_f32.cu / hg_kernels_f64.cu)
 // ---------------------------------------------------------------------------
 // Transform lengths with compile-time kernels; every other length runs the
@@ -1109,6 +1141,81 @@ cudaError_t launch_strided_t(const GridDev& g, const AxisPlanH& pl, const void* 
     return cudaGetLastError();
 }
 
+// Batched launchers (items in device memory, P problems, L loads each).
+#define HG_BATCH_DISPATCH(KERN, GRID, ...)                                                         \
+    do {                                                                                          \
+        if (g.d == 2) {                                                                           \
+            if (ct) {                                                                             \
+                switch (len) {                                                                    \
+                    HG_CT_SIZES_2D(HG_BCASE2)                                                     \
+                    default: return cudaErrorInvalidConfiguration;                                \
+                }                                                                                 \
+            } else {                                                                              \
+                le = launch_pdl(KERN<T, 2, 0>, GRID, threads_rt, smem, s, __VA_ARGS__);            \
+            }                                                                                     \
+        } else {                                                                                  \
+            if (ct) {                                                                             \
+                switch (len) {                                                                    \
+                    HG_CT_SIZES_3D(HG_BCASE3)                                                     \
+                    default: return cudaErrorInvalidConfiguration;                                \
+                }                                                                                 \
+            } else {                                                                              \
+                le = launch_pdl(KERN<T, 3, 0>, GRID, threads_rt, smem, s, __VA_ARGS__);            \
+            }                                                                                     \
+        }                                                                                         \
+    } while (0)
+
+template <typename T>
+cudaError_t launch_row_fwd_batch_t(const GridDev& g, const AxisPlanH& pl, const void* tw, const RowCfg& cfg,
+                                   const RowFwdArgs* items, int P, int L, cudaStream_t s) {
+    cudaError_t le = cudaSuccess;
+    dim3 grid((unsigned)cfg.nbx, (unsigned)((L + cfg.LB - 1) / cfg.LB), (unsigned)P);
+    const Cx<T>* twp = (const Cx<T>*)tw;
+    const int ct = cfg.ct, len = g.Nl, threads_rt = cfg.threads, smem = cfg.smem;
+#define HG_BCASE2(NV) case NV: le = launch_pdl(k_row_fwd_b<T, 2, NV>, grid, CT_THREADS, smem, s, g, pl, twp, items, cfg.RB, cfg.LB); break;
+#define HG_BCASE3(NV) case NV: le = launch_pdl(k_row_fwd_b<T, 3, NV>, grid, CT_THREADS, smem, s, g, pl, twp, items, cfg.RB, cfg.LB); break;
+    HG_BATCH_DISPATCH(k_row_fwd_b, grid, g, pl, twp, items, cfg.RB, cfg.LB);
+#undef HG_BCASE2
+#undef HG_BCASE3
+    if (le != cudaSuccess) return le;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_row_inv_batch_t(const GridDev& g, const AxisPlanH& pl, const void* tw, const RowCfg& cfg,
+                                   const RowInvArgs* items, int P, int L, cudaStream_t s) {
+    cudaError_t le = cudaSuccess;
+    dim3 grid((unsigned)cfg.nbx, (unsigned)((L + cfg.LB - 1) / cfg.LB), (unsigned)P);
+    const Cx<T>* twp = (const Cx<T>*)tw;
+    const int ct = cfg.ct, len = g.Nl, threads_rt = cfg.threads, smem = cfg.smem;
+#define HG_BCASE2(NV) case NV: le = launch_pdl(k_row_inv_b<T, 2, NV>, grid, CT_THREADS, smem, s, g, pl, twp, items, cfg.RB, cfg.LB); break;
+#define HG_BCASE3(NV) case NV: le = launch_pdl(k_row_inv_b<T, 3, NV>, grid, CT_THREADS, smem, s, g, pl, twp, items, cfg.RB, cfg.LB); break;
+    HG_BATCH_DISPATCH(k_row_inv_b, grid, g, pl, twp, items, cfg.RB, cfg.LB);
+#undef HG_BCASE2
+#undef HG_BCASE3
+    if (le != cudaSuccess) return le;
+    return cudaGetLastError();
+}
+
+// n, inner, outer: the axis and tiling of this strided pass (as in StrArgs).
+template <typename T>
+cudaError_t launch_strided_batch_t(const GridDev& g, const AxisPlanH& pl, const void* tw, const StrCfg& cfg,
+                                   const StrArgs* items, int P, int L, int n, long long inner,
+                                   long long outer, cudaStream_t s) {
+    cudaError_t le = cudaSuccess;
+    dim3 grid((unsigned)((inner + cfg.Cl - 1) / cfg.Cl), (unsigned)outer, (unsigned)(L * P));
+    const Cx<T>* twp = (const Cx<T>*)tw;
+    const int ct = cfg.ct, len = n, threads_rt = cfg.threads, smem = cfg.smem;
+#define HG_BCASE2(NV) case NV: le = launch_pdl(k_strided_b<T, 2, NV>, grid, CT_THREADS, smem, s, g, pl, twp, items, cfg.Cl, L); break;
+#define HG_BCASE3(NV) case NV: le = launch_pdl(k_strided_b<T, 3, NV>, grid, CT_THREADS, smem, s, g, pl, twp, items, cfg.Cl, L); break;
+    HG_BATCH_DISPATCH(k_strided_b, grid, g, pl, twp, items, cfg.Cl, L);
+#undef HG_BCASE2
+#undef HG_BCASE3
+    if (le != cudaSuccess) return le;
+    return cudaGetLastError();
+}
+#undef HG_BATCH_DISPATCH
+
 template <typename T>
 cudaError_t configure_t(int max_smem, const double* ctw) {
     cudaError_t e = cudaSuccess;
@@ -1128,8 +1235,10 @@ cudaError_t configure_t(int max_smem, const double* ctw) {
         cudaError_t e2 = cudaFuncSetAttribute(__VA_ARGS__, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem); \
         if (e2 != cudaSuccess) e = e2;                                                                     \
     } while (0)
-#define HG_SET2(NV) HG_SET(k_row_fwd<T, 2, NV>); HG_SET(k_row_inv<T, 2, NV>); HG_SET(k_strided<T, 2, NV>);
-#define HG_SET3(NV) HG_SET(k_row_fwd<T, 3, NV>); HG_SET(k_row_inv<T, 3, NV>); HG_SET(k_strided<T, 3, NV>);
+#define HG_SET2(NV) HG_SET(k_row_fwd<T, 2, NV>); HG_SET(k_row_inv<T, 2, NV>); HG_SET(k_strided<T, 2, NV>); \
+    HG_SET(k_row_fwd_b<T, 2, NV>); HG_SET(k_row_inv_b<T, 2, NV>); HG_SET(k_strided_b<T, 2, NV>);
+#define HG_SET3(NV) HG_SET(k_row_fwd<T, 3, NV>); HG_SET(k_row_inv<T, 3, NV>); HG_SET(k_strided<T, 3, NV>); \
+    HG_SET(k_row_fwd_b<T, 3, NV>); HG_SET(k_row_inv_b<T, 3, NV>); HG_SET(k_strided_b<T, 3, NV>);
     HG_SET2(0) HG_SET3(0)
     HG_CT_SIZES_2D(HG_SET2)
     HG_CT_SIZES_3D(HG_SET3)

@@ -124,6 +124,19 @@ int grid_alloc_common(hg_grid* g);
 hgk::CoeffsDev coeffs_for(const hg_grid* g, int prec, bool withA);
 int enqueue_forward_strided(hg_grid* g, int prec, int L, int check_status, int gamma_mode,
                             const double* A0, cudaStream_t s, hgk::Scalars* status_sc = nullptr);
+// The arguments of one operator application on one grid (d + 1 launches): the
+// last-axis forward pass, the strided passes in launch order, the last-axis
+// inverse pass.
+struct PassArgs {
+    hgk::RowFwdArgs fa;
+    hgk::StrArgs sa[3];
+    int nstr = 0;
+    hgk::RowInvArgs ia;
+};
+void cg_iteration_args(hg_grid* g, int prec, int L, PassArgs* pa);
+void matvec_args(hg_grid* g, int prec, int L, const void* u, bool unit_loads, bool withA,
+                 const double* A0dev, const double* A0host, int inv_mode, void* out, int check_status,
+                 hgk::Scalars* status_sc, PassArgs* pa);
 int enqueue_cg_iteration(hg_grid* g, int prec, int L, cudaStream_t s, int prof_pass = -1,
                          cudaEvent_t ev_before = nullptr, cudaEvent_t ev_after = nullptr);
 int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, bool withA,

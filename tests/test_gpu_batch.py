@@ -1,0 +1,122 @@
+"""Batched solves (hg_solve_batch: every pass one launch for all problems)
+against single solves and the oracle.
+
+A batched launch runs, for each problem, the same tile bodies with the same
+tile-to-CTA map and fixed-order reductions as that problem's own launch, so
+each problem's iterates, iteration counts and A_H equal its single solve
+bitwise.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(hg):
+    c = hg.Context(0)
+    yield c
+    c.close()
+
+
+def problems(n, count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        vf = rng.uniform(0.1, 0.5)
+        contrast = float(np.exp(rng.uniform(np.log(10.0), np.log(1e4))))
+        out.append(W.ellipses_2d(n, vf, contrast, np.random.default_rng(seed + 17 * k)))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_equals_single_solves(hg, ctx, prec):
+    pr = hg.HG_MIXED if prec == "mixed" else hg.HG_FP64
+    ms = problems(45, 9, 5)
+    grids = []
+    for m in ms:
+        g = ctx.grid(m.N)
+        g.set_coeffs_phase(m.phase, m.table)
+        grids.append(g)
+    o = hg.default_opts(tol=1e-7, prec=pr, max_iter=20000)
+    batch = ctx.solve_batch(grids, o)
+    fields = [g.field(1) for g in grids]
+    for g, b, f in zip(grids, batch, fields):
+        single = g.solve(o)
+        assert b["status"] == 0
+        assert b["iters"] == single["iters"] and b["outer"] == single["outer"]
+        np.testing.assert_array_equal(b["AH"], single["AH"])
+        np.testing.assert_array_equal(f, g.field(1))
+    for g in grids:
+        g.close()
+
+
+def test_batch_against_oracle_3d_and_runtime_sizes(hg, ctx):
+    rng = np.random.default_rng(2)
+    for N in [(15, 9, 15), (7, 9, 5), (45, 75)]:
+        As = [W.random_spd_field(N, rng, 1.0, 20.0) for _ in range(3)]
+        grids = []
+        for A in As:
+            g = ctx.grid(N)
+            g.set_coeffs_field(A)
+            grids.append(g)
+        res = ctx.solve_batch(grids, hg.default_opts(tol=1e-11))
+        for A, r in zip(As, res):
+            ref = O.solve_AH(A, N, tol=1e-11)["AH"]
+            assert np.max(np.abs(r["AH"] - ref)) <= 1e-8 * np.max(np.abs(ref))
+        resm = ctx.solve_batch(grids, hg.default_opts(tol=1e-9, prec=hg.HG_MIXED))
+        for A, r in zip(As, resm):
+            ref = O.solve_AH(A, N, tol=1e-11)["AH"]
+            assert np.max(np.abs(r["AH"] - ref)) <= 1e-6 * np.max(np.abs(ref))
+        for g in grids:
+            g.close()
+
+
+def test_batch_with_a_homogeneous_problem_and_loads_mask(hg, ctx):
+    ms = problems(27, 3, 9)
+    N = ms[0].N
+    grids = []
+    for m in ms:
+        g = ctx.grid(N)
+        g.set_coeffs_phase(m.phase, m.table)
+        grids.append(g)
+    A0 = np.array([[3.0, 1.0], [1.0, 2.0]])
+    h = ctx.grid(N)
+    h.set_coeffs_phase(np.zeros(N, np.uint8), A0[None])
+    grids.append(h)
+    o = hg.default_opts(tol=1e-8, prec=hg.HG_MIXED)
+    res = ctx.solve_batch(grids, o)
+    assert res[-1]["iters"] == [0, 0]
+    np.testing.assert_allclose(res[-1]["AH"], A0, atol=1e-13)
+    for g, r in zip(grids[:-1], res[:-1]):
+        single = g.solve(o)
+        np.testing.assert_array_equal(r["AH"], single["AH"])
+    only2 = ctx.solve_batch(grids, hg.default_opts(tol=1e-8, prec=hg.HG_MIXED, loads_mask=2))
+    for r in only2:
+        assert r["iters"][0] == 0 and r["AH"][0, 0] == 0.0
+    for g in grids:
+        g.close()
+
+
+def test_batch_errors(hg, ctx):
+    a, b = ctx.grid((15, 15)), ctx.grid((27, 27))
+    m = W.square_inclusion_15()
+    a.set_coeffs_phase(m.phase, m.table)
+    b.set_coeffs_phase(np.zeros((27, 27), np.uint8), np.eye(2)[None])
+    import ctypes
+    lib = hg.load()
+    hs = (ctypes.c_void_p * 2)(a.h, b.h)
+    res = (hg.Result * 2)()
+    assert lib.hg_solve_batch(hs, 2, ctypes.byref(hg.default_opts()), res) == -1
+    hs = (ctypes.c_void_p * 2)(a.h, a.h)
+    assert lib.hg_solve_batch(hs, 2, ctypes.byref(hg.default_opts()), res) == -1
+    hs1 = (ctypes.c_void_p * 1)(a.h)
+    assert lib.hg_solve_batch(hs1, 1, ctypes.byref(hg.default_opts(method=hg.HG_MS)), res) == -1
+    assert lib.hg_solve_batch(hs1, 1, ctypes.byref(hg.default_opts(formulation=hg.HG_DUAL)), res) == -1
+    assert lib.hg_solve_batch(hs1, 1, ctypes.byref(hg.default_opts(A0=2.0 * np.eye(2))), res) == -1
+    assert lib.hg_solve_batch(hs1, 0, ctypes.byref(hg.default_opts()), res) == -1
+    a.close()
+    b.close()
