@@ -21,6 +21,8 @@ Galerkin method for homogenization of periodic media" (arXiv:1311.0089):
   * Sec. 5.3                   Moulinec-Suquet fixed point (Neumann series)
   * Sec. 5.1 (Eq. Helmholtz_discrete) R^{dN} = U_N (+) E_N (+) J_N; the dual
                                (flux) problem on J_N that Sec. 6 announces
+  * Sec. 4.2 (Ga)              Galerkin approximation with exact integration,
+                               for coefficients constant on the pixels of a grid
   * Sec. 3 (Eq. forms_def1)    energy a(e,e) -> homogenized matrix A_H
                                (A_H itself is not defined in the paper; the
                                energy reading is stated in the project notes)
@@ -44,6 +46,8 @@ __all__ = [
     "dense_gamma_matrix", "solve_lsd_dense", "moulinec_suquet",
     "apply_gamma_J", "invert_coeffs", "cg_dual", "solve_AH_dual", "solve_dual_dense",
     "cg_ref", "solve_AH_ref",
+    "pixel_fourier_coeffs", "ga_quadrature_grid", "ga_coefficients", "apply_gamma_band", "solve_AH_ga",
+    "solve_ga_dense",
 ]
 
 
@@ -531,3 +535,163 @@ def solve_AH_ref(A: np.ndarray, N, A0: np.ndarray, Y=None, tol: float = 1e-10,
         xs.append(out["x"])
         es.append(E.reshape((d,) + (1,) * d) + out["x"])
     return {"AH": homogenized_energy(A, es), "AH_flux": homogenized_flux(A, es), "iters": iters, "x": xs}
+
+
+# ---------------------------------------------------------------------------
+# Galerkin approximation with exact integration (Sec. 4.2, Ga) for
+# coefficients constant on the pixels of a grid P
+# ---------------------------------------------------------------------------
+def pixel_fourier_coeffs(A_pix: np.ndarray, N: Sequence[int]) -> np.ndarray:
+    """Fourier coefficients A_hat(l), |l_a| <= N_a - 1, of A constant on the
+    pixels of the grid P = A_pix.shape[2:] (pixel k centred at x_k = k h,
+    width h = 2 Y / P).  Integrating exp(-i pi xi(l) . x) over a pixel gives
+    its centre value times prod_a sinc(l_a / P_a) (sinc(t) = sin(pi t)/(pi t)),
+    so A_hat(l) = DFT_P(A)(l mod P) prod_a sinc(l_a / P_a).
+    Returns (d, d, 2N_1 - 1, ...), index l + N - 1."""
+    P = A_pix.shape[2:]
+    nd = len(P)
+    Ah = dft(A_pix, nd)
+    idx = np.ix_(*[np.arange(-(n - 1), n) % p for n, p in zip(N, P)])
+    out = Ah[(slice(None), slice(None)) + idx]
+    for a, (n, p) in enumerate(zip(N, P)):
+        shape = [1] * (nd + 2)
+        shape[2 + a] = 2 * n - 1
+        out = out * np.sinc(np.arange(-(n - 1), n) / p).reshape(shape)
+    return out
+
+
+def ga_quadrature_grid(N: Sequence[int]) -> Tuple[int, ...]:
+    """The smallest odd M_a >= 2 N_a - 1 (a product of two trigonometric
+    polynomials of the trial space Z_N then integrates exactly on M)."""
+    return tuple(2 * n - 1 for n in N)
+
+
+def ga_coefficients(A_pix: np.ndarray, N: Sequence[int], M: Sequence[int]) -> np.ndarray:
+    """Values on the grid M of the Fourier series of A truncated to |l_a| <=
+    N_a - 1: the frequencies a product of two trial functions reaches, so for
+    u, v of the trial space mean_M(A_M u . v) is the exact integral of
+    A u . v (for M_a >= 2 N_a - 1).  Not SPD pointwise in general."""
+    Ahat = pixel_fourier_coeffs(A_pix, N)
+    spec = np.zeros(A_pix.shape[:2] + tuple(M), dtype=np.complex128)
+    idx = np.ix_(*[np.arange(-(n - 1), n) % m for n, m in zip(N, M)])
+    spec[(slice(None), slice(None)) + idx] = Ahat
+    return idft(spec, len(M)).real
+
+
+def apply_gamma_band(u: np.ndarray, M, N, Y=None, dual: bool = False) -> np.ndarray:
+    """Gamma_N (or the projection onto J_N for dual) on the grid M, followed by
+    the removal of every frequency outside the trial space Z_N."""
+    M = check_grid(M)
+    d = len(M)
+    uh = dft(u, d)
+    if dual:
+        xi = _xi_field(M, Y)
+        den = np.einsum("a...,a...->...", xi, xi)
+        num = np.einsum("a...,a...->...", xi, uh)
+        zero = den == 0
+        vh = uh - xi * np.where(zero, 0.0, num / np.where(zero, 1.0, den))
+        vh[(slice(None),) + tuple([0] * d)] = 0.0
+    else:
+        vh = np.einsum("ab...,b...->a...", gamma_hat(M, Y), uh)
+    band = np.ones(M, dtype=bool)
+    for a, (m, n) in enumerate(zip(M, N)):
+        shape = [1] * d
+        shape[a] = m
+        band &= (np.abs(freq_index(m)) <= (n - 1) // 2).reshape(shape)
+    vh = vh * band
+    return idft(vh, d).real
+
+
+def solve_AH_ga(A_pix: np.ndarray, N, M=None, Y=None, tol: float = 1e-12, maxiter: int = 10000,
+                dual: bool = False) -> Dict:
+    """Ga on the trial space Z_N for pixel-constant A: CG (the steps of `cg`)
+    on the grid M with the band-limited projection and the coefficients
+    `ga_coefficients`; A_H from the exact energy.  Ga minimises the energy over
+    a subspace of the continuous problem's fields, so its A_H bounds the
+    homogenized matrix of the pixelated medium from above; the dual (fluxes on
+    the band-limited J_N, coefficients A^-1) bounds it from below."""
+    N = check_grid(N)
+    d = len(N)
+    M = check_grid(ga_quadrature_grid(N) if M is None else M)
+    C = invert_coeffs(A_pix) if dual else A_pix
+    AM = ga_coefficients(C, N, M)
+    K = lambda u: apply_gamma_band(apply_A(AM, u), M, N, Y, dual)
+    es, iters = [], []
+    for j in range(d):
+        E = np.zeros(d)
+        E[j] = 1.0
+        Evec = E.reshape((d,) + (1,) * d) * np.ones((d,) + M)
+        b = -K(Evec)
+        x = np.zeros((d,) + M)
+        r = b.copy()
+        p = r.copy()
+        rr = inner(r, r)
+        bnorm = np.sqrt(rr)
+        AE = apply_A(AM, Evec)
+        it = 0
+        if bnorm > ZERO_RHS * np.sqrt(inner(AE, AE)):
+            rel = 1.0
+            while it < maxiter and rel > tol:
+                q = K(p)
+                alpha = rr / inner(p, q)
+                x = x + alpha * p
+                r = r - alpha * q
+                it += 1
+                rr_new = inner(r, r)
+                rel = np.sqrt(rr_new) / bnorm
+                p = r + (rr_new / rr) * p
+                rr = rr_new
+        iters.append(it)
+        es.append(Evec + x)
+    H = homogenized_energy(AM, es)
+    out = {"iters": iters, "M": M}
+    if dual:
+        out["CH"] = H
+        out["AH"] = np.linalg.inv(H)
+    else:
+        out["AH"] = H
+    return out
+
+
+def solve_ga_dense(A_pix: np.ndarray, N, Y=None) -> np.ndarray:
+    """Ga assembled in Fourier space for tiny trial spaces: e = E + e~ with
+    e~_hat(m) = xi(m) c(m) (curl-free), and the exact energy
+    sum_{m,n} conj(e_hat(n)) . A_hat(n - m) e_hat(m); its minimiser solves
+    sum_{m != 0} xi(n)^T A_hat(n - m) xi(m) c(m) = -xi(n)^T A_hat(n) E for
+    n != 0.  Returns A_H (d x d)."""
+    N = check_grid(N)
+    d = len(N)
+    Ahat = pixel_fourier_coeffs(A_pix, N)
+    grids = np.meshgrid(*[freq_index(n) for n in N], indexing="ij")
+    ms = np.stack([g.ravel() for g in grids], axis=1)
+    Yv = [1.0] * d if Y is None else Y
+    xi = ms / np.asarray(Yv, dtype=np.float64)
+    nz = [i for i in range(len(ms)) if np.any(ms[i] != 0)]
+    off = np.asarray(N) - 1
+
+    def Ah(l):
+        return Ahat[(slice(None), slice(None)) + tuple(l + off)]
+
+    AH = np.zeros((d, d))
+    es = []
+    for j in range(d):
+        E = np.zeros(d)
+        E[j] = 1.0
+        K = np.zeros((len(nz), len(nz)), dtype=np.complex128)
+        rhs = np.zeros(len(nz), dtype=np.complex128)
+        for a, n in enumerate(nz):
+            rhs[a] = -xi[n] @ Ah(ms[n]) @ E
+            for b, m in enumerate(nz):
+                K[a, b] = xi[n] @ Ah(ms[n] - ms[m]) @ xi[m]
+        c = np.linalg.solve(K, rhs)
+        eh = {tuple(ms[n]): xi[n] * c[a] for a, n in enumerate(nz)}
+        eh[tuple([0] * d)] = E.astype(np.complex128)
+        es.append(eh)
+    for i in range(d):
+        for j in range(d):
+            tot = 0.0
+            for kn, en in es[i].items():
+                for km, em in es[j].items():
+                    tot += np.conj(en) @ Ah(np.array(kn) - np.array(km)) @ em
+            AH[i, j] = tot.real
+    return AH
