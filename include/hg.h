@@ -195,6 +195,21 @@ int hg_set_coeffs(hg_grid* grid, const double* A, int layout, int on_device);
 int hg_set_coeffs_phase(hg_grid* grid, const uint8_t* phase, int n_phases,
                         const double* table, int on_device);
 
+/* Coefficients for the Galerkin scheme with exact integration (Sec. 4.2, Ga):
+ * A constant on the pixels of a grid P (phase: |P| bytes on the host, C order,
+ * entries in [0, n_phases); table: n_phases x d x d host doubles, each SPD),
+ * trial space Z_N with N = N_trial (odd per axis).  The grid is the quadrature
+ * grid M and needs M_a >= 2 N_a - 1 per axis, so that the grid mean of
+ * A_M u . v for trial fields u, v is their exact integral (A_M: the Fourier
+ * series of A truncated to |l_a| <= N_a - 1, built from the pixels' sinc
+ * coefficients).  Solves then restrict the projection Gamma_hat to Z_N and
+ * return the Ga A_H, an upper bound on the continuous A_H; an HG_DUAL solve
+ * uses (A^-1)_M and returns the matching lower bound.  HG_MS and a general A0
+ * are refused on such a grid (HG_ERR_ARG).  Blocks until the fields are built.
+ * Errors: HG_ERR_ARG (sizes, phases), HG_ERR_NOT_SPD, HG_ERR_OOM, HG_ERR_BUSY. */
+int hg_set_coeffs_exact(hg_grid* grid, const int* N_trial, const int* P, const uint8_t* phase,
+                        int n_phases, const double* table);
+
 /* Blocking solve of Eq. final_system for the loads in opts->loads_mask and
  * assembly of A_H (rows/columns of unsolved loads are left 0).  AH_out may be
  * NULL (d*d doubles, row-major); info may be NULL. */

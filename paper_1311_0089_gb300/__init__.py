@@ -37,6 +37,7 @@ STATUS = {
     -9: "HG_ERR_CANCELLED", -10: "HG_ERR_BREAKDOWN", -11: "HG_ERR_NO_COEFFS",
     -12: "HG_ERR_TOO_LARGE",
 }
+globals().update({name: code for code, name in STATUS.items()})
 
 
 class HGError(RuntimeError):
@@ -97,6 +98,7 @@ SIGNATURES = [
     ("hg_destroy_grid", _I, [_VP]),
     ("hg_set_coeffs", _I, [_VP, _VP, _I, _I]),
     ("hg_set_coeffs_phase", _I, [_VP, _VP, _I, _VP, _I]),
+    ("hg_set_coeffs_exact", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), _VP, _I, _VP]),
     ("hg_solve_AH", _I, [_VP, ctypes.POINTER(SolveOpts), _VP, ctypes.POINTER(Result)]),
     ("hg_get_field", _I, [_VP, _I, _VP, _I]),
     ("hg_submit", _I, [_VP, _VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(ctypes.c_uint64)]),
@@ -272,6 +274,18 @@ class Grid:
         if dev_p != dev_t:
             raise ValueError("phase map and table must both be on the host or both on the device")
         _check(load().hg_set_coeffs_phase(self.h, p, n_ph, t, dev_p), "hg_set_coeffs_phase")
+
+    def set_coeffs_exact(self, N_trial, phase, table):
+        """Ga coefficients: pixels of the grid phase.shape with the given table,
+        trial space N_trial; this grid is the quadrature grid (>= 2 N_trial - 1)."""
+        ph = np.ascontiguousarray(np.asarray(phase, np.uint8))
+        tb = np.ascontiguousarray(np.asarray(table, np.float64))
+        if ph.ndim != self.d or len(N_trial) != self.d:
+            raise ValueError("phase map and trial grid must have the grid's dimension")
+        nt = (_I * 3)(*[int(v) for v in N_trial])
+        P = (_I * 3)(*ph.shape)
+        _check(load().hg_set_coeffs_exact(self.h, nt, P, ph.ctypes.data, int(tb.shape[0]), tb.ctypes.data),
+               "hg_set_coeffs_exact")
 
     def set_coeffs(self, A, layout: int = HG_COEFF_FULL):
         """A: full (|N|, d, d) voxel-major, or packed (d(d+1)/2, |N|)."""

@@ -402,6 +402,7 @@ void cg_iteration_args(hg_grid* g, int prec, int L, PassArgs* pa) {
     memset(&sa, 0, sizeof(sa));
     sa.early_stage = 1;
     sa.L = L; sa.S = w.S; sa.sc = w.sc; sa.check_status = 1; sa.dual = g->form;
+    for (int a = 0; a < 3; ++a) sa.band[a] = g->band[a];
     if (g->has_ref) {   // Gamma_hat of the reference medium (its denominator xi . A0 xi)
         sa.has_A0 = 1;
         for (int i = 0; i < d * d; ++i) sa.A0[i] = g->ref[i];
@@ -440,6 +441,7 @@ void matvec_args(hg_grid* g, int prec, int L, const void* u, bool unit_loads, bo
     memset(&sa, 0, sizeof(sa));
     sa.early_stage = 1;
     sa.L = L; sa.S = w.S; sa.sc = sc; sa.check_status = check_status; sa.dual = g->form;
+    for (int a = 0; a < 3; ++a) sa.band[a] = g->band[a];
     if (A0host) {
         sa.has_A0 = 1;
         for (int i = 0; i < d * d; ++i) sa.A0[i] = A0host[i];

@@ -70,6 +70,11 @@ void free_inverse_coeffs(hg_grid* g) {
 }
 
 void free_coeffs(hg_grid* g) {
+    // cached CG graphs hold the coefficient pointers (and the band) they were captured with
+    for (int p = 0; p < 2; ++p) {
+        if (g->graphs[p].exec) cudaGraphExecDestroy(g->graphs[p].exec);
+        g->graphs[p] = hgrt::GraphCache();
+    }
     dev_free(g->ctx, g->d_phase);
     g->d_phase = nullptr;
     for (int p = 0; p < 2; ++p) {
@@ -79,6 +84,8 @@ void free_coeffs(hg_grid* g) {
     }
     free_inverse_coeffs(g);
     g->coeff_mode = -1;
+    g->exact = false;
+    g->band[0] = g->band[1] = g->band[2] = 0;
 }
 
 struct DeviceGuard {
@@ -95,9 +102,11 @@ int validate_solve_opts(const hg_grid* g, hg_solve_opts* o) {
         !std::isfinite(o->lambda_ref) || (o->formulation != HG_PRIMAL && o->formulation != HG_DUAL))
         return HG_ERR_ARG;
     if (o->A0[0] != 0.0) {
-        if (o->method != HG_CG || o->formulation != HG_PRIMAL) return HG_ERR_ARG;
+        if (o->method != HG_CG || o->formulation != HG_PRIMAL || g->exact) return HG_ERR_ARG;
         if (!is_spd(o->A0, g->gd.d)) return HG_ERR_NOT_SPD;
     }
+    // exact-integration coefficients are not SPD pointwise: no eigenvalue bounds
+    if (g->exact && o->method == HG_MS) return HG_ERR_ARG;
     o->loads_mask &= (1u << g->gd.d) - 1u;
     return HG_OK;
 }
@@ -328,6 +337,8 @@ int hg_set_coeffs(hg_grid* g, const double* A, int layout, int on_device) {
     HG_CU(cudaStreamSynchronize(c->stream));
     g->coeff_mode = 1;
     g->bounds_ok[0] = g->bounds_ok[1] = false;
+    g->exact = false;
+    g->band[0] = g->band[1] = g->band[2] = 0;
     return HG_OK;
 }
 
@@ -379,8 +390,87 @@ int hg_set_coeffs_phase(hg_grid* g, const uint8_t* phase, int n_phases, const do
     g->coeff_mode = 0;
     g->bounds_ok[0] = g->bounds_ok[1] = false;
     g->inv_ok = false;   // a reused phase table keeps its buffers; the inverse is redone
+    g->exact = false;
+    g->band[0] = g->band[1] = g->band[2] = 0;
     g->n_phases = n_phases;
     return HG_OK;
+}
+
+int hg_set_coeffs_exact(hg_grid* g, const int* N_trial, const int* P, const uint8_t* phase, int n_phases,
+                        const double* table) {
+    if (!g || !N_trial || !P || !phase || !table || n_phases < 1 || n_phases > 256) return HG_ERR_ARG;
+    if (g->borrowed.load() > 0) return HG_ERR_BUSY;
+    const int d = g->gd.d;
+    long long Pt = 1;
+    for (int a = 0; a < d; ++a) {
+        if (N_trial[a] < 1 || (N_trial[a] % 2) == 0 || 2 * N_trial[a] - 1 > g->gd.N[a]) return HG_ERR_ARG;
+        if (P[a] < 1 || P[a] > 4096) return HG_ERR_ARG;
+        Pt *= P[a];
+    }
+    std::vector<double> tb((size_t)n_phases * d * d), tinv(tb.size());
+    memcpy(tb.data(), table, tb.size() * sizeof(double));
+    for (int p = 0; p < n_phases; ++p) {
+        const double* a = &tb[(size_t)p * d * d];
+        if (!is_spd(a, d)) return HG_ERR_NOT_SPD;
+        // A^-1 for the dual: adjugate over determinant
+        double* r = &tinv[(size_t)p * d * d];
+        if (d == 2) {
+            const double det = a[0] * a[3] - a[1] * a[2];
+            r[0] = a[3] / det; r[1] = -a[1] / det; r[2] = -a[2] / det; r[3] = a[0] / det;
+        } else {
+            const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8];
+            const double c02 = a[3] * a[7] - a[4] * a[6], c10 = a[2] * a[7] - a[1] * a[8];
+            const double c11 = a[0] * a[8] - a[2] * a[6], c12 = a[1] * a[6] - a[0] * a[7];
+            const double c20 = a[1] * a[5] - a[2] * a[4], c21 = a[2] * a[3] - a[0] * a[5];
+            const double c22 = a[0] * a[4] - a[1] * a[3];
+            const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+            r[0] = c00 / det; r[1] = c10 / det; r[2] = c20 / det;
+            r[3] = c01 / det; r[4] = c11 / det; r[5] = c21 / det;
+            r[6] = c02 / det; r[7] = c12 / det; r[8] = c22 / det;
+        }
+    }
+    if (n_phases < 256)
+        for (long long k = 0; k < Pt; ++k)
+            if (phase[k] >= n_phases) return HG_ERR_ARG;
+    hg_ctx* c = g->ctx;
+    DeviceGuard dg(c->device);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    cudaStream_t s = c->stream;
+    const size_t nf = (size_t)(d * (d + 1) / 2) * g->gd.M;
+    free_coeffs(g);
+    int st;
+    uint8_t* d_phase = nullptr;
+    double* d_tab = nullptr;
+    auto done = [&](int code) {
+        dev_free(c, d_phase);
+        dev_free(c, d_tab);
+        return code;
+    };
+    if ((st = dev_alloc(c, (void**)&d_phase, (size_t)Pt))) return done(st);
+    if ((st = dev_alloc(c, (void**)&d_tab, 2 * tb.size() * sizeof(double)))) return done(st);
+    for (int p = 0; p < 2; ++p) {
+        if ((st = dev_alloc(c, &g->d_field[p], nf * (p ? sizeof(float) : sizeof(double))))) return done(st);
+        if ((st = dev_alloc(c, &g->d_field_inv[p], nf * (p ? sizeof(float) : sizeof(double))))) return done(st);
+    }
+    cudaError_t e = cudaMemcpyAsync(d_phase, phase, (size_t)Pt, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab, tb.data(), tb.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_tab + tb.size(), tinv.data(), tb.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "hg_set_coeffs_exact");
+        return done(HG_ERR_CUDA);
+    }
+    if ((st = ga_build_field(g, N_trial, P, d_phase, d_tab, (double*)g->d_field[0], (float*)g->d_field[1], s)))
+        return done(st);
+    if ((st = ga_build_field(g, N_trial, P, d_phase, d_tab + tb.size(), (double*)g->d_field_inv[0],
+                             (float*)g->d_field_inv[1], s)))
+        return done(st);
+    g->coeff_mode = 1;
+    g->bounds_ok[0] = g->bounds_ok[1] = false;
+    g->inv_ok = true;   // the dual's coefficients are (A^-1)_M, not the pointwise inverse of A_M
+    g->exact = true;
+    for (int a = 0; a < 3; ++a) g->band[a] = a < d ? N_trial[a] : 0;
+    return done(HG_OK);
 }
 
 int hg_solve_AH(hg_grid* g, const hg_solve_opts* opts, double* AH_out, hg_result* info) {

@@ -132,6 +132,8 @@ struct StrArgs {
     int early_stage;            // 1: twiddle/coefficient staging may precede the wait for
                                 //    the previous kernel (tables written only by copies)
     int dual;                   // STR_GAMMA projects onto J_N (identity - mean - Gamma)
+    int band[3];                // STR_GAMMA: > 0: keep only frequencies |m_a| <= (band_a - 1) / 2
+                                // (the trial space of the Galerkin scheme with exact integration)
 };
 
 struct RowInvArgs {

@@ -645,6 +645,20 @@ __device__ __forceinline__ void strided_body(GridDev g, AxisPlanH pl, const Cx<T
                 xi_rest[D - 1] = (T)k2 * inv_y(g, D - 1, T());
             }
         }
+        // Galerkin scheme with exact integration: the trial space is the band
+        // |m_a| <= (band_a - 1) / 2 of this grid's frequencies; no output
+        // outside it
+        bool lane_band = true;
+        if (a.band[0] > 0 && lane_ok) {
+            if (D == 2) {
+                lane_band = i <= (a.band[1] - 1) / 2;
+            } else {
+                const int f1 = freq_of(i / g.H, g.N[1]);
+                lane_band = f1 <= (a.band[1] - 1) / 2 && -f1 <= (a.band[1] - 1) / 2 &&
+                            i % g.H <= (a.band[D - 1] - 1) / 2;
+            }
+        }
+        const int mb = a.band[0] > 0 ? (a.band[0] - 1) / 2 : n;
         const T invY0 = inv_y(g, 0, T());
         const T invM = inv_m(g, T());
         // the row's frequency in T, stepped with the row (integers below 2^24
@@ -682,8 +696,10 @@ __device__ __forceinline__ void strided_body(GridDev g, AxisPlanH pl, const Cx<T
                     num.y += xi[al] * th[al].y;
                 }
             }
+            const int fm = m <= half ? m : m - n;
+            const bool inb = lane_band && fm <= mb && -fm <= mb;
             C s = czero<T>();
-            if (den > T(0)) {
+            if (den > T(0) && inb) {
                 const T f = div_proj(invM, den);
                 s.x = num.x * f;
                 s.y = num.y * f;
@@ -694,7 +710,7 @@ __device__ __forceinline__ void strided_body(GridDev g, AxisPlanH pl, const Cx<T
 #pragma unroll
                 for (int al = 0; al < D; ++al) {
                     C q = czero<T>();
-                    if (den > T(0)) {
+                    if (den > T(0) && inb) {
                         q.x = th[al].x * invM - s.x * xi[al];
                         q.y = th[al].y * invM - s.y * xi[al];
                     }

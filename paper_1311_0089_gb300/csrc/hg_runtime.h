@@ -73,6 +73,10 @@ struct hg_grid {
     uint8_t* d_phase = nullptr;
     void* d_table[2] = {nullptr, nullptr};
     void* d_field[2] = {nullptr, nullptr};
+    // Galerkin scheme with exact integration: this grid is the quadrature grid
+    // and band the trial space Z_N (0: GaNi on this grid)
+    int band[3] = {0, 0, 0};
+    bool exact = false;
     // inverse coefficients A^-1 for the dual formulation (made on first use)
     void* d_table_inv[2] = {nullptr, nullptr};
     void* d_field_inv[2] = {nullptr, nullptr};
@@ -173,6 +177,8 @@ void grid_free_work(hg_grid* g);
 size_t ctx_reclaim(hg_ctx* ctx, hg_grid* keep);
 int solve_impl(hg_grid* g, const hg_solve_opts* o, double* AH_out, hg_result* info);
 int validate_solve_opts(const hg_grid* g, hg_solve_opts* o);
+int ga_build_field(hg_grid* g, const int* Ntr, const int* P, const uint8_t* phase, const double* table,
+                   double* out64, float* out32, cudaStream_t s);
 hgk::Weight grid_weight(const hg_grid* g);   // the scalar product of the iteration
 
 // scheduler (hg_sched.cpp)

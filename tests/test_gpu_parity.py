@@ -390,3 +390,26 @@ def test_mixed_high_contrast_accuracy(hg, ctx):
     oref = O.solve_AH(small.full_field(), small.N, tol=1e-12)["AH"]
     assert rel_max(mixed["AH"], oref) < 1e-6
     g.close()
+
+
+def test_resetting_coefficients_between_solves(hg, ctx):
+    # every change of the coefficient storage (phase map <-> field, another
+    # phase count) drops the cached CG graphs that point at the old buffers
+    N = (27, 27)
+    rng = np.random.default_rng(31)
+    m2 = W.Microstructure(N, (rng.random(N) < 0.3).astype(np.uint8), W.isotropic_table([1.0, 30.0], 2))
+    m3 = W.Microstructure(N, rng.integers(0, 3, size=N).astype(np.uint8), W.isotropic_table([1.0, 5.0, 80.0], 2))
+    A = W.random_spd_field(N, rng, 1.0, 20.0)
+    g = ctx.grid(N)
+    for prec in (hg.HG_FP64, hg.HG_MIXED):
+        o = hg.default_opts(tol=1e-10, prec=prec)
+        for kind, src in (("phase", m2), ("field", A), ("phase", m3), ("phase", m2), ("field", A)):
+            if kind == "phase":
+                g.set_coeffs_phase(src.phase, src.table)
+                ref = O.solve_AH(src.full_field(), N, tol=1e-11)["AH"]
+            else:
+                g.set_coeffs_field(src)
+                ref = O.solve_AH(src, N, tol=1e-11)["AH"]
+            r = g.solve(o)
+            assert rel_max(r["AH"], ref) <= (1e-8 if prec == hg.HG_FP64 else 1e-6)
+    g.close()
