@@ -50,11 +50,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tol", type=float, default=TOL)
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "batched", "serving", "ms"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "batched", "serving", "ms", "ga"],
                     help="c2: 729x729 (default, the headline); c3: 135^3 3D; batched: 256 2D "
                          "problems through the scheduler; serving: Poisson request stream; "
                          "ms: Moulinec-Suquet fixed point against CG on the 729x729 geometry "
-                         "over contrasts 10, 100, 1000")
+                         "over contrasts 10, 100, 1000; ga: Galerkin scheme with exact integration "
+                         "(upper and lower bounds) on the 729x729 pixels for trial grids 81..405")
     ap.add_argument("--duration", type=float, default=20.0, help="serving: arrival window (s)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--passes-once", action="store_true",
@@ -831,6 +832,84 @@ def run_ms(args):
     return 0
 
 
+def run_ga(args):
+    """Guaranteed bounds (Sec. 4.2, Ga): the 729x729 circles as pixel-constant
+    coefficients, trial spaces N = 81, 243, 405 on quadrature grids M >= 2N - 1;
+    primal (upper) and dual (lower) solve per N, the GaNi A_H on 729 for context."""
+    import torch
+    import paper_1311_0089_gb300 as hg
+    import workloads as W
+    torch.cuda.set_device(0)
+    hg.load()
+    base = W.circles_2d()
+    ctx = hg.Context(0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    inner = max(0.5 * args.tol, 1e-6)
+    o_up = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=inner)
+    o_lo = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=inner, formulation=hg.HG_DUAL)
+    gani = reference_AH("c2")
+    trials = ((81, 175), (243, 525), (405, 875))
+    rows, headline, clocks = [], None, None
+    sampler = ClockSampler(0)
+    for n, m in trials:
+        g = ctx.grid((m, m))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_coeffs_exact((n, n), base.phase, base.table)
+        t_setup = time.perf_counter() - t0
+        for _ in range(max(1, args.warmup)):
+            g.solve(o_up)
+            g.solve(o_lo)
+        steps = args.steps if n == trials[-1][0] else max(1, min(3, args.steps))
+        if n == trials[-1][0]:
+            sampler.start()
+        tu, tl = [], []
+        for _ in range(steps):
+            for o, ts in ((o_up, tu), (o_lo, tl)):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = g.solve(o)
+                ts.append(time.perf_counter() - t0)
+                if o is o_up:
+                    up = r
+                else:
+                    lo = r
+        if n == trials[-1][0]:
+            clocks = sampler.stop()
+        t_up, t_lo = statistics.median(tu), statistics.median(tl)
+        gap = np.asarray(up["AH"]) - np.asarray(lo["AH"])
+        rows.append({"N": n, "M": m, "setup_ms": t_setup * 1e3,
+                     "upper_AH": np.asarray(up["AH"]).tolist(), "lower_AH": np.asarray(lo["AH"]).tolist(),
+                     "upper_iters": up["iters"], "lower_iters": lo["iters"],
+                     "upper_ms": t_up * 1e3, "lower_ms": t_lo * 1e3,
+                     "gap_min_eig": float(np.min(np.linalg.eigvalsh(0.5 * (gap + gap.T)))),
+                     "rel_gap_11": float(gap[0, 0] / up["AH"][0][0]),
+                     "gani_729_11_within": bool(lo["AH"][0][0] <= gani[0, 0] <= up["AH"][0][0])})
+        if n == trials[-1][0]:
+            headline = (m, t_up + t_lo, sum(up["iters"]) + sum(lo["iters"]))
+        g.close()
+    m, t_pair, iters = headline
+    line = {
+        "metric": "Ga bound pair (upper + lower A_H) voxel-iterations/sec on the quadrature grid",
+        "value": m * m * iters / t_pair, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_pair * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "729x729 pixels, 40 seeded circles r~U[10,30], phases 1*I / 100*I; Ga with "
+                               "exact integration on trial grid %dx%d (quadrature grid %dx%d), primal and "
+                               "dual, FP32 inner + FP64 refinement, stop at rel. residual %g"
+                               % (trials[-1][0], trials[-1][0], m, m, args.tol),
+                   "l2": "flushed between solves (512 MiB write)"},
+        "bound_pairs_per_s": 1.0 / t_pair,
+        "gani_729_AH": gani.tolist(),
+        "trials": rows,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.passes_once:
@@ -841,6 +920,8 @@ def main():
         return run_serving(args)
     if args.impl == "ours" and args.workload == "ms":
         return run_ms(args)
+    if args.impl == "ours" and args.workload == "ga":
+        return run_ga(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
