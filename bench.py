@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the library's default launch geometry (no hg_tune before the warm-up)")
     ap.add_argument("--tol", type=float, default=TOL)
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "batched", "serving", "ms", "ga"],
                     help="c2: 729x729 (default, the headline); c3: 135^3 3D; batched: 256 2D "
@@ -208,14 +210,16 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_key):
+def profiled_traffic(kernel_key, geometry=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+    the current kernel source with the launch geometry in use (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         ent = t.get(kernel_key)
         if ent and ent.get("kernel_source_sha") == kernel_source_hash():
+            if geometry is not None and ent.get("launch_geometry") not in (None, geometry):
+                return None
             return ent["dram_bytes_per_launch"]
     except Exception:
         pass
@@ -326,6 +330,12 @@ def run_ours(args):
     # usually suffices at tol = 1e-5
     o_mixed = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=max(0.5 * args.tol, 1e-6))
     o_fp64 = hg.default_opts(tol=args.tol, prec=hg.HG_FP64)
+    # launch geometry: the autotuner (hg_tune) times every tiling of the passes
+    # the kernels accept and keeps the fastest; set-up, outside the timed region
+    tuned = None
+    if not args.no_tune:
+        tuned = {"mixed": g.tune(hg.HG_MIXED, reps=20 if d == 2 else 4),
+                 "fp64": g.tune(hg.HG_FP64, reps=4 if d == 2 else 1)}
 
     def step(opts):
         flush.fill_(1.0)
@@ -435,7 +445,8 @@ def run_ours(args):
     roof = {
         "bound": "hbm", "kernel": dom["kernel"], "achieved": achieved,
         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-        "peak_kind": peak_kind, "traffic": profiled_traffic("fp32_" + keys[dom_pass] + ("" if d == 2 else "_3d")),
+        "peak_kind": peak_kind, "traffic": profiled_traffic("fp32_" + keys[dom_pass] + ("" if d == 2 else "_3d"),
+                                     g.launch_cfg(hg.HG_MIXED)),
         "bytes_per_launch": dom["bytes"], "ms_per_launch": dom_avg_ms, "launches_timed": dom_n,
         "timing": "CUDA events around this pass in the first iteration of every graph chunk (8 iterations) "
                   "inside the captured graphs of the timed solves, on the stream the kernels run on",
@@ -469,6 +480,8 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": int(launches),
+        "launch_geometry": tuned if tuned else {"mixed": g.launch_cfg(hg.HG_MIXED),
+                                                 "fp64": g.launch_cfg(hg.HG_FP64), "tuned": False},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -489,6 +502,7 @@ def run_passes_once(args):
     g = ctx.grid(ms.N)
     g.set_coeffs_phase(ms.phase, ms.table)
     for prec in (hg.HG_MIXED, hg.HG_FP64):
+        print("launch geometry (%s): %s" % ("mixed" if prec == hg.HG_MIXED else "fp64", g.launch_cfg(prec)))
         for p in range(g.num_passes()):
             t, name = g.time_pass(p, prec, reps=1)
             print(f"{name}: {t * 1e3:.1f} us")
@@ -515,6 +529,21 @@ def run_batched(args):
         g.set_coeffs_phase(torch.from_numpy(ms.phase).to(dev), torch.from_numpy(ms.table).to(dev))
         grids.append(g)
     o_mixed = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=max(0.5 * args.tol, 1e-6))
+    # launch geometry per grid size: the first grid of each size is tuned, the
+    # others read the autotuner's cache (set-up, outside the timed region)
+    tune_note = {"tuned": False}
+    if not args.no_tune:
+        import tempfile
+        cache = os.path.join(tempfile.mkdtemp(), "hg_tune.txt")
+        chosen = {}
+        for ms, g in zip(probs, grids):
+            for pr, name in ((hg.HG_MIXED, "mixed"), (hg.HG_FP64, "fp64")):
+                t = g.tune(pr, reps=10, cache_path=cache)
+                if not t["from_cache"]:
+                    chosen["%dx%d %s" % (ms.N[0], ms.N[1], name)] = {
+                        "chosen": t["chosen"], "heuristic": t["heuristic"],
+                        "ms_chosen": t["ms_chosen"], "ms_heuristic": t["ms_heuristic"]}
+        tune_note = {"tuned": True, "per_size": chosen}
     # the plain FP64 path needs a tighter residual for 1e-6 in A_H at contrasts
     # up to 1e4 (its A_H error is about 3e-6 at 1e-5 there, 3e-8 at 1e-6)
     tol64 = args.tol / 5
@@ -541,49 +570,26 @@ def run_batched(args):
     t_total = sum(times)
     solves_per_s = len(grids) * args.steps / t_total
 
-    # the same problems through hg_solve_batch: one batched solve per grid size
-    # (every pass one launch for all problems of that size)
-    groups = {}
-    for i, ms in enumerate(probs):
-        groups.setdefault(ms.N, []).append(i)
-
-    # one context (own stream) per size, the sizes' batches on concurrent host
-    # threads (the binding's foreign calls release the interpreter lock)
-    import threading as th
-    gctx, ggrids = {}, {}
-    for N, idx in groups.items():
-        c = hg.Context(0, use_torch_stream=False)
-        gs = []
-        for i in idx:
-            g = c.grid(N)
-            g.set_coeffs_phase(torch.from_numpy(probs[i].phase).to(dev), torch.from_numpy(probs[i].table).to(dev))
-            gs.append(g)
-        gctx[N], ggrids[N] = c, gs
-
+    # the same problems in ONE hg_solve_batch call: per grid size every pass is
+    # one launch for all its problems, and the CG iterations of all sizes are
+    # one captured CUDA graph (a branch per size) per chunk of iterations
     def batch_kernels():
-        out = [None] * len(grids)
-
-        def run(N):
-            for i, r in zip(groups[N], gctx[N].solve_batch(ggrids[N], o_mixed)):
-                out[i] = r
         t0 = time.perf_counter()
-        ths = [th.Thread(target=run, args=(N,)) for N in groups]
-        for t in ths:
-            t.start()
-        for t in ths:
-            t.join()
+        out = ctx.solve_batch(grids, o_mixed)
         return out, time.perf_counter() - t0
 
     for _ in range(max(1, args.warmup)):
         batch_kernels()
     sampler = ClockSampler(0)
     sampler.start()
+    l0 = ctx.launches()
     bk_times, bk_vox, bk_res = [], 0, None
     for _ in range(args.steps):
         bk_res, t = batch_kernels()
         bk_times.append(t)
         bk_vox += sum(int(np.prod(ms.N)) * sum(r["iters"]) for ms, r in zip(probs, bk_res))
     bk_clocks = sampler.stop()
+    bk_launches = (ctx.launches() - l0) // max(1, args.steps)
     assert all(r["status"] == 0 for r in bk_res)
     bk_total = sum(bk_times)
     bk_solves_per_s = len(grids) * args.steps / bk_total
@@ -617,10 +623,15 @@ def run_batched(args):
         "voxel_iter_per_s": vox / t_total,
         "AH_max_rel_err_vs_fp64_tol1e-10": err,
         "batched_kernels": {"solves_per_s": bk_solves_per_s, "voxel_iter_per_s": bk_vox / bk_total,
-                            "how": "one hg_solve_batch per grid size (every pass one launch for all "
-                                   "problems of that size), the five sizes concurrently on their own "
-                                   "streams; a batch iterates until its slowest problem converges",
+                            "how": "one hg_solve_batch call for all 256 problems: per grid size every "
+                                   "pass one launch for all its problems, the CG iterations of all "
+                                   "sizes one CUDA graph (a branch per size) per 8 iterations; each "
+                                   "problem's FP64 refinement step as soon as its inner FP32 solve "
+                                   "stops; the graph is captured again over the running problems "
+                                   "when they fall to half",
+                            "kernel_launches_per_batch": int(bk_launches),
                             "AH_max_rel_err_vs_fp64_tol1e-10": err_bk, "clocks": bk_clocks},
+        "launch_geometry": tune_note,
         "plain_fp64_per_request": {"solves_per_s": 1.0 / t_fp64, "sample": "32 seeded problems",
                                    "tol": tol64, "AH_max_rel_err_vs_fp64_tol1e-10": err64},
         "mixed_blocking_per_request": {"solves_per_s": 1.0 / t_mixed_seq},
@@ -628,10 +639,6 @@ def run_batched(args):
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
-    for N in ggrids:
-        for g in ggrids[N]:
-            g.close()
-        gctx[N].close()
     for g in grids:
         g.close()
     ctx.close()

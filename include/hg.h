@@ -215,15 +215,19 @@ int hg_set_coeffs_exact(hg_grid* grid, const int* N_trial, const int* P, const u
  * NULL (d*d doubles, row-major); info may be NULL. */
 int hg_solve_AH(hg_grid* grid, const hg_solve_opts* opts, double* AH_out, hg_result* info);
 
-/* Batched blocking solve of n problems of one grid shape (same d, N and Y; each
- * grid with its own coefficients): every pass of the iteration is one launch for
- * all problems (the launch's z index picks the problem), the CG iterations of
- * the batch are captured check_every at a time in one CUDA graph, and each
+/* Batched blocking solve of n problems, each grid with its own shape (d, N,
+ * Y) and coefficients.  Problems of one shape form a group: every pass of the
+ * iteration is one launch for all problems of the group (the launch's z index
+ * picks the problem).  The CG iterations of the whole batch are captured
+ * check_every at a time in one CUDA graph with one branch per group, so the
+ * groups run concurrently and one graph launch steps every problem; each
  * problem keeps its own convergence status, so converged problems drop out of
- * the launches.  results[p] (n entries) is the result of grids[p]; device_ms and
- * wall_ms are those of the whole batch.  Supports HG_CG, HG_PRIMAL, A0 = I,
- * HG_FP64 and HG_MIXED, time_pass = -1 (else HG_ERR_ARG).  Returns the first
- * non-OK status of a problem, or HG_OK. */
+ * the launches.  A group runs with the launch geometry of its first grid.
+ * results[p] (n entries) is the result of grids[p]; device_ms and wall_ms are
+ * those of the whole batch.  Each problem solves its own d loads (those in
+ * loads_mask).  Supports HG_CG, HG_PRIMAL, A0 = I, HG_FP64 and HG_MIXED,
+ * time_pass = -1 (else HG_ERR_ARG); all grids on one context, each at most
+ * once.  Returns the first non-OK status of a problem, or HG_OK. */
 int hg_solve_batch(hg_grid* const* grids, int n, const hg_solve_opts* opts, hg_result* results);
 
 /* Copy e~_load of the last solve (d x |N| doubles, component-major); after an
@@ -277,6 +281,61 @@ int hg_spectrum(hg_grid* grid, const double* u, double* S_out, int prec, int on_
  * kernel attributes, codelet constants): make it before any stream capture. */
 int hg_apply_noalloc(int d, const int* N, const uint8_t* phase, int n_phases,
                      const double* table, const double* u, double* out, void* cuda_stream);
+
+/* ---- launch geometry and its autotuner ------------------------------------
+ * Not in the paper: the paper gives no kernel.  Each CG iteration runs d + 1
+ * passes over the grid (the last-axis forward pass with the A_N p product, the
+ * strided passes with the Gamma_hat projection of Eq. Gamma_hat, the last-axis
+ * inverse pass with the CG update).  How a pass tiles the grid over CTAs
+ * changes its speed, not its result beyond the rounding of the reductions'
+ * partial sums. */
+typedef struct {
+    int row_rb;      /* grid rows (lines along the last axis) staged per CTA by the
+                        last-axis passes (forward and inverse share it)          */
+    int row_lb;      /* loads staged per CTA by the last-axis passes (1..d)      */
+    int lanes[2];    /* pencils per component staged per CTA by the strided pass
+                        of axis a (a = 0, and a = 1 in 3D; 0 where unused), a
+                        power of two                                             */
+} hg_launch_cfg;
+
+/* The grid's current geometry for precision prec (HG_FP64 or HG_MIXED, the
+ * latter meaning the FP32 kernels). */
+int hg_get_launch_cfg(hg_grid* grid, int prec, hg_launch_cfg* out);
+/* Sets it.  HG_ERR_ARG if the kernels cannot run that tile (too many pencils
+ * for shared memory or registers, lanes not a power of two, more rows than the
+ * grid); HG_ERR_BUSY while a ticket holds the grid.  Drops the grid's cached
+ * CUDA graphs of that precision. */
+int hg_set_launch_cfg(hg_grid* grid, int prec, const hg_launch_cfg* cfg);
+
+typedef struct {
+    hg_launch_cfg chosen;      /* geometry set on the grid                        */
+    hg_launch_cfg heuristic;   /* the library's default for this grid             */
+    double ms_chosen;          /* one CG iteration's passes, ms (timed; or the
+                                  cache's record when from_cache)                 */
+    double ms_heuristic;       /* same with the default geometry (0 from cache)   */
+    int candidates;            /* geometries timed (0 from cache)                 */
+    int from_cache;            /* 1: taken from cache_path without timing         */
+} hg_tune_result;
+
+/* Autotuner: times every geometry the kernels can run for this grid shape and
+ * precision (all rows x loads tiles of the last-axis passes, all lane counts of
+ * each strided pass), each over `reps` launches of its passes (CUDA events on
+ * the context stream, best of three), on the grid's own coefficients with
+ * steady-state CG scalars, and sets the fastest (the default unless another is
+ * at least 3% faster: closer timings are within the run-to-run spread).  cache_path (NULL: no cache) is a text file of one
+ * record per line, "hg-tune-v1 <device> <SMs> <prec> <d> <N0> <N1> <N2> <rb>
+ * <lb> <lanes0> <lanes1> <ms>", device = its name with blanks as '_': a record
+ * for this device, shape and precision is applied without timing (the last
+ * such line wins); otherwise the result is appended.  The work buffers are
+ * left with meaningless values (every solve starts from its right-hand side).
+ * Errors: HG_ERR_ARG, HG_ERR_NO_COEFFS, HG_ERR_BUSY, HG_ERR_CUDA. */
+int hg_tune(hg_grid* grid, int prec, int reps, const char* cache_path, hg_tune_result* out);
+
+/* Looks up a record of the cache format above (host only, no device work):
+ * HG_OK and *out if found, HG_ERR_ARG if not (or unreadable); *ms_out (may be
+ * NULL) receives the recorded time. */
+int hg_tune_cache_find(const char* cache_path, const char* device_name, int sm_count, int prec, int d,
+                       const int* N, hg_launch_cfg* out, double* ms_out);
 
 /* Kernel launches made through this context so far (all entry points). */
 long long hg_launch_count(hg_ctx* ctx);

@@ -86,6 +86,23 @@ class Result(ctypes.Structure):
         }
 
 
+class LaunchCfg(ctypes.Structure):
+    _fields_ = [("row_rb", ctypes.c_int), ("row_lb", ctypes.c_int), ("lanes", ctypes.c_int * 2)]
+
+    def to_dict(self) -> dict:
+        return {"row_rb": self.row_rb, "row_lb": self.row_lb, "lanes": list(self.lanes)}
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("chosen", LaunchCfg), ("heuristic", LaunchCfg), ("ms_chosen", ctypes.c_double),
+                ("ms_heuristic", ctypes.c_double), ("candidates", ctypes.c_int), ("from_cache", ctypes.c_int)]
+
+    def to_dict(self) -> dict:
+        return {"chosen": self.chosen.to_dict(), "heuristic": self.heuristic.to_dict(),
+                "ms_chosen": self.ms_chosen, "ms_heuristic": self.ms_heuristic,
+                "candidates": self.candidates, "from_cache": bool(self.from_cache)}
+
+
 _lib = None
 
 # (name, restype, argtypes) of every entry point declared in include/hg.h
@@ -111,6 +128,11 @@ SIGNATURES = [
     ("hg_time_pass", _I, [_VP, _I, _I, _I, ctypes.POINTER(_D), ctypes.c_char_p]),
     ("hg_num_passes", _I, [_VP]),
     ("hg_solve_batch", _I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(SolveOpts), ctypes.POINTER(Result)]),
+    ("hg_get_launch_cfg", _I, [_VP, _I, ctypes.POINTER(LaunchCfg)]),
+    ("hg_set_launch_cfg", _I, [_VP, _I, ctypes.POINTER(LaunchCfg)]),
+    ("hg_tune", _I, [_VP, _I, _I, ctypes.c_char_p, ctypes.POINTER(TuneResult)]),
+    ("hg_tune_cache_find", _I, [ctypes.c_char_p, ctypes.c_char_p, _I, _I, _I, ctypes.POINTER(_I),
+                                ctypes.POINTER(LaunchCfg), ctypes.POINTER(_D)]),
     ("hg_strerror", ctypes.c_char_p, [_I]),
 ]
 
@@ -136,6 +158,17 @@ def load(path: Optional[str] = None):
 def _check(st: int, where: str):
     if st != HG_OK:
         raise HGError(st, where)
+
+
+def tune_cache_find(path: str, device_name: str, sm_count: int, prec: int, N: Sequence[int]):
+    """hg_tune_cache_find: (launch geometry dict, recorded ms) or None."""
+    d = len(N)
+    Narr = (_I * 3)(*(list(N) + [0] * (3 - d)))
+    c = LaunchCfg()
+    ms = ctypes.c_double()
+    st = load().hg_tune_cache_find(path.encode(), device_name.encode(), sm_count, prec, d, Narr,
+                                   ctypes.byref(c), ctypes.byref(ms))
+    return (c.to_dict(), ms.value) if st == HG_OK else None
 
 
 def default_opts(**kw) -> SolveOpts:
@@ -216,7 +249,8 @@ class Context:
 
     def solve_batch(self, grids: Sequence["Grid"], opts: Optional[SolveOpts] = None,
                     raise_on_error: bool = True) -> list:
-        """hg_solve_batch: grids of one shape solved together; one result dict each."""
+        """hg_solve_batch: grids solved together (one launch per pass for each
+        shape, one CUDA graph for all shapes); one result dict each."""
         n = len(grids)
         hs = (_VP * n)(*[g.h for g in grids])
         res = (Result * n)()
@@ -339,6 +373,25 @@ class Grid:
             raise ValueError("spectrum() takes a host array")
         _check(load().hg_spectrum(self.h, pu, out.ctypes.data_as(ctypes.c_void_p), prec, 0), "hg_spectrum")
         return out[..., 0] + 1j * out[..., 1]
+
+    def launch_cfg(self, prec: int = HG_FP64) -> dict:
+        """hg_get_launch_cfg: the passes' tiling for precision prec."""
+        c = LaunchCfg()
+        _check(load().hg_get_launch_cfg(self.h, prec, ctypes.byref(c)), "hg_get_launch_cfg")
+        return c.to_dict()
+
+    def set_launch_cfg(self, prec: int, row_rb: int, row_lb: int, lanes: Sequence[int]):
+        """hg_set_launch_cfg (raises HGError HG_ERR_ARG for a tile the kernels cannot run)."""
+        ln = list(lanes) + [0] * (2 - len(lanes))
+        c = LaunchCfg(row_rb, row_lb, (ctypes.c_int * 2)(*ln))
+        _check(load().hg_set_launch_cfg(self.h, prec, ctypes.byref(c)), "hg_set_launch_cfg")
+
+    def tune(self, prec: int = HG_MIXED, reps: int = 10, cache_path: Optional[str] = None) -> dict:
+        """hg_tune: time every admissible geometry and keep the fastest."""
+        r = TuneResult()
+        _check(load().hg_tune(self.h, prec, reps, cache_path.encode() if cache_path else None, ctypes.byref(r)),
+               "hg_tune")
+        return r.to_dict()
 
     def num_passes(self) -> int:
         return int(load().hg_num_passes(self.h))

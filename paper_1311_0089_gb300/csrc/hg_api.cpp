@@ -93,102 +93,102 @@ int min_radix(const AxisPlanH& pl) {
     return pl.nstages ? r : 1;
 }
 
-// Row pass: choose loads-per-CTA LB and rows-per-CTA RB.
+// Row pass geometry with RB grid rows and LB loads per CTA, if the kernels
+// can run it: the compile-time kernels stage at most ct_npmax complex pencils
+// of 256 threads, the runtime kernels at most MAXB butterflies per thread of
+// at most row_max_threads() threads in max_smem bytes; both keep the offsets
+// of at most MAX_REAL_ROWS_HOST real rows.
+bool make_row_cfg(int prec, int n, int d, int L, int RB, int LB, int minR, size_t csize, int max_smem,
+                  long long rows, RowCfg& cfg) {
+    const int maxb = 2, maxt = row_max_threads();
+    if (RB < 1 || LB < 1 || LB > L || RB > rows) return false;
+    const int nreal = RB * LB * d;
+    const int ncplx = (nreal + 1) / 2;
+    if (nreal > MAX_REAL_ROWS_HOST) return false;
+    if (ct_length(d, n)) {
+        if (ncplx > ct_npmax(prec, n)) return false;
+        cfg.threads = CT_THREADS_HOST;
+        cfg.smem = (int)((size_t)(ncplx + 1) * n * csize);
+        cfg.ct = 1;
+    } else {
+        const long long bfly = std::max<long long>((long long)ncplx * n / std::max(minR, 1), 1);
+        const size_t smem = (size_t)ncplx * n * csize;
+        if (bfly > (long long)maxb * maxt || smem > (size_t)max_smem) return false;
+        int thr = (int)((bfly + maxb - 1) / maxb);
+        cfg.threads = std::max(64, std::min(maxt, ((thr + 31) / 32) * 32));
+        cfg.smem = (int)smem;
+        cfg.ct = 0;
+    }
+    cfg.RB = RB;
+    cfg.LB = LB;
+    cfg.nbx = (rows + RB - 1) / RB;
+    cfg.nby = (L + LB - 1) / LB;
+    return true;
+}
+
+// Row pass: choose loads-per-CTA LB and rows-per-CTA RB.  The most loads per
+// CTA first, then the most rows that keep at least two CTAs per SM (and, for
+// the runtime kernels, at most 32 KB of pencils).
 bool choose_row_cfg(int prec, int n, int d, int L, int minR, size_t csize, int max_smem,
                     long long rows, RowCfg& cfg) {
-    const int maxb = 2, maxt = row_max_threads();
     const size_t target = 32 * 1024;
-    if (ct_length(d, n)) {
-        // compile-time kernel: 256 threads, at most ct_npmax pencils per CTA
-        const int npmax = ct_npmax(prec, n);
-        for (int LB = L; LB >= 1; --LB) {
-            int bestRB = 0;
-            for (int RB = 1; RB <= 64; ++RB) {
-                const int ncplx = (RB * LB * d + 1) / 2;
-                if (ncplx > npmax || RB > rows) break;
-                if (RB > 1 && rows / RB < 2 * 152) break;
-                bestRB = RB;
-            }
-            if (bestRB > 0) {
-                const int ncplx = (bestRB * LB * d + 1) / 2;
-                cfg.RB = bestRB; cfg.LB = LB; cfg.threads = CT_THREADS_HOST;
-                cfg.smem = (int)((size_t)(ncplx + 1) * n * csize);
-                cfg.nbx = (rows + bestRB - 1) / bestRB;
-                cfg.nby = (L + LB - 1) / LB;
-                cfg.ct = 1;
-                return true;
-            }
-        }
-        return false;
-    }
     for (int LB = L; LB >= 1; --LB) {
-        int bestRB = 0;
+        RowCfg best{};
+        bool found = false;
         for (int RB = 1; RB <= 64; ++RB) {
-            const int nreal = RB * LB * d;
-            const int ncplx = (nreal + 1) / 2;
-            const long long bfly = (long long)ncplx * n / std::max(minR, 1);
-            const size_t smem = (size_t)ncplx * n * csize;
-            if (bfly > (long long)maxb * maxt || smem > (size_t)max_smem) break;
-            if (RB > 1 && (smem > target || rows / RB < 2 * 152)) break;
-            if (RB > rows) break;
-            bestRB = RB;
+            RowCfg c{};
+            if (!make_row_cfg(prec, n, d, L, RB, LB, minR, csize, max_smem, rows, c)) break;
+            if (RB > 1 && (rows / RB < 2 * 152 || (!c.ct && (size_t)c.smem > target))) break;
+            best = c;
+            found = true;
         }
-        if (bestRB > 0) {
-            const int nreal = bestRB * LB * d;
-            const int ncplx = (nreal + 1) / 2;
-            const long long bfly = std::max<long long>((long long)ncplx * n / std::max(minR, 1), 1);
-            int thr = (int)((bfly + maxb - 1) / maxb);
-            thr = std::max(64, std::min(maxt, ((thr + 31) / 32) * 32));
-            cfg.RB = bestRB;
-            cfg.LB = LB;
-            cfg.threads = thr;
-            cfg.smem = (int)((size_t)ncplx * n * csize);
-            cfg.nbx = (rows + bestRB - 1) / bestRB;
-            cfg.nby = (L + LB - 1) / LB;
-            cfg.ct = 0;
+        if (found) {
+            cfg = best;
             return true;
         }
     }
     return false;
 }
 
+// Strided pass geometry with Cl lanes (pencils per component, a power of two)
+// per CTA, if the kernels can run it.
+bool make_str_cfg(int prec, int n, int d, int Cl, int minR, size_t csize, int max_smem, long long inner,
+                  StrCfg& cfg) {
+    const int maxb = 2, maxt = row_max_threads();
+    if (Cl < 1 || (Cl & (Cl - 1)) || (Cl > 1 && Cl > inner)) return false;
+    if (ct_length(d, n)) {
+        if (d * Cl > ct_npmax(prec, n) || Cl > ct_max_lanes(d)) return false;
+        cfg.threads = CT_THREADS_HOST;
+        cfg.smem = (int)((size_t)(d * Cl + 1) * n * csize);
+        cfg.ct = 1;
+    } else {
+        if (Cl > 32) return false;
+        const long long bfly = std::max<long long>((long long)d * Cl * n / std::max(minR, 1), 1);
+        const size_t smem = (size_t)d * Cl * n * csize;
+        if (bfly > (long long)maxb * maxt || smem > (size_t)max_smem) return false;
+        int thr = (int)((bfly + maxb - 1) / maxb);
+        cfg.threads = std::max(64, std::min(maxt, ((thr + 31) / 32) * 32));
+        cfg.smem = (int)smem;
+        cfg.ct = 0;
+    }
+    cfg.Cl = Cl;
+    return true;
+}
+
 bool choose_str_cfg(int prec, int n, int d, int minR, size_t csize, int max_smem,
                     long long inner, long long outer, int L, StrCfg& cfg) {
-    const int maxb = 2, maxt = row_max_threads();
     const int prefer_lanes = 2;   // more, smaller CTAs beat full 32-byte rows here
-    if (ct_length(d, n)) {
-        const int npmax = ct_npmax(prec, n);
-        int best = 0;
-        for (int Cl = 1; Cl <= 16; Cl *= 2) {   // powers of two (lane = tid & (Cl-1))
-            if (d * Cl > npmax || (Cl > 1 && Cl > inner)) break;
-            if (Cl > prefer_lanes && ((inner + Cl - 1) / Cl) * outer * L < 4 * 152) break;
-            if (Cl > 2 * prefer_lanes || Cl > ct_max_lanes(d)) break;
-            best = Cl;
-        }
-        if (!best) return false;
-        cfg.Cl = best;
-        cfg.threads = CT_THREADS_HOST;
-        cfg.smem = (int)((size_t)(d * best + 1) * n * csize);
-        cfg.ct = 1;
-        return true;
-    }
+    const bool ct = ct_length(d, n);
     int best = 0;
-    for (int Cl = 1; Cl <= 32; Cl *= 2) {   // powers of two (lane = tid & (Cl-1))
-        const long long bfly = (long long)d * Cl * n / std::max(minR, 1);
-        const size_t smem = (size_t)d * Cl * n * csize;
-        if (bfly > (long long)maxb * maxt || smem > (size_t)max_smem) break;
-        if (Cl > 1 && (Cl > prefer_lanes || Cl > inner)) break;
+    for (int Cl = 1; Cl <= 32; Cl *= 2) {
+        StrCfg c{};
+        if (!make_str_cfg(prec, n, d, Cl, minR, csize, max_smem, inner, c)) break;
+        if (Cl > prefer_lanes && (!ct || ((inner + Cl - 1) / Cl) * outer * L < 4 * 152)) break;
+        if (Cl > 2 * prefer_lanes) break;
         best = Cl;
+        cfg = c;
     }
-    if (!best) return false;
-    const long long bfly = std::max<long long>((long long)d * best * n / std::max(minR, 1), 1);
-    int thr = (int)((bfly + maxb - 1) / maxb);
-    thr = std::max(64, std::min(maxt, ((thr + 31) / 32) * 32));
-    cfg.Cl = best;
-    cfg.threads = thr;
-    cfg.smem = (int)((size_t)d * best * n * csize);
-    cfg.ct = 0;
-    return true;
+    return best > 0;
 }
 
 // ----------------------------------------------------------------------------
@@ -309,6 +309,25 @@ int grid_alloc_common(hg_grid* g) {
     if ((st = dev_alloc(g->ctx, (void**)&g->d_A0, 16 * sizeof(double)))) return st;
     HG_CU(cudaStreamSynchronize(g->ctx->stream));
     (void)gd;
+    return HG_OK;
+}
+
+int grid_ensure_partial(hg_grid* g, long long nbx) {
+    int st;
+    if ((st = grid_alloc_common(g))) return st;
+    const long long need = nbx * MAXL;
+    if (need <= g->partial_slots) return HG_OK;
+    double* fresh = nullptr;
+    if ((st = dev_alloc(g->ctx, (void**)&fresh, (size_t)need * sizeof(double)))) return st;
+    HG_CU(cudaStreamSynchronize(g->ctx->stream));
+    dev_free(g->ctx, g->partial);
+    g->partial = fresh;
+    g->partial_slots = need;
+    // cached CG graphs hold the old pointer
+    for (int p = 0; p < 2; ++p) {
+        if (g->graphs[p].exec) cudaGraphExecDestroy(g->graphs[p].exec);
+        g->graphs[p] = GraphCache();
+    }
     return HG_OK;
 }
 

@@ -1,15 +1,17 @@
-// hg_solve_batch: many problems of one grid shape stepped together.
+// hg_solve_batch: many problems stepped together.
 //
-// Every pass of the CG iteration (and of the right-hand side, the projection
-// of the correction and the FP64 residual) is one launch for all P problems:
-// the pass kernels take the arguments of problem p from a device array
-// (grid z = problem), so a batch of small grids fills the GPU in one launch
-// where P single solves would each be bound by launch latency.  The CG
-// iterations are captured `check_every` at a time in one CUDA graph for the
-// whole batch; each problem keeps its own scalars, convergence status and
-// reduction slots, and a converged problem's tiles exit at once.  The small
-// per-problem steps (scalar set-up, inner set-up, x64 += delta, A_H) are
-// plain per-grid launches.
+// Problems of one grid shape form a group.  Every pass of the CG iteration
+// (and of the right-hand side, the projection of the correction and the FP64
+// residual) is one launch for all problems of a group: the pass kernels take
+// the arguments of problem p from a device array (grid z = problem), so a
+// group of small grids fills the GPU in one launch where single solves would
+// each be bound by launch latency.  The CG iterations of the whole batch are
+// captured `check_every` at a time in ONE CUDA graph with one branch per
+// group, so the groups' passes overlap on the device and one graph launch
+// steps every problem; each problem keeps its own scalars, convergence status
+// and reduction slots, and a converged problem's tiles exit at once.  The
+// small per-problem steps (scalar set-up, inner set-up, x64 += delta, A_H)
+// are plain per-grid launches.
 #include "hg.h"
 #include "hg_internal.h"
 #include "hg_runtime.h"
@@ -101,67 +103,125 @@ int launch_batch(hg_grid* g0, int prec, const BatchItems& it, int P, cudaStream_
     return HG_OK;
 }
 
-struct Batch {
+// Problems of one grid shape: every pass one launch for all of them.
+struct Group {
     std::vector<hg_grid*> gs;
+    std::vector<int> pos;        // their positions in the batch
+    int P = 0, L = 0;
+    cudaStream_t side = nullptr; // capture branch of this group
+    cudaEvent_t join = nullptr;
+};
+
+struct Batch {
+    std::vector<hg_grid*> gs;    // every problem, in the caller's order
+    std::vector<Group> groups;
     hg_solve_opts o{};
-    int P = 0, L = 0, prec = 0;
+    int P = 0, prec = 0;
     cudaStream_t s = nullptr;
     Arena ar;
-    const Scalars** d_src_outer = nullptr;   // per-problem scalar pointers (device)
-    const Scalars** d_src_inner = nullptr;
+    const Scalars** d_src = nullptr;         // per-problem outer, then inner, scalar pointers (device)
     Scalars* d_gather = nullptr;
     Scalars* h_gather = nullptr;              // pinned
     cudaGraphExec_t cg_exec = nullptr;
+    long long nk = 0;                        // launches per iteration of the captured graph
+    cudaEvent_t fork = nullptr;
     ~Batch() {
         if (cg_exec) cudaGraphExecDestroy(cg_exec);
         if (h_gather) cudaFreeHost(h_gather);
+        for (Group& gr : groups) {
+            if (gr.join) cudaEventDestroy(gr.join);
+            if (gr.side) cudaStreamDestroy(gr.side);
+        }
+        if (fork) cudaEventDestroy(fork);
     }
 };
 
-// Copies every problem's scalars (inner or outer) to b.h_gather.
+// Copies every problem's outer scalars (inner = false) to h_gather[0, P), or
+// the outer and the inner ones (inner = true) to h_gather[0, P) and [P, 2P).
 int read_scalars(Batch& b, bool inner) {
-    HG_CU(launch_gather_scalars(inner ? b.d_src_inner : b.d_src_outer, b.d_gather, b.P, b.s));
-    HG_CU(cudaMemcpyAsync(b.h_gather, b.d_gather, sizeof(Scalars) * MAXL * b.P, cudaMemcpyDeviceToHost, b.s));
+    const int n = inner ? 2 * b.P : b.P;
+    HG_CU(launch_gather_scalars(b.d_src, b.d_gather, n, b.s));
+    HG_CU(cudaMemcpyAsync(b.h_gather, b.d_gather, sizeof(Scalars) * MAXL * n, cudaMemcpyDeviceToHost, b.s));
     HG_CU(cudaStreamSynchronize(b.s));
     return HG_OK;
 }
 
-bool any_status(const Batch& b, int status) {
-    for (int p = 0; p < b.P; ++p)
-        for (int l = 0; l < b.L; ++l)
-            if (b.h_gather[p * MAXL + l].status == status) return true;
+bool any_load(const Batch& b, int p, bool inner, int status) {
+    const Scalars* h = b.h_gather + (size_t)(inner ? b.P + p : p) * MAXL;
+    for (int l = 0; l < b.gs[p]->gd.d; ++l)
+        if (h[l].status == status) return true;
     return false;
 }
 
-int make_items(Batch& b, BatchItems* it, int prec, const void* const* u, bool unit_loads, bool withA,
+int make_items(Batch& b, Group& gr, BatchItems* it, int prec, const void* const* u, bool unit_loads, bool withA,
                int inv_mode, bool outer_status) {
-    std::vector<PassArgs> pas(b.P);
-    for (int p = 0; p < b.P; ++p) {
-        hg_grid* g = b.gs[p];
-        matvec_args(g, prec, b.L, u ? u[p] : nullptr, unit_loads, withA, nullptr, nullptr, inv_mode, nullptr, 1,
+    std::vector<PassArgs> pas(gr.P);
+    for (int p = 0; p < gr.P; ++p) {
+        hg_grid* g = gr.gs[p];
+        matvec_args(g, prec, gr.L, u ? u[p] : nullptr, unit_loads, withA, nullptr, nullptr, inv_mode, nullptr, 1,
                     outer_status ? g->work[0].sc : nullptr, &pas[p]);
     }
     return upload_items(b.ar, pas, b.s, it);
 }
 
-// The CUDA graph of check_every batched CG iterations of precision prec.
-int make_cg_graph(Batch& b, int prec) {
-    std::vector<PassArgs> pas(b.P);
-    for (int p = 0; p < b.P; ++p) cg_iteration_args(b.gs[p], prec, b.L, &pas[p]);
-    BatchItems it;
+// The CUDA graph of check_every batched CG iterations of precision prec over
+// the problems marked in `member`: one branch per grid shape (the shapes'
+// passes overlap on the device), each a chain of that shape's batched
+// launches with its group's launch geometry.  Returns the problems captured.
+int make_cg_graph(Batch& b, int prec, const std::vector<char>& member, int* captured) {
+    const size_t G = b.groups.size();
+    std::vector<BatchItems> its(G);
+    std::vector<int> cnt(G, 0);
     int st;
-    if ((st = upload_items(b.ar, pas, b.s, &it))) return st;
+    *captured = 0;
+    for (size_t k = 0; k < G; ++k) {
+        Group& gr = b.groups[k];
+        std::vector<PassArgs> pas;
+        for (int p = 0; p < gr.P; ++p) {
+            if (!member[gr.pos[p]]) continue;
+            pas.emplace_back();
+            cg_iteration_args(gr.gs[p], prec, gr.L, &pas.back());
+        }
+        cnt[k] = (int)pas.size();
+        *captured += cnt[k];
+        if (cnt[k] && (st = upload_items(b.ar, pas, b.s, &its[k]))) return st;
+    }
     HG_CU(cudaStreamSynchronize(b.s));
     hg_ctx* c = b.gs[0]->ctx;
     cudaStream_t cs = c->cap_stream;
     const long long before = c->launches.load();
+    const int chunk = std::max(1, b.o.check_every);
+    b.nk = 0;
     HG_CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < std::max(1, b.o.check_every) && st == HG_OK; ++i) st = launch_batch(b.gs[0], prec, it, b.P, cs);
+    cudaError_t e = cudaEventRecord(b.fork, cs);
+    st = HG_OK;
+    int on_cs = -1;   // the first captured group runs on the capture stream itself
+    for (size_t k = 0; k < G && e == cudaSuccess && st == HG_OK; ++k) {
+        if (!cnt[k]) continue;
+        Group& gr = b.groups[k];
+        b.nk += gr.gs[0]->gd.d + 1;
+        cudaStream_t ss = cs;
+        if (on_cs < 0) {
+            on_cs = (int)k;
+        } else {
+            ss = gr.side;
+            e = cudaStreamWaitEvent(ss, b.fork, 0);
+        }
+        for (int i = 0; i < chunk && e == cudaSuccess && st == HG_OK; ++i)
+            st = launch_batch(gr.gs[0], prec, its[k], cnt[k], ss);
+        if (ss != cs && e == cudaSuccess) e = cudaEventRecord(gr.join, ss);
+    }
+    for (size_t k = 0; k < G && e == cudaSuccess; ++k)
+        if (cnt[k] && (int)k != on_cs) e = cudaStreamWaitEvent(cs, b.groups[k].join, 0);
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     c->launches -= c->launches.load() - before;   // capture is not execution
-    if (st) { if (graph) cudaGraphDestroy(graph); return st; }
-    if (e != cudaSuccess) { set_last_cuda_error(e, "cudaStreamEndCapture"); return HG_ERR_CUDA; }
+    if (st || e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (st) return st;
+        set_last_cuda_error(e != cudaSuccess ? e : e2, "batched CG graph capture");
+        return HG_ERR_CUDA;
+    }
     if (b.cg_exec) { cudaGraphExecDestroy(b.cg_exec); b.cg_exec = nullptr; }
     e = cudaGraphInstantiate(&b.cg_exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -169,65 +229,131 @@ int make_cg_graph(Batch& b, int prec) {
     return HG_OK;
 }
 
-// Runs graph chunks until no system of the batch is active (inner scalars for
-// the mixed path, outer for FP64) or max_iter + 2 chunks have been launched.
-int run_cg(Batch& b, bool inner) {
+// The FP64 refinement step of one problem of the mixed path, enqueued as
+// soon as its inner FP32 solve has stopped (the steps of its single solve):
+// delta <- Gamma_N delta (FP32), x64 += delta, x64 <- Gamma_N x64 (FP64, tol
+// < 1e-8), r = -G A (E + x64) (FP64), and the next inner start, which is
+// idle for the loads the residual found converged.  No host sync: the next
+// graph chunk sees the new inner status.
+int refine_one(Batch& b, hg_grid* g) {
+    const GridDev& gd = g->gd;
+    const int L = gd.d;
+    hg_ctx* c = g->ctx;
+    int st = enqueue_matvec(g, 1, L, g->work[1].x, false, false, nullptr, nullptr, INV_PROJ, nullptr, 1, b.s,
+                            g->work[0].sc);
+    if (st) return st;
+    HG_CU(launch_outer_update(gd, L, (double*)g->work[0].x, (const float*)g->work[1].x, g->work[0].sc,
+                              g->work[1].sc, b.s));
+    c->launches++;
+    if (b.o.tol < 1e-8 &&
+        (st = enqueue_matvec(g, 0, L, g->work[0].x, false, false, nullptr, nullptr, INV_PROJ, nullptr, 1, b.s)))
+        return st;
+    if ((st = enqueue_matvec(g, 0, L, g->work[0].x, true, true, nullptr, nullptr, INV_RESID, nullptr, 1, b.s)))
+        return st;
+    HG_CU(launch_inner_init(gd, L, (const double*)g->work[0].r, (float*)g->work[1].r, (float*)g->work[1].p,
+                            (float*)g->work[1].x, g->work[0].sc, g->work[1].sc, b.o.inner_tol, b.o.max_iter, 64,
+                            grid_weight(g), g->partial, g->counters + 4, b.s));
+    c->launches++;
+    return HG_OK;
+}
+
+// Steps the batch in graph chunks until no problem is active.  FP64: the CG
+// of every problem.  Mixed: the inner FP32 CG in the graph, and each
+// problem's refinement step as soon as its inner solve has stopped, so the
+// problems progress independently (continuous batching inside the batch).
+// When the problems still running fall to 3/4 of those captured, the graph
+// is captured again over them alone (converged problems cost no launches).
+int run_batch(Batch& b) {
+    const bool mixed = b.prec == 1;
     const int chunk = std::max(1, b.o.check_every);
-    const long long nk = (long long)(b.gs[0]->gd.d + 1);
-    for (long long launched = 0;; launched += chunk) {
+    std::vector<char> member(b.P, 1);
+    int captured = 0, st;
+    if ((st = make_cg_graph(b, b.prec, member, &captured))) return st;
+    const long long max_chunks =
+        (mixed ? (long long)std::max(1, b.o.max_outer) : 1LL) * ((long long)b.o.max_iter / chunk + 3);
+    for (long long k = 0;; ++k) {
         HG_CU(cudaGraphLaunch(b.cg_exec, b.s));
-        b.gs[0]->ctx->launches += nk * chunk;
-        int st = read_scalars(b, inner);
-        if (st) return st;
-        if (!any_status(b, ST_ACTIVE) || launched + chunk > (long long)b.o.max_iter + 2 * chunk) break;
+        b.gs[0]->ctx->launches += b.nk * chunk;
+        if ((st = read_scalars(b, mixed))) return st;
+        int running = 0;
+        for (int p = 0; p < b.P; ++p) {
+            member[p] = 0;
+            if (!any_load(b, p, false, ST_ACTIVE)) continue;
+            member[p] = 1;
+            ++running;
+            if (!mixed || any_load(b, p, true, ST_ACTIVE)) continue;
+            // inner solve stopped: refine, unless the refinement steps are spent
+            // (the outer scalars count them)
+            const Scalars* ho = b.h_gather + (size_t)p * MAXL;
+            int steps = 0;
+            for (int l = 0; l < b.gs[p]->gd.d; ++l)
+                if (ho[l].status == ST_ACTIVE) steps = std::max(steps, ho[l].iters);
+            if (steps >= std::max(1, b.o.max_outer)) {
+                member[p] = 0;
+                --running;
+                continue;
+            }
+            if ((st = refine_one(b, b.gs[p]))) return st;
+        }
+        if (running == 0 || k + 1 >= max_chunks) break;
+        if (4 * running <= 3 * captured && (st = make_cg_graph(b, b.prec, member, &captured))) return st;
     }
     return HG_OK;
 }
 
+void load_status(const Batch& b, int L, int* init_st) {
+    for (int l = 0; l < MAXL; ++l) init_st[l] = (l < L && ((b.o.loads_mask >> l) & 1u)) ? ST_ACTIVE : ST_IDLE;
+}
+
 int start_rhs(Batch& b, bool fp32) {
-    int init_st[MAXL];
-    for (int l = 0; l < MAXL; ++l) init_st[l] = (l < b.L && ((b.o.loads_mask >> l) & 1u)) ? ST_ACTIVE : ST_IDLE;
     for (hg_grid* g : b.gs) {
-        HG_CU(launch_init_scalars(g->work[0].sc, b.L, init_st, b.o.tol, b.prec ? b.o.max_outer : b.o.max_iter,
+        int init_st[MAXL];
+        load_status(b, g->gd.d, init_st);
+        HG_CU(launch_init_scalars(g->work[0].sc, g->gd.d, init_st, b.o.tol, b.prec ? b.o.max_outer : b.o.max_iter,
                                   0.0, 1.0, b.s));
         g->ctx->launches++;
     }
-    BatchItems it;
     int st;
-    if (!fp32) {
-        if ((st = make_items(b, &it, 0, nullptr, true, true, INV_RHS, false))) return st;
-        if ((st = launch_batch(b.gs[0], 0, it, b.P, b.s))) return st;
-        if (b.prec == 0) return HG_OK;
-        for (hg_grid* g : b.gs) {
-            const GridDev& gd = g->gd;
-            HG_CU(launch_inner_init(gd, b.L, (const double*)g->work[0].r, (float*)g->work[1].r, (float*)g->work[1].p,
-                                    (float*)g->work[1].x, g->work[0].sc, g->work[1].sc, b.o.inner_tol, b.o.max_iter,
-                                    64, grid_weight(g), g->partial, g->counters + 4, b.s));
+    for (Group& gr : b.groups) {
+        BatchItems it;
+        if (!fp32) {
+            if ((st = make_items(b, gr, &it, 0, nullptr, true, true, INV_RHS, false))) return st;
+            if ((st = launch_batch(gr.gs[0], 0, it, gr.P, b.s))) return st;
+            if (b.prec == 0) continue;
+            for (hg_grid* g : gr.gs) {
+                const GridDev& gd = g->gd;
+                HG_CU(launch_inner_init(gd, gr.L, (const double*)g->work[0].r, (float*)g->work[1].r,
+                                        (float*)g->work[1].p, (float*)g->work[1].x, g->work[0].sc, g->work[1].sc,
+                                        b.o.inner_tol, b.o.max_iter, 64, grid_weight(g), g->partial,
+                                        g->counters + 4, b.s));
+                g->ctx->launches++;
+            }
+            continue;
+        }
+        for (hg_grid* g : gr.gs)
+            HG_CU(cudaMemsetAsync(g->work[0].x, 0, sizeof(double) * (size_t)gr.L * g->gd.d * g->gd.M, b.s));
+        if ((st = make_items(b, gr, &it, 1, nullptr, true, true, INV_RHS, true))) return st;
+        if ((st = launch_batch(gr.gs[0], 1, it, gr.P, b.s))) return st;
+        for (hg_grid* g : gr.gs) {
+            HG_CU(launch_inner_init(g->gd, gr.L, nullptr, nullptr, nullptr, nullptr, g->work[0].sc, g->work[1].sc,
+                                    b.o.inner_tol, b.o.max_iter, 64, grid_weight(g), g->partial, g->counters + 4,
+                                    b.s));
             g->ctx->launches++;
         }
-        return HG_OK;
-    }
-    for (hg_grid* g : b.gs)
-        HG_CU(cudaMemsetAsync(g->work[0].x, 0, sizeof(double) * (size_t)b.L * g->gd.d * g->gd.M, b.s));
-    if ((st = make_items(b, &it, 1, nullptr, true, true, INV_RHS, true))) return st;
-    if ((st = launch_batch(b.gs[0], 1, it, b.P, b.s))) return st;
-    for (hg_grid* g : b.gs) {
-        HG_CU(launch_inner_init(g->gd, b.L, nullptr, nullptr, nullptr, nullptr, g->work[0].sc, g->work[1].sc,
-                                b.o.inner_tol, b.o.max_iter, 64, grid_weight(g), g->partial, g->counters + 4, b.s));
-        g->ctx->launches++;
     }
     return HG_OK;
 }
 
 // One problem's right-hand side in FP64 and its inner start from it.
 int restart_rhs64(Batch& b, hg_grid* g) {
+    const int L = g->gd.d;
     int init_st[MAXL];
-    for (int l = 0; l < MAXL; ++l) init_st[l] = (l < b.L && ((b.o.loads_mask >> l) & 1u)) ? ST_ACTIVE : ST_IDLE;
-    HG_CU(launch_init_scalars(g->work[0].sc, b.L, init_st, b.o.tol, b.o.max_outer, 0.0, 1.0, b.s));
+    load_status(b, L, init_st);
+    HG_CU(launch_init_scalars(g->work[0].sc, L, init_st, b.o.tol, b.o.max_outer, 0.0, 1.0, b.s));
     g->ctx->launches++;
-    int st = enqueue_matvec(g, 0, b.L, nullptr, true, true, nullptr, nullptr, INV_RHS, nullptr, 1, b.s);
+    int st = enqueue_matvec(g, 0, L, nullptr, true, true, nullptr, nullptr, INV_RHS, nullptr, 1, b.s);
     if (st) return st;
-    HG_CU(launch_inner_init(g->gd, b.L, (const double*)g->work[0].r, (float*)g->work[1].r, (float*)g->work[1].p,
+    HG_CU(launch_inner_init(g->gd, L, (const double*)g->work[0].r, (float*)g->work[1].r, (float*)g->work[1].p,
                             (float*)g->work[1].x, g->work[0].sc, g->work[1].sc, b.o.inner_tol, b.o.max_iter, 64,
                             grid_weight(g), g->partial, g->counters + 4, b.s));
     g->ctx->launches++;
@@ -249,75 +375,51 @@ int solve_batch(Batch& b, hg_result* results) {
     const double t0 = wall_ms();
     const long long launches0 = c->launches.load();
     int st;
-    for (hg_grid* g : b.gs) {
-        if ((st = grid_alloc_common(g))) return st;
-        if ((st = grid_alloc_work(g, 0))) return st;
-        if (b.prec == 1 && (st = grid_alloc_work(g, 1))) return st;
-        g->form = 0;
-        g->has_ref = 0;
+    for (Group& gr : b.groups) {
+        // every problem of a group runs its first problem's launch geometry:
+        // its reduction slots must hold that many CTAs
+        hg_grid* lead = gr.gs[0];
+        const long long nbx = std::max(lead->rowcfg[0].nbx, lead->rowcfg[1].nbx);
+        for (hg_grid* g : gr.gs) {
+            if ((st = grid_alloc_common(g))) return st;
+            if ((st = grid_ensure_partial(g, nbx))) return st;
+            if ((st = grid_alloc_work(g, 0))) return st;
+            if (b.prec == 1 && (st = grid_alloc_work(g, 1))) return st;
+            g->form = 0;
+            g->has_ref = 0;
+        }
+        HG_CU(cudaStreamCreateWithFlags(&gr.side, cudaStreamNonBlocking));
+        HG_CU(cudaEventCreateWithFlags(&gr.join, cudaEventDisableTiming));
     }
-    // per-problem scalar pointers for the gathers
-    std::vector<const Scalars*> outer(b.P), inner(b.P);
+    HG_CU(cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming));
+    // per-problem scalar pointers for the gathers: outer, then inner
+    std::vector<const Scalars*> src(2 * b.P);
     for (int p = 0; p < b.P; ++p) {
-        outer[p] = b.gs[p]->work[0].sc;
-        inner[p] = b.gs[p]->work[b.prec].sc;
+        src[p] = b.gs[p]->work[0].sc;
+        src[b.P + p] = b.gs[p]->work[b.prec].sc;
     }
-    if ((st = b.ar.get(b.P * sizeof(Scalars*), (void**)&b.d_src_outer))) return st;
-    if ((st = b.ar.get(b.P * sizeof(Scalars*), (void**)&b.d_src_inner))) return st;
-    if ((st = b.ar.get(b.P * MAXL * sizeof(Scalars), (void**)&b.d_gather))) return st;
-    HG_CU(cudaMallocHost((void**)&b.h_gather, b.P * MAXL * sizeof(Scalars)));
-    HG_CU(cudaMemcpyAsync(b.d_src_outer, outer.data(), b.P * sizeof(Scalars*), cudaMemcpyHostToDevice, b.s));
-    HG_CU(cudaMemcpyAsync(b.d_src_inner, inner.data(), b.P * sizeof(Scalars*), cudaMemcpyHostToDevice, b.s));
+    if ((st = b.ar.get(2 * b.P * sizeof(Scalars*), (void**)&b.d_src))) return st;
+    if ((st = b.ar.get(2 * b.P * MAXL * sizeof(Scalars), (void**)&b.d_gather))) return st;
+    HG_CU(cudaMallocHost((void**)&b.h_gather, 2 * b.P * MAXL * sizeof(Scalars)));
+    HG_CU(cudaMemcpyAsync(b.d_src, src.data(), 2 * b.P * sizeof(Scalars*), cudaMemcpyHostToDevice, b.s));
     HG_CU(cudaEventRecord(g0->ev0, b.s));
 
-    if ((st = make_cg_graph(b, b.prec))) return st;
     if (b.prec == 0) {
         if ((st = start_rhs(b, false))) return st;
-        if ((st = run_cg(b, false))) return st;
     } else {
         if ((st = start_rhs(b, true))) return st;
-        // FP32 projection, FP64 projection (tol < 1e-8) and FP64 residual items
-        std::vector<const void*> x32(b.P), x64(b.P);
-        for (int p = 0; p < b.P; ++p) { x32[p] = b.gs[p]->work[1].x; x64[p] = b.gs[p]->work[0].x; }
-        BatchItems proj32, proj64, resid;
-        if ((st = make_items(b, &proj32, 1, x32.data(), false, false, INV_PROJ, true))) return st;
-        if ((st = make_items(b, &proj64, 0, x64.data(), false, false, INV_PROJ, false))) return st;
-        if ((st = make_items(b, &resid, 0, x64.data(), true, true, INV_RESID, false))) return st;
         // a problem whose FP32 right-hand side is too small to decide the zero
         // test starts over with the FP64 one, as its single solve does
         if ((st = read_scalars(b, false))) return st;
-        for (int p = 0; p < b.P; ++p) {
-            bool recheck = false;
-            for (int l = 0; l < b.L; ++l) recheck |= b.h_gather[p * MAXL + l].status == ST_RHS_RECHECK;
-            if (recheck && (st = restart_rhs64(b, b.gs[p]))) return st;
-        }
-        for (int outer_it = 0;;) {
-            if ((st = run_cg(b, true))) return st;
-            if ((st = launch_batch(g0, 1, proj32, b.P, b.s))) return st;
-            for (hg_grid* g : b.gs) {
-                HG_CU(launch_outer_update(g->gd, b.L, (double*)g->work[0].x, (const float*)g->work[1].x,
-                                          g->work[0].sc, g->work[1].sc, b.s));
-                c->launches++;
-            }
-            if (b.o.tol < 1e-8 && (st = launch_batch(g0, 0, proj64, b.P, b.s))) return st;
-            if ((st = launch_batch(g0, 0, resid, b.P, b.s))) return st;
-            if ((st = read_scalars(b, false))) return st;
-            ++outer_it;
-            if (!any_status(b, ST_ACTIVE) || outer_it >= std::max(1, b.o.max_outer)) break;
-            for (hg_grid* g : b.gs) {
-                HG_CU(launch_inner_init(g->gd, b.L, (const double*)g->work[0].r, (float*)g->work[1].r,
-                                        (float*)g->work[1].p, (float*)g->work[1].x, g->work[0].sc, g->work[1].sc,
-                                        b.o.inner_tol, b.o.max_iter, 64, grid_weight(g), g->partial,
-                                        g->counters + 4, b.s));
-                c->launches++;
-            }
-        }
+        for (int p = 0; p < b.P; ++p)
+            if (any_load(b, p, false, ST_RHS_RECHECK) && (st = restart_rhs64(b, b.gs[p]))) return st;
     }
+    if ((st = run_batch(b))) return st;
     // A_H per problem, then every problem's outer scalars
     for (hg_grid* g : b.gs) {
         const GridDev& gd = g->gd;
-        HG_CU(launch_energy(gd, b.L, coeffs_for(g, 0, true), (const double*)g->work[0].x, b.o.loads_mask,
-                            g->partial, g->counters + 5, g->d_AH, b.s));
+        HG_CU(launch_energy(gd, gd.d, coeffs_for(g, 0, true), (const double*)g->work[0].x,
+                            b.o.loads_mask & ((1u << gd.d) - 1u), g->partial, g->counters + 5, g->d_AH, b.s));
         c->launches++;
         HG_CU(cudaMemcpyAsync(g->h_AH, g->d_AH, sizeof(double) * 2 * gd.d * gd.d, cudaMemcpyDeviceToHost, b.s));
     }
@@ -335,7 +437,7 @@ int solve_batch(Batch& b, hg_result* results) {
         r.d = gd.d;
         for (int i = 0; i < gd.d * gd.d; ++i) { r.AH[i] = g->h_AH[i]; r.AH_flux[i] = g->h_AH[gd.d * gd.d + i]; }
         int res = HG_OK;
-        for (int l = 0; l < b.L; ++l) {
+        for (int l = 0; l < gd.d; ++l) {
             const Scalars& sc = b.h_gather[p * MAXL + l];
             const int ms = map_status(sc.status);
             if (b.prec == 0) {
@@ -357,6 +459,13 @@ int solve_batch(Batch& b, hg_result* results) {
     return overall;
 }
 
+bool same_shape(const hg_grid* a, const hg_grid* b) {
+    if (a->gd.d != b->gd.d) return false;
+    for (int k = 0; k < 3; ++k)
+        if (a->gd.N[k] != b->gd.N[k] || a->gd.Y[k] != b->gd.Y[k]) return false;
+    return true;
+}
+
 }  // namespace
 
 extern "C" int hg_solve_batch(hg_grid* const* grids, int n, const hg_solve_opts* opts, hg_result* results) {
@@ -365,31 +474,43 @@ extern "C" int hg_solve_batch(hg_grid* const* grids, int n, const hg_solve_opts*
     if (!g0) return HG_ERR_ARG;
     hg_solve_opts o;
     if (opts) o = *opts; else hg_default_opts(&o);
-    int st = validate_solve_opts(g0, &o);
-    if (st) return st;
-    if (o.method != HG_CG || o.formulation != HG_PRIMAL || o.A0[0] != 0.0 || o.time_pass != -1) return HG_ERR_ARG;
     hg_ctx* c = g0->ctx;
     for (int p = 0; p < n; ++p) {
-        const hg_grid* g = grids[p];
-        if (!g || g->ctx != c || g->gd.d != g0->gd.d) return HG_ERR_ARG;
-        for (int a = 0; a < 3; ++a)
-            if (g->gd.N[a] != g0->gd.N[a] || g->gd.Y[a] != g0->gd.Y[a]) return HG_ERR_ARG;
+        hg_grid* g = grids[p];
+        if (!g || g->ctx != c) return HG_ERR_ARG;
+        hg_solve_opts og = o;
+        int st = validate_solve_opts(g, &og);
+        if (st) return st;
         if (g->coeff_mode < 0) return HG_ERR_NO_COEFFS;
         if (g->borrowed.load() > 0) return HG_ERR_BUSY;
         for (int q = 0; q < p; ++q)
             if (grids[q] == g) return HG_ERR_ARG;   // each problem needs its own buffers
     }
+    if (o.method != HG_CG || o.formulation != HG_PRIMAL || o.A0[0] != 0.0 || o.time_pass != -1) return HG_ERR_ARG;
+    // loads beyond a problem's d are ignored per problem (its own d loads)
     cudaSetDevice(c->device);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     Batch b;
     b.gs.assign(grids, grids + n);
     b.o = o;
     b.P = n;
-    b.L = g0->gd.d;
     b.prec = o.prec == HG_MIXED ? 1 : 0;
     b.s = c->stream;
     b.ar.ctx = c;
-    st = solve_batch(b, results);
+    for (int p = 0; p < n; ++p) {
+        Group* gr = nullptr;
+        for (Group& q : b.groups)
+            if (same_shape(q.gs[0], grids[p])) { gr = &q; break; }
+        if (!gr) {
+            b.groups.emplace_back();
+            gr = &b.groups.back();
+            gr->L = grids[p]->gd.d;
+        }
+        gr->gs.push_back(grids[p]);
+        gr->pos.push_back(p);
+        gr->P++;
+    }
+    int st = solve_batch(b, results);
     if (st != HG_OK && st != HG_ERR_NOT_CONVERGED && st != HG_ERR_BREAKDOWN) cudaStreamSynchronize(b.s);
     return st;
 }

@@ -110,6 +110,75 @@ int validate_solve_opts(const hg_grid* g, hg_solve_opts* o) {
     o->loads_mask &= (1u << g->gd.d) - 1u;
     return HG_OK;
 }
+
+// Buffers and steady-state CG scalars (every system active, alpha = beta =
+// 0.5, no convergence) for timing single passes of precision pr on the
+// primal operator with A0 = I.  The work buffers are left with meaningless
+// values: every solve starts from its own right-hand side.
+int timing_state(hg_grid* g, int pr, cudaStream_t s) {
+    g->form = 0;
+    g->has_ref = 0;
+    int st;
+    if ((st = grid_alloc_common(g))) return st;
+    if ((st = grid_alloc_work(g, pr))) return st;
+    Scalars hs[MAXL];
+    memset(hs, 0, sizeof(hs));
+    for (int l = 0; l < MAXL; ++l) {
+        hs[l].rr = 1.0; hs[l].alpha = 0.5; hs[l].beta = 0.5; hs[l].bnorm = 1.0; hs[l].tol = 0.0;
+        hs[l].alpha_f = 0.5f; hs[l].beta_f = 0.5f;
+        hs[l].max_iter = 1 << 30; hs[l].status = ST_ACTIVE;
+    }
+    HG_CU(cudaMemcpyAsync(g->work[pr].sc, hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+    return HG_OK;
+}
+
+// One launch of pass `pass` of the CG iteration (0 = last-axis forward pass,
+// 1.. = strided passes in launch order, hg_num_passes - 1 = last-axis
+// inverse pass) on the state timing_state() set up, with the grid's current
+// launch geometry; nm (64 chars) receives the pass name if not null.
+int enqueue_timing_pass(hg_grid* g, int pr, int pass, char* nm, cudaStream_t s) {
+    const GridDev& gd = g->gd;
+    const int L = gd.d, last = gd.d - 1;
+    const int np = gd.d == 2 ? 3 : 5;
+    Work& w = g->work[pr];
+    if (pass == 0) {
+        RowFwdArgs fa;
+        memset(&fa, 0, sizeof(fa));
+        fa.early_stage = 1;
+        fa.mode = FWD_CG; fa.L = L; fa.co = coeffs_for(g, pr, true);
+        fa.p = w.p; fa.r = w.r; fa.S = w.S; fa.sc = w.sc;
+        fa.partial = g->partial; fa.counter = g->counters + 0; fa.check_status = 0;
+        if (nm) snprintf(nm, 64, "k_row_fwd<%s,%d> (A.p + R2C DFT, axis %d)", pr ? "float" : "double", gd.d, last);
+        HG_CU(launch_row_fwd(pr, gd, g->plan[last], g->tw[pr], g->rowcfg[pr], fa, s));
+    } else if (pass == np - 1) {
+        RowInvArgs ia;
+        memset(&ia, 0, sizeof(ia));
+        ia.early_stage = 1;
+        ia.mode = INV_CG; ia.L = L; ia.S = w.S; ia.x = w.x; ia.r = w.r; ia.p = w.p;
+        ia.sc = w.sc; ia.partial = g->partial; ia.counter = g->counters + 1; ia.check_status = 0;
+        if (nm) snprintf(nm, 64, "k_row_inv<%s,%d> (C2R DFT + CG update, axis %d)", pr ? "float" : "double", gd.d, last);
+        HG_CU(launch_row_inv(pr, gd, g->plan[last], g->tw[pr], g->rowcfg[pr], ia, s));
+    } else if (pass > 0 && pass < np - 1) {
+        StrArgs sa;
+        memset(&sa, 0, sizeof(sa));
+        sa.early_stage = 1;
+        sa.L = L; sa.S = w.S; sa.sc = w.sc; sa.check_status = 0;
+        int axis;
+        if (gd.d == 2 || pass == 2) {
+            axis = 0; sa.mode = STR_GAMMA; sa.outer = 1; sa.n = gd.N[0]; sa.inner = gd.Ms / gd.N[0];
+        } else {
+            axis = 1; sa.mode = pass == 1 ? STR_FWD : STR_INV; sa.outer = gd.N[0]; sa.n = gd.N[1]; sa.inner = gd.H;
+        }
+        sa.axis = axis;
+        if (nm) snprintf(nm, 64, "k_strided<%s,%d> (%s, axis %d)", pr ? "float" : "double", gd.d,
+                         sa.mode == STR_GAMMA ? "DFT + Gamma_hat + iDFT" : sa.mode == STR_FWD ? "DFT" : "iDFT", axis);
+        HG_CU(launch_strided(pr, gd, g->plan[axis], g->tw[pr], g->strcfg[pr][axis], sa, s));
+    } else {
+        return HG_ERR_ARG;
+    }
+    g->ctx->launches++;
+    return HG_OK;
+}
 }  // namespace hgrt
 
 extern "C" {
@@ -588,67 +657,15 @@ int hg_time_pass(hg_grid* g, int prec, int pass, int reps, double* ms_out, char*
     hg_ctx* c = g->ctx;
     DeviceGuard dg(c->device);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
-    g->form = 0;   // primal operator
-    g->has_ref = 0;  // reference medium I
     cudaStream_t s = c->stream;
     const int pr = prec == HG_MIXED ? 1 : 0;
     int st;
-    if ((st = grid_alloc_common(g))) return st;
-    if ((st = grid_alloc_work(g, pr))) return st;
-    const GridDev& gd = g->gd;
-    const int L = gd.d, last = gd.d - 1;
-    Work& w = g->work[pr];
-    // steady-state CG scalars: every system active, alpha = beta = 0.5
-    Scalars hs[MAXL];
-    memset(hs, 0, sizeof(hs));
-    for (int l = 0; l < MAXL; ++l) {
-        hs[l].rr = 1.0; hs[l].alpha = 0.5; hs[l].beta = 0.5; hs[l].bnorm = 1.0; hs[l].tol = 0.0;
-        hs[l].alpha_f = 0.5f; hs[l].beta_f = 0.5f;
-        hs[l].max_iter = 1 << 30; hs[l].status = ST_ACTIVE;
-    }
-    HG_CU(cudaMemcpyAsync(w.sc, hs, sizeof(hs), cudaMemcpyHostToDevice, s));
-    auto launch_one = [&](char* nm) -> int {
-        if (pass == 0) {
-            RowFwdArgs fa;
-            memset(&fa, 0, sizeof(fa));
-            fa.early_stage = 1;
-            fa.mode = FWD_CG; fa.L = L; fa.co = coeffs_for(g, pr, true);
-            fa.p = w.p; fa.r = w.r; fa.S = w.S; fa.sc = w.sc;
-            fa.partial = g->partial; fa.counter = g->counters + 0; fa.check_status = 0;
-            if (nm) snprintf(nm, 64, "k_row_fwd<%s,%d> (A.p + R2C DFT, axis %d)", pr ? "float" : "double", gd.d, last);
-            HG_CU(launch_row_fwd(pr, gd, g->plan[last], g->tw[pr], g->rowcfg[pr], fa, s));
-        } else if (pass == np - 1) {
-            RowInvArgs ia;
-            memset(&ia, 0, sizeof(ia));
-            ia.early_stage = 1;
-            ia.mode = INV_CG; ia.L = L; ia.S = w.S; ia.x = w.x; ia.r = w.r; ia.p = w.p;
-            ia.sc = w.sc; ia.partial = g->partial; ia.counter = g->counters + 1; ia.check_status = 0;
-            if (nm) snprintf(nm, 64, "k_row_inv<%s,%d> (C2R DFT + CG update, axis %d)", pr ? "float" : "double", gd.d, last);
-            HG_CU(launch_row_inv(pr, gd, g->plan[last], g->tw[pr], g->rowcfg[pr], ia, s));
-        } else {
-            StrArgs sa;
-            memset(&sa, 0, sizeof(sa));
-            sa.early_stage = 1;
-            sa.L = L; sa.S = w.S; sa.sc = w.sc; sa.check_status = 0;
-            int axis;
-            if (gd.d == 2 || pass == 2) {
-                axis = 0; sa.mode = STR_GAMMA; sa.outer = 1; sa.n = gd.N[0]; sa.inner = gd.Ms / gd.N[0];
-            } else {
-                axis = 1; sa.mode = pass == 1 ? STR_FWD : STR_INV; sa.outer = gd.N[0]; sa.n = gd.N[1]; sa.inner = gd.H;
-            }
-            sa.axis = axis;
-            if (nm) snprintf(nm, 64, "k_strided<%s,%d> (%s, axis %d)", pr ? "float" : "double", gd.d,
-                             sa.mode == STR_GAMMA ? "DFT + Gamma_hat + iDFT" : sa.mode == STR_FWD ? "DFT" : "iDFT", axis);
-            HG_CU(launch_strided(pr, gd, g->plan[axis], g->tw[pr], g->strcfg[pr][axis], sa, s));
-        }
-        c->launches++;
-        return HG_OK;
-    };
+    if ((st = timing_state(g, pr, s))) return st;
     char nm[64] = {0};
-    if ((st = launch_one(nm))) return st;   // warm-up
+    if ((st = enqueue_timing_pass(g, pr, pass, nm, s))) return st;   // warm-up
     HG_CU(cudaEventRecord(g->ev0, s));
     for (int i = 0; i < reps; ++i)
-        if ((st = launch_one(nullptr))) return st;
+        if ((st = enqueue_timing_pass(g, pr, pass, nullptr, s))) return st;
     HG_CU(cudaEventRecord(g->ev1, s));
     HG_CU(cudaEventSynchronize(g->ev1));
     float ms = 0.f;

@@ -213,6 +213,7 @@ cudaError_t configure_kernels(int max_smem);
 bool ct_length(int d, int n);
 int ct_npmax(int prec, int n);
 enum { CT_THREADS_HOST = 256 };   // = CT_THREADS
+enum { MAX_REAL_ROWS_HOST = 64 };  // = MAX_REAL_ROWS: real rows one row-pass CTA stages
 // Most lanes of a compile-time strided tile (the device bounds its per-thread
 // loads by it; the host never chooses more).
 __host__ __device__ constexpr int ct_max_lanes(int d) { return d == 2 ? 2 : 4; }

@@ -2,6 +2,8 @@
 #include "hg_kernels.cuh"
 
 namespace hgk {
+// the host's tile limits (hg_internal.h) are the kernels' own
+static_assert(MAX_REAL_ROWS == MAX_REAL_ROWS_HOST, "host row tiles and device offset table disagree");
 cudaError_t launch_row_fwd_f32(const GridDev& g, const AxisPlanH& pl, const void* tw, const RowCfg& c,
                                 const RowFwdArgs& a, cudaStream_t s) {
     return launch_row_fwd_t<float>(g, pl, tw, c, a, s);

@@ -119,6 +119,12 @@ int grid_init_plans(hg_grid* g);
 // FFT plan and launch geometry helpers (hg_api.cpp)
 bool factor(int n, hgk::AxisPlanH& pl);
 int min_radix(const hgk::AxisPlanH& pl);
+// make_*: the geometry with the given tile, if the kernels can run it;
+// choose_*: the default (heuristic) geometry.
+bool make_row_cfg(int prec, int n, int d, int L, int RB, int LB, int minR, size_t csize, int max_smem,
+                  long long rows, hgk::RowCfg& cfg);
+bool make_str_cfg(int prec, int n, int d, int Cl, int minR, size_t csize, int max_smem, long long inner,
+                  hgk::StrCfg& cfg);
 bool choose_row_cfg(int prec, int n, int d, int L, int minR, size_t csize, int max_smem,
                     long long rows, hgk::RowCfg& cfg);
 bool choose_str_cfg(int prec, int n, int d, int minR, size_t csize, int max_smem,
@@ -180,6 +186,13 @@ int validate_solve_opts(const hg_grid* g, hg_solve_opts* o);
 int ga_build_field(hg_grid* g, const int* Ntr, const int* P, const uint8_t* phase, const double* table,
                    double* out64, float* out32, cudaStream_t s);
 hgk::Weight grid_weight(const hg_grid* g);   // the scalar product of the iteration
+// Single-pass timing (hg_time_pass, hg_tune): buffers and steady-state
+// scalars, then one launch of pass `pass` with the grid's launch geometry.
+int timing_state(hg_grid* g, int pr, cudaStream_t s);
+int enqueue_timing_pass(hg_grid* g, int pr, int pass, char* nm, cudaStream_t s);
+// Reduction slots for row passes of nbx CTAs per load (reallocated when the
+// current buffer is smaller; the caller holds ctx->mu with no work in flight).
+int grid_ensure_partial(hg_grid* g, long long nbx);
 
 // scheduler (hg_sched.cpp)
 Scheduler* sched_create(hg_ctx* ctx);

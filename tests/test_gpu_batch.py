@@ -1,5 +1,5 @@
-"""Batched solves (hg_solve_batch: every pass one launch for all problems)
-against single solves and the oracle.
+"""Batched solves (hg_solve_batch: every pass one launch for all problems of a
+shape, one CUDA graph for all shapes) against single solves and the oracle.
 
 A batched launch runs, for each problem, the same tile bodies with the same
 tile-to-CTA map and fixed-order reductions as that problem's own launch, so
@@ -101,16 +101,53 @@ def test_batch_with_a_homogeneous_problem_and_loads_mask(hg, ctx):
         g.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_of_mixed_shapes_equals_single_solves(hg, ctx, prec):
+    """2D and 3D problems of five shapes (compile-time and run-time FFT
+    lengths) in one call: one CUDA graph per chunk with a branch per shape.
+    Each problem's result equals its single solve bitwise and the oracle
+    within the path's tolerance."""
+    pr = hg.HG_MIXED if prec == "mixed" else hg.HG_FP64
+    rng = np.random.default_rng(31)
+    shapes = [(45, 45), (27, 27, 27), (75, 75), (15, 9, 15), (63, 35)]
+    probs = []
+    for k in range(10):
+        N = shapes[k % len(shapes)]
+        if len(N) == 2 and k < 5:
+            m = W.ellipses_2d(N[0], 0.3, 50.0, np.random.default_rng(100 + k))
+            probs.append((N, ("phase", m.phase, m.table)))
+        else:
+            probs.append((N, ("field", W.random_spd_field(N, rng, 1.0, 30.0))))
+    grids = []
+    for N, c in probs:
+        g = ctx.grid(N)
+        if c[0] == "phase":
+            g.set_coeffs_phase(c[1], c[2])
+        else:
+            g.set_coeffs_field(c[1])
+        grids.append(g)
+    o = hg.default_opts(tol=1e-8, prec=pr, max_iter=20000)
+    batch = ctx.solve_batch(grids, o)
+    for g, b, (N, c) in zip(grids, batch, probs):
+        assert b["status"] == 0 and b["AH"].shape == (len(N), len(N))
+        single = g.solve(o)
+        assert b["iters"] == single["iters"] and b["outer"] == single["outer"]
+        np.testing.assert_array_equal(b["AH"], single["AH"])
+    for g, b, (N, c) in list(zip(grids, batch, probs))[5:8]:
+        ref = O.solve_AH(c[1], N, tol=1e-11)["AH"]
+        bound = 1e-6 if prec == "mixed" else 1e-7
+        assert np.max(np.abs(b["AH"] - ref)) <= bound * np.max(np.abs(ref))
+    for g in grids:
+        g.close()
+
+
 def test_batch_errors(hg, ctx):
-    a, b = ctx.grid((15, 15)), ctx.grid((27, 27))
+    a = ctx.grid((15, 15))
     m = W.square_inclusion_15()
     a.set_coeffs_phase(m.phase, m.table)
-    b.set_coeffs_phase(np.zeros((27, 27), np.uint8), np.eye(2)[None])
     import ctypes
     lib = hg.load()
-    hs = (ctypes.c_void_p * 2)(a.h, b.h)
     res = (hg.Result * 2)()
-    assert lib.hg_solve_batch(hs, 2, ctypes.byref(hg.default_opts()), res) == -1
     hs = (ctypes.c_void_p * 2)(a.h, a.h)
     assert lib.hg_solve_batch(hs, 2, ctypes.byref(hg.default_opts()), res) == -1
     hs1 = (ctypes.c_void_p * 1)(a.h)
@@ -118,5 +155,11 @@ def test_batch_errors(hg, ctx):
     assert lib.hg_solve_batch(hs1, 1, ctypes.byref(hg.default_opts(formulation=hg.HG_DUAL)), res) == -1
     assert lib.hg_solve_batch(hs1, 1, ctypes.byref(hg.default_opts(A0=2.0 * np.eye(2))), res) == -1
     assert lib.hg_solve_batch(hs1, 0, ctypes.byref(hg.default_opts()), res) == -1
+    other = hg.Context(0)
+    b = other.grid((15, 15))
+    b.set_coeffs_phase(m.phase, m.table)
+    hs = (ctypes.c_void_p * 2)(a.h, b.h)   # grids of two contexts
+    assert lib.hg_solve_batch(hs, 2, ctypes.byref(hg.default_opts()), res) == -1
     a.close()
     b.close()
+    other.close()
