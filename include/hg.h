@@ -222,7 +222,10 @@ int hg_solve_AH(hg_grid* grid, const hg_solve_opts* opts, double* AH_out, hg_res
  * check_every at a time in one CUDA graph with one branch per group, so the
  * groups run concurrently and one graph launch steps every problem; each
  * problem keeps its own convergence status, so converged problems drop out of
- * the launches.  A group runs with the launch geometry of its first grid.
+ * the launches.  HG_MIXED: each problem's FP64 refinement step runs as soon as
+ * its inner FP32 solve stops, beside the next graph launch; every problem's
+ * iterates equal those of its own hg_solve_AH.  A group runs with the launch
+ * geometry of its first grid.
  * results[p] (n entries) is the result of grids[p]; device_ms and wall_ms are
  * those of the whole batch.  Each problem solves its own d loads (those in
  * loads_mask).  Supports HG_CG, HG_PRIMAL, A0 = I, HG_FP64 and HG_MIXED,

@@ -9,9 +9,12 @@
 // captured `check_every` at a time in ONE CUDA graph with one branch per
 // group, so the groups' passes overlap on the device and one graph launch
 // steps every problem; each problem keeps its own scalars, convergence status
-// and reduction slots, and a converged problem's tiles exit at once.  The
-// small per-problem steps (scalar set-up, inner set-up, x64 += delta, A_H)
-// are plain per-grid launches.
+// and reduction slots, and a converged problem's tiles exit at once.  In mixed
+// precision a problem whose inner FP32 solve has stopped gets its FP64
+// refinement step (batched per shape) on a second stream while the next
+// chunk runs, so problems progress independently.  The small per-problem
+// steps (scalar set-up, inner set-up, x64 += delta, A_H) are plain per-grid
+// launches.
 #include "hg.h"
 #include "hg_internal.h"
 #include "hg_runtime.h"
@@ -64,25 +67,38 @@ struct Arena {
     }
 };
 
-int upload_items(Arena& ar, const std::vector<PassArgs>& pas, cudaStream_t s, BatchItems* it) {
+// Device arrays for the items of up to cap problems.
+int alloc_items(Arena& ar, size_t cap, BatchItems* it) {
+    int st;
+    if ((st = ar.get(cap * sizeof(RowFwdArgs), (void**)&it->fa))) return st;
+    if ((st = ar.get(cap * sizeof(RowInvArgs), (void**)&it->ia))) return st;
+    for (int k = 0; k < 3; ++k)
+        if ((st = ar.get(cap * sizeof(StrArgs), (void**)&it->sa[k]))) return st;
+    return HG_OK;
+}
+
+// Copies the items of pas into it's arrays (allocated for at least
+// pas.size() problems), on stream s after the work already enqueued there.
+int copy_items(const std::vector<PassArgs>& pas, cudaStream_t s, BatchItems* it) {
     const size_t P = pas.size();
     std::vector<RowFwdArgs> fa(P);
     std::vector<RowInvArgs> ia(P);
     std::vector<StrArgs> sa(P);
     for (size_t p = 0; p < P; ++p) { fa[p] = pas[p].fa; ia[p] = pas[p].ia; }
-    int st;
-    if ((st = ar.get(P * sizeof(RowFwdArgs), (void**)&it->fa))) return st;
-    if ((st = ar.get(P * sizeof(RowInvArgs), (void**)&it->ia))) return st;
     HG_CU(cudaMemcpyAsync(it->fa, fa.data(), P * sizeof(RowFwdArgs), cudaMemcpyHostToDevice, s));
     HG_CU(cudaMemcpyAsync(it->ia, ia.data(), P * sizeof(RowInvArgs), cudaMemcpyHostToDevice, s));
     for (int k = 0; k < pas[0].nstr; ++k) {
         for (size_t p = 0; p < P; ++p) sa[p] = pas[p].sa[k];
-        if ((st = ar.get(P * sizeof(StrArgs), (void**)&it->sa[k]))) return st;
         HG_CU(cudaMemcpyAsync(it->sa[k], sa.data(), P * sizeof(StrArgs), cudaMemcpyHostToDevice, s));
     }
     // the host vectors are pageable: cudaMemcpyAsync has staged them on return
     it->first = pas[0];
     return HG_OK;
+}
+
+int upload_items(Arena& ar, const std::vector<PassArgs>& pas, cudaStream_t s, BatchItems* it) {
+    int st = alloc_items(ar, pas.size(), it);
+    return st ? st : copy_items(pas, s, it);
 }
 
 // The launches of one operator application for all P problems.
@@ -108,6 +124,8 @@ struct Group {
     std::vector<hg_grid*> gs;
     std::vector<int> pos;        // their positions in the batch
     int P = 0, L = 0;
+    BatchItems refine[3];        // items of the refinement launches (FP32 projection,
+                                 // FP64 projection, FP64 residual), capacity P
     cudaStream_t side = nullptr; // capture branch of this group
     cudaEvent_t join = nullptr;
 };
@@ -125,6 +143,8 @@ struct Batch {
     cudaGraphExec_t cg_exec = nullptr;
     long long nk = 0;                        // launches per iteration of the captured graph
     cudaEvent_t fork = nullptr;
+    cudaStream_t side = nullptr;             // refinement steps (mixed), beside the graph chunks
+    cudaEvent_t refined = nullptr;
     ~Batch() {
         if (cg_exec) cudaGraphExecDestroy(cg_exec);
         if (h_gather) cudaFreeHost(h_gather);
@@ -133,6 +153,8 @@ struct Batch {
             if (gr.side) cudaStreamDestroy(gr.side);
         }
         if (fork) cudaEventDestroy(fork);
+        if (refined) cudaEventDestroy(refined);
+        if (side) cudaStreamDestroy(side);
     }
 };
 
@@ -229,40 +251,70 @@ int make_cg_graph(Batch& b, int prec, const std::vector<char>& member, int* capt
     return HG_OK;
 }
 
-// The FP64 refinement step of one problem of the mixed path, enqueued as
-// soon as its inner FP32 solve has stopped (the steps of its single solve):
-// delta <- Gamma_N delta (FP32), x64 += delta, x64 <- Gamma_N x64 (FP64, tol
-// < 1e-8), r = -G A (E + x64) (FP64), and the next inner start, which is
-// idle for the loads the residual found converged.  No host sync: the next
-// graph chunk sees the new inner status.
-int refine_one(Batch& b, hg_grid* g) {
-    const GridDev& gd = g->gd;
-    const int L = gd.d;
-    hg_ctx* c = g->ctx;
-    int st = enqueue_matvec(g, 1, L, g->work[1].x, false, false, nullptr, nullptr, INV_PROJ, nullptr, 1, b.s,
-                            g->work[0].sc);
-    if (st) return st;
-    HG_CU(launch_outer_update(gd, L, (double*)g->work[0].x, (const float*)g->work[1].x, g->work[0].sc,
-                              g->work[1].sc, b.s));
-    c->launches++;
-    if (b.o.tol < 1e-8 &&
-        (st = enqueue_matvec(g, 0, L, g->work[0].x, false, false, nullptr, nullptr, INV_PROJ, nullptr, 1, b.s)))
-        return st;
-    if ((st = enqueue_matvec(g, 0, L, g->work[0].x, true, true, nullptr, nullptr, INV_RESID, nullptr, 1, b.s)))
-        return st;
-    HG_CU(launch_inner_init(gd, L, (const double*)g->work[0].r, (float*)g->work[1].r, (float*)g->work[1].p,
-                            (float*)g->work[1].x, g->work[0].sc, g->work[1].sc, b.o.inner_tol, b.o.max_iter, 64,
-                            grid_weight(g), g->partial, g->counters + 4, b.s));
-    c->launches++;
+// The FP64 refinement step of the mixed path for the problems marked in
+// `due` (whose inner FP32 solves have stopped), the steps of their single
+// solves: delta <- Gamma_N delta (FP32), x64 += delta, x64 <- Gamma_N x64
+// (FP64, tol < 1e-8), r = -G A (E + x64) (FP64).  Per grid shape the
+// projections and the residual are one launch per pass for all its due
+// problems.  Enqueued on stream s; restart_due() then starts their next inner
+// solves (idle for the loads the residual found converged).
+int refine_due(Batch& b, const std::vector<char>& due, cudaStream_t s) {
+    hg_ctx* c = b.gs[0]->ctx;
+    int st;
+    for (Group& gr : b.groups) {
+        std::vector<hg_grid*> sub;
+        for (int i = 0; i < gr.P; ++i)
+            if (due[gr.pos[i]]) sub.push_back(gr.gs[i]);
+        if (sub.empty()) continue;
+        const int n = (int)sub.size(), L = gr.L;
+        std::vector<PassArgs> pas(n);
+        for (int i = 0; i < n; ++i)
+            matvec_args(sub[i], 1, L, sub[i]->work[1].x, false, false, nullptr, nullptr, INV_PROJ, nullptr, 1,
+                        sub[i]->work[0].sc, &pas[i]);
+        if ((st = copy_items(pas, s, &gr.refine[0])) || (st = launch_batch(gr.gs[0], 1, gr.refine[0], n, s)))
+            return st;
+        for (hg_grid* g : sub) {
+            HG_CU(launch_outer_update(g->gd, L, (double*)g->work[0].x, (const float*)g->work[1].x, g->work[0].sc,
+                                      g->work[1].sc, s));
+            c->launches++;
+        }
+        if (b.o.tol < 1e-8) {
+            for (int i = 0; i < n; ++i)
+                matvec_args(sub[i], 0, L, sub[i]->work[0].x, false, false, nullptr, nullptr, INV_PROJ, nullptr, 1,
+                            nullptr, &pas[i]);
+            if ((st = copy_items(pas, s, &gr.refine[1])) || (st = launch_batch(gr.gs[0], 0, gr.refine[1], n, s)))
+                return st;
+        }
+        for (int i = 0; i < n; ++i)
+            matvec_args(sub[i], 0, L, sub[i]->work[0].x, true, true, nullptr, nullptr, INV_RESID, nullptr, 1, nullptr,
+                        &pas[i]);
+        if ((st = copy_items(pas, s, &gr.refine[2])) || (st = launch_batch(gr.gs[0], 0, gr.refine[2], n, s)))
+            return st;
+    }
+    return HG_OK;
+}
+
+int restart_due(Batch& b, const std::vector<char>& due, cudaStream_t s) {
+    for (int p = 0; p < b.P; ++p) {
+        if (!due[p]) continue;
+        hg_grid* g = b.gs[p];
+        HG_CU(launch_inner_init(g->gd, g->gd.d, (const double*)g->work[0].r, (float*)g->work[1].r,
+                                (float*)g->work[1].p, (float*)g->work[1].x, g->work[0].sc, g->work[1].sc,
+                                b.o.inner_tol, b.o.max_iter, 64, grid_weight(g), g->partial, g->counters + 4, s));
+        g->ctx->launches++;
+    }
     return HG_OK;
 }
 
 // Steps the batch in graph chunks until no problem is active.  FP64: the CG
-// of every problem.  Mixed: the inner FP32 CG in the graph, and each
-// problem's refinement step as soon as its inner solve has stopped, so the
-// problems progress independently (continuous batching inside the batch).
-// When the problems still running fall to 3/4 of those captured, the graph
-// is captured again over them alone (converged problems cost no launches).
+// of every problem.  Mixed: the inner FP32 CG in the graph; a problem whose
+// inner solve has stopped gets its FP64 refinement step on a second stream
+// while the next chunk runs (its tiles in that chunk exit at once: its inner
+// status is not active), and its next inner solve starts before the chunk
+// after, so the problems progress independently and the FP64 refinement
+// overlaps the FP32 iterations of the others.  When the problems still
+// running fall to 3/4 of those captured, the graph is captured again over them
+// alone (converged problems cost no launches).
 int run_batch(Batch& b) {
     const bool mixed = b.prec == 1;
     const int chunk = std::max(1, b.o.check_every);
@@ -270,18 +322,28 @@ int run_batch(Batch& b) {
     int captured = 0, st;
     if ((st = make_cg_graph(b, b.prec, member, &captured))) return st;
     const long long max_chunks =
-        (mixed ? (long long)std::max(1, b.o.max_outer) : 1LL) * ((long long)b.o.max_iter / chunk + 3);
+        (mixed ? (long long)std::max(1, b.o.max_outer) : 1LL) * ((long long)b.o.max_iter / chunk + 3) + 2;
+    std::vector<char> due(b.P, 0), refining(b.P, 0);
+    int nrefining = 0;
     for (long long k = 0;; ++k) {
         HG_CU(cudaGraphLaunch(b.cg_exec, b.s));
         b.gs[0]->ctx->launches += b.nk * chunk;
+        if (nrefining) {
+            // the refinement steps enqueued on the side stream during this chunk
+            HG_CU(cudaEventRecord(b.refined, b.side));
+            HG_CU(cudaStreamWaitEvent(b.s, b.refined, 0));
+        }
         if ((st = read_scalars(b, mixed))) return st;
-        int running = 0;
+        // refined problems start their next inner solve in the next chunk
+        if (nrefining && (st = restart_due(b, refining, b.s))) return st;
+        int running = 0, ndue = 0;
         for (int p = 0; p < b.P; ++p) {
             member[p] = 0;
+            due[p] = 0;
             if (!any_load(b, p, false, ST_ACTIVE)) continue;
             member[p] = 1;
             ++running;
-            if (!mixed || any_load(b, p, true, ST_ACTIVE)) continue;
+            if (!mixed || refining[p] || any_load(b, p, true, ST_ACTIVE)) continue;
             // inner solve stopped: refine, unless the refinement steps are spent
             // (the outer scalars count them)
             const Scalars* ho = b.h_gather + (size_t)p * MAXL;
@@ -293,10 +355,24 @@ int run_batch(Batch& b) {
                 --running;
                 continue;
             }
-            if ((st = refine_one(b, b.gs[p]))) return st;
+            due[p] = 1;
+            ++ndue;
+        }
+        refining.swap(due);
+        nrefining = ndue;
+        if (nrefining) {
+            // after this chunk's reads, before the next chunk
+            HG_CU(cudaEventRecord(b.refined, b.s));
+            HG_CU(cudaStreamWaitEvent(b.side, b.refined, 0));
+            if ((st = refine_due(b, refining, b.side))) return st;
         }
         if (running == 0 || k + 1 >= max_chunks) break;
         if (4 * running <= 3 * captured && (st = make_cg_graph(b, b.prec, member, &captured))) return st;
+    }
+    if (nrefining) {
+        // stopped at the chunk limit with refinements in flight
+        HG_CU(cudaEventRecord(b.refined, b.side));
+        HG_CU(cudaStreamWaitEvent(b.s, b.refined, 0));
     }
     return HG_OK;
 }
@@ -390,8 +466,13 @@ int solve_batch(Batch& b, hg_result* results) {
         }
         HG_CU(cudaStreamCreateWithFlags(&gr.side, cudaStreamNonBlocking));
         HG_CU(cudaEventCreateWithFlags(&gr.join, cudaEventDisableTiming));
+        if (b.prec == 1)
+            for (int k = 0; k < 3; ++k)
+                if ((st = alloc_items(b.ar, gr.P, &gr.refine[k]))) return st;
     }
     HG_CU(cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming));
+    HG_CU(cudaEventCreateWithFlags(&b.refined, cudaEventDisableTiming));
+    HG_CU(cudaStreamCreateWithFlags(&b.side, cudaStreamNonBlocking));
     // per-problem scalar pointers for the gathers: outer, then inner
     std::vector<const Scalars*> src(2 * b.P);
     for (int p = 0; p < b.P; ++p) {

@@ -331,9 +331,9 @@ __device__ __forceinline__ void row_offsets(long long* s_off, int nreal, int nl,
 // ---------------------------------------------------------------------------
 // last-axis forward pass (prologue + real-to-complex DFT)
 // ---------------------------------------------------------------------------
-template <typename T, int D, int NN>
+template <typename T, int D, int NN, typename Args = RowFwdArgs>
 __device__ __forceinline__ void row_fwd_body(GridDev g, AxisPlanH pl, const Cx<T>* __restrict__ tw,
-                                             RowFwdArgs a, int RB, int LB, TileIdx ti) {
+                                             Args a, int RB, int LB, TileIdx ti) {
     typedef Cx<T> C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
@@ -559,9 +559,9 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd(GridDev g, AxisP
 // ---------------------------------------------------------------------------
 // strided-axis pass (complex DFT along one axis; Fourier projection on axis 0)
 // ---------------------------------------------------------------------------
-template <typename T, int D, int NN>
+template <typename T, int D, int NN, typename Args = StrArgs>
 __device__ __forceinline__ void strided_body(GridDev g, AxisPlanH pl, const Cx<T>* __restrict__ tw,
-                                             StrArgs a, int Cl, TileIdx ti) {
+                                             Args a, int Cl, TileIdx ti) {
     typedef Cx<T> C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
@@ -749,9 +749,9 @@ __global__ void __launch_bounds__(PassThreads<NN>::v, StridedMinBlocks<T, D, NN>
 // ---------------------------------------------------------------------------
 // last-axis inverse pass (complex-to-real DFT + CG update)
 // ---------------------------------------------------------------------------
-template <typename T, int D, int NN>
+template <typename T, int D, int NN, typename Args = RowInvArgs>
 __device__ __forceinline__ void row_inv_body(GridDev g, AxisPlanH pl, const Cx<T>* __restrict__ tw,
-                                             RowInvArgs a, int RB, int LB, TileIdx ti) {
+                                             Args a, int RB, int LB, TileIdx ti) {
     typedef Cx<T> C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
@@ -1008,12 +1008,30 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv(GridDev g, AxisP
 // slots and tickets) are items[p] in device memory; the grid's z index picks
 // the problem (strided: z = problem * L + load).  Twiddles and launch geometry
 // are those of the shared shape.
+// The arguments of this CTA's problem, copied once per CTA from the device
+// array into shared memory: the pass body then reads them (some fields with
+// run-time indices, e.g. the loads E) from shared memory, where a by-value
+// copy of a global struct would be a per-thread copy in local memory.
+// Items are written by the host before the launch, never by the previous
+// kernel, so the copy may precede the programmatic-dependency wait.
+template <typename Args>
+__device__ __forceinline__ const Args& stage_item(const Args* __restrict__ items, int p) {
+    static_assert(sizeof(Args) % 4 == 0 && sizeof(Args) <= 4 * 64 * 32, "item larger than the copy loop");
+    __shared__ __align__(16) unsigned char raw[sizeof(Args)];
+    const unsigned* src = reinterpret_cast<const unsigned*>(items + p);
+    unsigned* dst = reinterpret_cast<unsigned*>(raw);
+    for (int i = threadIdx.x; i < (int)(sizeof(Args) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    return *reinterpret_cast<const Args*>(raw);
+}
+
 template <typename T, int D, int NN>
 __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_fwd_b(GridDev g, AxisPlanH pl,
                                                                  const Cx<T>* __restrict__ tw,
                                                                  const RowFwdArgs* __restrict__ items,
                                                                  int RB, int LB) {
-    row_fwd_body<T, D, NN>(g, pl, tw, items[blockIdx.z], RB, LB, TileIdx::of_block());
+    row_fwd_body<T, D, NN, const RowFwdArgs&>(g, pl, tw, stage_item(items, blockIdx.z), RB, LB,
+                                              TileIdx::of_block());
 }
 
 template <typename T, int D, int NN>
@@ -1021,7 +1039,8 @@ __global__ void __launch_bounds__(PassThreads<NN>::v) k_row_inv_b(GridDev g, Axi
                                                                  const Cx<T>* __restrict__ tw,
                                                                  const RowInvArgs* __restrict__ items,
                                                                  int RB, int LB) {
-    row_inv_body<T, D, NN>(g, pl, tw, items[blockIdx.z], RB, LB, TileIdx::of_block());
+    row_inv_body<T, D, NN, const RowInvArgs&>(g, pl, tw, stage_item(items, blockIdx.z), RB, LB,
+                                              TileIdx::of_block());
 }
 
 template <typename T, int D, int NN>
@@ -1030,7 +1049,7 @@ k_strided_b(GridDev g, AxisPlanH pl, const Cx<T>* __restrict__ tw, const StrArgs
             int L) {
     TileIdx ti = TileIdx::of_block();
     ti.z = (int)blockIdx.z % L;
-    strided_body<T, D, NN>(g, pl, tw, items[blockIdx.z / L], Cl, ti);
+    strided_body<T, D, NN, const StrArgs&>(g, pl, tw, stage_item(items, (int)blockIdx.z / L), Cl, ti);
 }
 
 // ---------------------------------------------------------------------------
