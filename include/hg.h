@@ -299,6 +299,13 @@ typedef struct {
     int lanes[2];    /* pencils per component staged per CTA by the strided pass
                         of axis a (a = 0, and a = 1 in 3D; 0 where unused), a
                         power of two                                             */
+    int radix[3][8]; /* order of the radix-3/5/7 Stockham stages of the FFT along
+                        axis a, zero-terminated, for the lengths without
+                        compile-time kernels (whose plan is read at run time);
+                        all zero for the other axes.  hg_set_launch_cfg: all
+                        zero = the default order (3s, then 5s, then 7s); a
+                        permutation of the length's factors otherwise.  The
+                        order is the grid's, shared by both precisions.          */
 } hg_launch_cfg;
 
 /* The grid's current geometry for precision prec (HG_FP64 or HG_MIXED, the
@@ -306,8 +313,9 @@ typedef struct {
 int hg_get_launch_cfg(hg_grid* grid, int prec, hg_launch_cfg* out);
 /* Sets it.  HG_ERR_ARG if the kernels cannot run that tile (too many pencils
  * for shared memory or registers, lanes not a power of two, more rows than the
- * grid); HG_ERR_BUSY while a ticket holds the grid.  Drops the grid's cached
- * CUDA graphs of that precision. */
+ * grid, a radix order that is not a permutation of the axis length's factors
+ * or is given for a length with compile-time kernels); HG_ERR_BUSY while a
+ * ticket holds the grid.  Drops the grid's cached CUDA graphs. */
 int hg_set_launch_cfg(hg_grid* grid, int prec, const hg_launch_cfg* cfg);
 
 typedef struct {
@@ -321,13 +329,17 @@ typedef struct {
 } hg_tune_result;
 
 /* Autotuner: times every geometry the kernels can run for this grid shape and
- * precision (all rows x loads tiles of the last-axis passes, all lane counts of
- * each strided pass), each over `reps` launches of its passes (CUDA events on
- * the context stream, best of three), on the grid's own coefficients with
- * steady-state CG scalars, and sets the fastest (the default unless another is
- * at least 3% faster: closer timings are within the run-to-run spread).  cache_path (NULL: no cache) is a text file of one
- * record per line, "hg-tune-v1 <device> <SMs> <prec> <d> <N0> <N1> <N2> <rb>
- * <lb> <lanes0> <lanes1> <ms>", device = its name with blanks as '_': a record
+ * precision (all rows x loads tiles of the last-axis passes, all lane counts
+ * of each strided pass, every distinct radix order of each axis whose length
+ * has no compile-time kernel), each over `reps` launches of its passes (CUDA
+ * events on the context stream, best of three), on the grid's own
+ * coefficients with steady-state CG scalars, and sets the fastest (the
+ * default unless another is at least 3% faster: closer timings are within the
+ * run-to-run spread).  cache_path (NULL: no cache) is a text file of one
+ * record per line, "hg-tune-v2 <device> <SMs> <prec> <d> <N0> <N1> <N2> <rb>
+ * <lb> <lanes0> <lanes1> <ms> <order0> <order1> <order2>", device = its name
+ * with blanks as '_', order_a = the radix order of axis a as digits ("357"),
+ * or 0 (the default order, or a length with compile-time kernels): a record
  * for this device, shape and precision is applied without timing (the last
  * such line wins); otherwise the result is appended.  The work buffers are
  * left with meaningless values (every solve starts from its right-hand side).

@@ -87,10 +87,12 @@ class Result(ctypes.Structure):
 
 
 class LaunchCfg(ctypes.Structure):
-    _fields_ = [("row_rb", ctypes.c_int), ("row_lb", ctypes.c_int), ("lanes", ctypes.c_int * 2)]
+    _fields_ = [("row_rb", ctypes.c_int), ("row_lb", ctypes.c_int), ("lanes", ctypes.c_int * 2),
+                ("radix", (ctypes.c_int * 8) * 3)]
 
     def to_dict(self) -> dict:
-        return {"row_rb": self.row_rb, "row_lb": self.row_lb, "lanes": list(self.lanes)}
+        return {"row_rb": self.row_rb, "row_lb": self.row_lb, "lanes": list(self.lanes),
+                "radix": [[r for r in self.radix[a] if r] for a in range(3)]}
 
 
 class TuneResult(ctypes.Structure):
@@ -380,10 +382,19 @@ class Grid:
         _check(load().hg_get_launch_cfg(self.h, prec, ctypes.byref(c)), "hg_get_launch_cfg")
         return c.to_dict()
 
-    def set_launch_cfg(self, prec: int, row_rb: int, row_lb: int, lanes: Sequence[int]):
-        """hg_set_launch_cfg (raises HGError HG_ERR_ARG for a tile the kernels cannot run)."""
+    def set_launch_cfg(self, prec: int, row_rb: int, row_lb: int, lanes: Sequence[int], radix=None):
+        """hg_set_launch_cfg (raises HGError HG_ERR_ARG for a geometry the kernels
+        cannot run).  radix: per axis the radix order ([] = the default order);
+        None keeps the grid's current orders."""
+        if radix is None:
+            radix = self.launch_cfg(prec)["radix"]
         ln = list(lanes) + [0] * (2 - len(lanes))
-        c = LaunchCfg(row_rb, row_lb, (ctypes.c_int * 2)(*ln))
+        c = LaunchCfg()
+        c.row_rb, c.row_lb = row_rb, row_lb
+        c.lanes[0], c.lanes[1] = ln[0], ln[1]
+        for a, order in enumerate(list(radix)[:3]):
+            for k, r in enumerate(order):
+                c.radix[a][k] = int(r)
         _check(load().hg_set_launch_cfg(self.h, prec, ctypes.byref(c)), "hg_set_launch_cfg")
 
     def tune(self, prec: int = HG_MIXED, reps: int = 10, cache_path: Optional[str] = None) -> dict:

@@ -35,7 +35,11 @@ using namespace hgrt;
 
 namespace {
 
-constexpr const char* CACHE_TAG = "hg-tune-v1";
+constexpr const char* CACHE_TAG = "hg-tune-v2";
+
+// Axes whose FFT plan is read at run time (no compile-time kernel): only
+// their radix order is a tunable.
+bool runtime_axis(const hg_grid* g, int a) { return !ct_length(g->gd.d, g->gd.N[a]); }
 
 hg_launch_cfg cfg_of(const hg_grid* g, int pr) {
     hg_launch_cfg c;
@@ -43,11 +47,43 @@ hg_launch_cfg cfg_of(const hg_grid* g, int pr) {
     c.row_rb = g->rowcfg[pr].RB;
     c.row_lb = g->rowcfg[pr].LB;
     for (int a = 0; a < g->gd.d - 1 && a < 2; ++a) c.lanes[a] = g->strcfg[pr][a].Cl;
+    for (int a = 0; a < g->gd.d; ++a)
+        if (runtime_axis(g, a))
+            for (int k = 0; k < g->plan[a].nstages && k < 8; ++k) c.radix[a][k] = g->plan[a].radix[k];
     return c;
 }
 
 bool same_cfg(const hg_launch_cfg& a, const hg_launch_cfg& b) {
-    return a.row_rb == b.row_rb && a.row_lb == b.row_lb && a.lanes[0] == b.lanes[0] && a.lanes[1] == b.lanes[1];
+    return a.row_rb == b.row_rb && a.row_lb == b.row_lb && a.lanes[0] == b.lanes[0] && a.lanes[1] == b.lanes[1] &&
+           memcmp(a.radix, b.radix, sizeof(a.radix)) == 0;
+}
+
+// The plan of axis a with the radix order `order` (zero-terminated; all zero:
+// the default order), if it is one: a permutation of the length's factors,
+// and only for an axis whose plan is read at run time.
+bool plan_with_order(const hg_grid* g, int a, const int* order, AxisPlanH& out) {
+    AxisPlanH pl{};
+    if (!factor(g->gd.N[a], pl)) return false;
+    pl.tw_off = g->plan[a].tw_off;
+    if (order[0] == 0) {
+        out = pl;
+        return true;
+    }
+    if (!runtime_axis(g, a)) return false;
+    int n = 0;
+    while (n < 8 && order[n] != 0) ++n;
+    if (n != pl.nstages) return false;
+    for (int r : {3, 5, 7}) {   // the same multiset of radices
+        int want = 0, have = 0;
+        for (int k = 0; k < n; ++k) {
+            want += order[k] == r;
+            have += pl.radix[k] == r;
+        }
+        if (want != have) return false;
+    }
+    for (int k = 0; k < n; ++k) pl.radix[k] = order[k];
+    out = pl;
+    return true;
 }
 
 size_t csize_of(int pr) { return pr == 0 ? 16 : 8; }
@@ -67,17 +103,29 @@ bool str_cfg(const hg_grid* g, int pr, int a, int Cl, StrCfg& out) {
     return make_str_cfg(pr, gd.N[a], gd.d, Cl, min_radix(g->plan[a]), csize_of(pr), g->ctx->max_smem, inner, out);
 }
 
-void drop_graphs(hg_grid* g, int pr) {
-    if (g->graphs[pr].exec) cudaGraphExecDestroy(g->graphs[pr].exec);
-    g->graphs[pr] = GraphCache();
+void drop_graphs(hg_grid* g) {
+    for (int pr = 0; pr < 2; ++pr) {
+        if (g->graphs[pr].exec) cudaGraphExecDestroy(g->graphs[pr].exec);
+        g->graphs[pr] = GraphCache();
+    }
 }
 
 // Validates c for g and sets it (caller holds ctx->mu, no work of g in flight).
 int apply_cfg(hg_grid* g, int pr, const hg_launch_cfg& c) {
     RowCfg rc{};
     StrCfg sc[2]{};
+    AxisPlanH pl[3]{};
+    const int d = g->gd.d;
+    for (int a = 0; a < 3; ++a) {
+        if (a < d) {
+            if (!plan_with_order(g, a, c.radix[a], pl[a])) return HG_ERR_ARG;
+        } else if (c.radix[a][0] != 0) {
+            return HG_ERR_ARG;
+        }
+    }
+    // the tiles' limits depend on the smallest radix only, not on the order
     if (!row_cfg(g, pr, c.row_rb, c.row_lb, rc)) return HG_ERR_ARG;
-    const int nstr = g->gd.d - 1;
+    const int nstr = d - 1;
     for (int a = 0; a < 2; ++a) {
         if (a < nstr) {
             if (!str_cfg(g, pr, a, c.lanes[a], sc[a])) return HG_ERR_ARG;
@@ -91,7 +139,8 @@ int apply_cfg(hg_grid* g, int pr, const hg_launch_cfg& c) {
     if ((st = grid_ensure_partial(g, nbx))) return st;
     g->rowcfg[pr] = rc;
     for (int a = 0; a < nstr; ++a) g->strcfg[pr][a] = sc[a];
-    drop_graphs(g, pr);
+    for (int a = 0; a < d; ++a) g->plan[a] = pl[a];
+    drop_graphs(g);
     return HG_OK;
 }
 
@@ -131,6 +180,28 @@ std::string device_key(int device, int* sms) {
     return n;
 }
 
+// Radix order <-> digit string ("357"; "0" for none).
+void order_to_str(const int* order, char* out) {
+    int n = 0;
+    while (n < 8 && order[n] != 0) {
+        out[n] = (char)('0' + order[n]);
+        ++n;
+    }
+    if (n == 0) out[n++] = '0';
+    out[n] = 0;
+}
+
+bool order_from_str(const char* str, int* order) {
+    for (int k = 0; k < 8; ++k) order[k] = 0;
+    if (strcmp(str, "0") == 0) return true;
+    int n = 0;
+    for (; str[n]; ++n) {
+        if (n >= 8 || (str[n] != '3' && str[n] != '5' && str[n] != '7')) return false;
+        order[n] = str[n] - '0';
+    }
+    return n > 0;
+}
+
 int cache_find(const char* path, const std::string& dev, int sms, int pr, int d, const int* N, hg_launch_cfg* out,
                double* ms_out) {
     FILE* f = fopen(path, "r");
@@ -138,18 +209,24 @@ int cache_find(const char* path, const std::string& dev, int sms, int pr, int d,
     char line[512];
     bool found = false;
     while (fgets(line, sizeof(line), f)) {
-        char tag[32], name[256];
+        char tag[32], name[256], o[3][16];
         int s_sms, s_pr, s_d, n0, n1, n2, rb, lb, l0, l1;
         double ms;
-        if (sscanf(line, "%31s %255s %d %d %d %d %d %d %d %d %d %d %lf", tag, name, &s_sms, &s_pr, &s_d, &n0, &n1,
-                   &n2, &rb, &lb, &l0, &l1, &ms) != 13)
+        if (sscanf(line, "%31s %255s %d %d %d %d %d %d %d %d %d %d %lf %15s %15s %15s", tag, name, &s_sms, &s_pr,
+                   &s_d, &n0, &n1, &n2, &rb, &lb, &l0, &l1, &ms, o[0], o[1], o[2]) != 16)
             continue;
         if (strcmp(tag, CACHE_TAG) != 0 || dev != name || s_sms != sms || s_pr != pr || s_d != d) continue;
         if (n0 != N[0] || n1 != N[1] || n2 != (d == 3 ? N[2] : 0)) continue;
-        out->row_rb = rb;
-        out->row_lb = lb;
-        out->lanes[0] = l0;
-        out->lanes[1] = l1;
+        hg_launch_cfg c;
+        memset(&c, 0, sizeof(c));
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) ok = ok && order_from_str(o[a], c.radix[a]);
+        if (!ok) continue;
+        c.row_rb = rb;
+        c.row_lb = lb;
+        c.lanes[0] = l0;
+        c.lanes[1] = l1;
+        *out = c;
         if (ms_out) *ms_out = ms;
         found = true;   // later records override earlier ones
     }
@@ -161,8 +238,10 @@ void cache_append(const char* path, const std::string& dev, int sms, int pr, int
                   const hg_launch_cfg& c, double ms) {
     FILE* f = fopen(path, "a");
     if (!f) return;   // a cache that cannot be written only costs a re-tune
-    fprintf(f, "%s %s %d %d %d %d %d %d %d %d %d %d %.6f\n", CACHE_TAG, dev.c_str(), sms, pr, d, N[0], N[1],
-            d == 3 ? N[2] : 0, c.row_rb, c.row_lb, c.lanes[0], c.lanes[1], ms);
+    char o[3][16];
+    for (int a = 0; a < 3; ++a) order_to_str(c.radix[a], o[a]);
+    fprintf(f, "%s %s %d %d %d %d %d %d %d %d %d %d %.6f %s %s %s\n", CACHE_TAG, dev.c_str(), sms, pr, d, N[0],
+            N[1], d == 3 ? N[2] : 0, c.row_rb, c.row_lb, c.lanes[0], c.lanes[1], ms, o[0], o[1], o[2]);
     fclose(f);
 }
 
@@ -235,6 +314,11 @@ int hg_tune(hg_grid* g, int prec, int reps, const char* cache_path, hg_tune_resu
             if (!choose_str_cfg(pr, gd.N[a], d, min_radix(g->plan[a]), csize_of(pr), c->max_smem, inner, outer, d, sc))
                 return HG_ERR_UNSUPPORTED_SIZE;
             heur.lanes[a] = sc.Cl;
+        }
+        for (int a = 0; a < d; ++a) {
+            AxisPlanH pl{};
+            if (runtime_axis(g, a) && factor(gd.N[a], pl))
+                for (int k = 0; k < pl.nstages && k < 8; ++k) heur.radix[a][k] = pl.radix[k];
         }
     }
     res.heuristic = heur;
@@ -311,6 +395,39 @@ int hg_tune(hg_grid* g, int prec, int reps, const char* cache_path, hg_tune_resu
             if (t < t_best && t < 0.97 * t_heur) {
                 t_best = t;
                 best.lanes[a] = Cl;
+            }
+        }
+        if ((st = apply_cfg(g, pr, best))) return st;
+    }
+
+    // radix order of every axis whose plan is read at run time: each distinct
+    // permutation of its factors (the default order, ascending, first)
+    for (int a = 0; a < d; ++a) {
+        if (!runtime_axis(g, a) || heur.radix[a][1] == 0) continue;   // one stage: no choice
+        std::vector<int> passes;
+        if (a == d - 1) passes = {0, np - 1};
+        else if (a == 0) passes = {d == 2 ? 1 : 2};
+        else passes = {1, 3};
+        double t_heur = 0.0;
+        if ((st = time_passes(g, pr, passes, reps, &t_heur))) return st;
+        double t_best = t_heur;
+        ++res.candidates;
+        int order[8] = {0}, n = 0;
+        while (n < 8 && heur.radix[a][n] != 0) {
+            order[n] = heur.radix[a][n];
+            ++n;
+        }
+        int tried = 0;
+        while (std::next_permutation(order, order + n) && ++tried <= 24) {
+            hg_launch_cfg cand = best;
+            for (int k = 0; k < 8; ++k) cand.radix[a][k] = order[k];
+            if ((st = apply_cfg(g, pr, cand))) return st;
+            double t = 0.0;
+            if ((st = time_passes(g, pr, passes, reps, &t))) return st;
+            ++res.candidates;
+            if (t < t_best && t < 0.97 * t_heur) {
+                t_best = t;
+                best = cand;
             }
         }
         if ((st = apply_cfg(g, pr, best))) return st;

@@ -78,7 +78,8 @@ def test_every_geometry_gives_the_oracle_solution(hg, ctx, N, kind, prec):
     iters0 = None
     for rb, lb, ln in cfgs:
         g.set_launch_cfg(pr, rb, lb, ln)
-        assert g.launch_cfg(pr) == {"row_rb": rb, "row_lb": lb, "lanes": list(ln)}
+        got = g.launch_cfg(pr)
+        assert (got["row_rb"], got["row_lb"], got["lanes"]) == (rb, lb, list(ln))
         r = g.solve(o)
         assert r["status"] == 0
         err = np.max(np.abs(r["AH"] - ref)) / np.max(np.abs(ref))
@@ -125,7 +126,7 @@ def test_tune_then_solve_and_cache(hg, ctx, N, tmp_path):
         r = g.solve(hg.default_opts(tol=1e-10, prec=pr))
         assert np.max(np.abs(r["AH"] - ref)) <= bound * np.max(np.abs(ref))
     lines = open(cache).read().splitlines()
-    assert len(lines) == 2 and all(ln.startswith("hg-tune-v1 ") for ln in lines)
+    assert len(lines) == 2 and all(ln.startswith("hg-tune-v2 ") for ln in lines)
     # a second grid of the same shape takes the cached geometry without timing
     g2 = ctx.grid(N)
     set_c(g2)
@@ -162,3 +163,69 @@ def test_batch_runs_a_tuned_lead_geometry_on_untuned_problems(hg, ctx):
         assert np.max(np.abs(r["AH"] - ref)) <= 1e-6 * np.max(np.abs(ref))
     for g in grids:
         g.close()
+
+
+def test_default_row_tile_fits_the_offset_table_3d_runtime_length(hg, ctx):
+    """A 3D grid with a run-time last-axis length and many rows: the default
+    row tile stays within the 64 real rows a row-pass CTA can index, and the
+    mixed solve matches the oracle."""
+    N = (49, 63, 25)
+    A = W.random_spd_field(N, np.random.default_rng(12), 1.0, 20.0)
+    g = ctx.grid(N)
+    g.set_coeffs_field(A)
+    for pr in (hg.HG_MIXED, hg.HG_FP64):
+        c = g.launch_cfg(pr)
+        assert c["row_rb"] * c["row_lb"] * 3 <= 64, c
+    ref = O.solve_AH(A, N, tol=1e-11)["AH"]
+    r = g.solve(hg.default_opts(tol=1e-9, prec=hg.HG_MIXED))
+    assert np.max(np.abs(r["AH"] - ref)) <= 1e-6 * np.max(np.abs(ref))
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_every_radix_order_gives_the_oracle_solution(hg, ctx, prec):
+    """Run-time FFT plans: every order of the radix-3/5/7 stages along each
+    axis (105 = 3 5 7 and 63 = 3 3 7 in 2D; 3D with 25 = 5 5 and 21 = 3 7)."""
+    import itertools
+    pr = hg.HG_MIXED if prec == "mixed" else hg.HG_FP64
+    bound = 1e-6 if prec == "mixed" else 1e-8
+    for N in [(105, 63), (21, 15, 25)]:
+        A = W.random_spd_field(N, np.random.default_rng(5), 1.0, 30.0)
+        ref = O.solve_AH(A, N, tol=1e-11)["AH"]
+        g = ctx.grid(N)
+        g.set_coeffs_field(A)
+        c = g.launch_cfg(pr)
+        default = c["radix"]
+        assert [sorted(o) for o in default[:len(N)]] == [o for o in default[:len(N)]]   # ascending
+        o = hg.default_opts(tol=1e-10, prec=pr)
+        for a in range(len(N)):
+            for order in sorted(set(itertools.permutations(default[a]))):
+                radix = [list(x) for x in default]
+                radix[a] = list(order)
+                g.set_launch_cfg(pr, c["row_rb"], c["row_lb"], c["lanes"], radix)
+                assert g.launch_cfg(pr)["radix"][a] == list(order)
+                r = g.solve(o)
+                err = np.max(np.abs(r["AH"] - ref)) / np.max(np.abs(ref))
+                assert r["status"] == 0 and err <= bound, (N, a, order, err)
+            g.set_launch_cfg(pr, c["row_rb"], c["row_lb"], c["lanes"], default)
+        g.close()
+
+
+def test_radix_orders_are_validated(hg, ctx):
+    g = ctx.grid((105, 45))     # 105 has a run-time plan, 45 a compile-time kernel
+    g.set_coeffs_field(W.random_spd_field((105, 45), np.random.default_rng(2), 1.0, 5.0))
+    c = g.launch_cfg(hg.HG_MIXED)
+    assert c["radix"][0] == [3, 5, 7] and c["radix"][1] == []
+    for bad in ([[3, 5], [], []], [[3, 5, 5], [], []], [[3, 5, 7], [3, 3, 5], []], [[2, 5, 7], [], []],
+                [[3, 5, 7], [], [3]]):
+        with pytest.raises(hg.HGError) as e:
+            g.set_launch_cfg(hg.HG_MIXED, c["row_rb"], c["row_lb"], c["lanes"], bad)
+        assert e.value.status == hg.HG_ERR_ARG
+    g.set_launch_cfg(hg.HG_MIXED, c["row_rb"], c["row_lb"], c["lanes"], [[7, 3, 5], [], []])
+    # the order is the grid's: both precisions see it
+    assert g.launch_cfg(hg.HG_FP64)["radix"][0] == [7, 3, 5]
+    t = g.tune(hg.HG_MIXED, reps=2)
+    assert t["heuristic"]["radix"][0] == [3, 5, 7]
+    assert sorted(t["chosen"]["radix"][0]) == [3, 5, 7]
+    assert t["candidates"] >= 6
+    g.close()

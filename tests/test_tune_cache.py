@@ -21,26 +21,32 @@ def write(path, lines):
 def test_lookup_last_record_wins(hg, tmp_path):
     p = str(tmp_path / "cache.txt")
     write(p, [
-        "hg-tune-v1 NVIDIA_GB300 152 1 2 729 729 0 2 2 2 0 0.058000",
-        "hg-tune-v1 NVIDIA_GB300 152 0 2 729 729 0 1 2 1 0 0.540000",
-        "hg-tune-v1 NVIDIA_GB300 152 1 3 135 135 135 3 3 2 4 0.470000",
-        "hg-tune-v1 NVIDIA_GB300 152 1 2 729 729 0 1 2 1 0 0.055000",
+        "hg-tune-v2 NVIDIA_GB300 152 1 2 729 729 0 2 2 2 0 0.058000 0 0 0",
+        "hg-tune-v2 NVIDIA_GB300 152 0 2 729 729 0 1 2 1 0 0.540000 0 0 0",
+        "hg-tune-v2 NVIDIA_GB300 152 1 3 135 135 135 3 3 2 4 0.470000 0 0 0",
+        "hg-tune-v2 NVIDIA_GB300 152 1 2 729 729 0 1 2 1 0 0.055000 0 0 0",
+        "hg-tune-v2 NVIDIA_GB300 152 1 2 105 63 0 4 2 2 0 0.020000 735 373 0",
     ])
     cfg, ms = hg.tune_cache_find(p, "NVIDIA_GB300", 152, hg.HG_MIXED, (729, 729))
-    assert cfg == {"row_rb": 1, "row_lb": 2, "lanes": [1, 0]} and ms == pytest.approx(0.055)
+    assert cfg == {"row_rb": 1, "row_lb": 2, "lanes": [1, 0], "radix": [[], [], []]}
+    assert ms == pytest.approx(0.055)
     cfg, ms = hg.tune_cache_find(p, "NVIDIA_GB300", 152, hg.HG_FP64, (729, 729))
-    assert cfg == {"row_rb": 1, "row_lb": 2, "lanes": [1, 0]} and ms == pytest.approx(0.54)
+    assert cfg == {"row_rb": 1, "row_lb": 2, "lanes": [1, 0], "radix": [[], [], []]}
+    assert ms == pytest.approx(0.54)
     cfg, ms = hg.tune_cache_find(p, "NVIDIA_GB300", 152, hg.HG_MIXED, (135, 135, 135))
-    assert cfg == {"row_rb": 3, "row_lb": 3, "lanes": [2, 4]}
+    assert cfg == {"row_rb": 3, "row_lb": 3, "lanes": [2, 4], "radix": [[], [], []]}
+    cfg, ms = hg.tune_cache_find(p, "NVIDIA_GB300", 152, hg.HG_MIXED, (105, 63))
+    assert cfg == {"row_rb": 4, "row_lb": 2, "lanes": [2, 0], "radix": [[7, 3, 5], [3, 7, 3], []]}
 
 
 def test_no_match_and_malformed_lines(hg, tmp_path):
     p = str(tmp_path / "cache.txt")
     write(p, [
         "garbage",
-        "hg-tune-v0 NVIDIA_GB300 152 1 2 729 729 0 2 2 2 0 0.058",     # other format version
-        "hg-tune-v1 NVIDIA_GB300 152 1 2 729 729 0 2 2",               # truncated
-        "hg-tune-v1 NVIDIA_B200 148 1 2 243 243 0 2 2 2 0 0.010",
+        "hg-tune-v1 NVIDIA_GB300 152 1 2 729 729 0 2 2 2 0 0.058",     # older format version
+        "hg-tune-v2 NVIDIA_GB300 152 1 2 729 729 0 2 2 2 0 0.058",     # truncated
+        "hg-tune-v2 NVIDIA_GB300 152 1 2 729 729 0 2 2 2 0 0.058 0 0 x",   # bad radix order
+        "hg-tune-v2 NVIDIA_B200 148 1 2 243 243 0 2 2 2 0 0.010 0 0 0",
     ])
     assert hg.tune_cache_find(p, "NVIDIA_GB300", 152, hg.HG_MIXED, (729, 729)) is None
     assert hg.tune_cache_find(p, "NVIDIA_B200", 148, hg.HG_MIXED, (243, 243)) is not None
