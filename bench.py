@@ -58,6 +58,8 @@ def parse():
                          "ms: Moulinec-Suquet fixed point against CG on the 729x729 geometry "
                          "over contrasts 10, 100, 1000; ga: Galerkin scheme with exact integration "
                          "(upper and lower bounds) on the 729x729 pixels for trial grids 81..405")
+    ap.add_argument("--check-every", type=int, default=8,
+                    help="batched: CG iterations per captured graph chunk (host status check between chunks)")
     ap.add_argument("--duration", type=float, default=20.0, help="serving: arrival window (s)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--passes-once", action="store_true",
@@ -528,7 +530,8 @@ def run_batched(args):
         g = ctx.grid(ms.N)
         g.set_coeffs_phase(torch.from_numpy(ms.phase).to(dev), torch.from_numpy(ms.table).to(dev))
         grids.append(g)
-    o_mixed = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=max(0.5 * args.tol, 1e-6))
+    o_mixed = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=max(0.5 * args.tol, 1e-6),
+                              check_every=args.check_every)
     # launch geometry per grid size: the first grid of each size is tuned, the
     # others read the autotuner's cache (set-up, outside the timed region)
     tune_note = {"tuned": False}
@@ -620,9 +623,9 @@ def run_batched(args):
                                "{45,75,135,243,375}^2, vf U[0.1,0.5], contrast log-uniform [10,1e4], "
                                "loads e1,e2, rel. residual %g; one hg_solve_batch call: per grid size "
                                "every pass one launch for all its problems, the CG iterations of all "
-                               "sizes one captured CUDA graph (a branch per size) per 8 iterations, "
+                               "sizes one captured CUDA graph (a branch per size) per %d iterations, "
                                "each problem's FP64 refinement on a second stream as soon as its inner "
-                               "FP32 solve stops; autotuned launch geometry" % args.tol},
+                               "FP32 solve stops; autotuned launch geometry" % (args.tol, args.check_every)},
         "voxel_iter_per_s": bk_vox / bk_total,
         "kernel_launches_per_batch": int(bk_launches),
         "AH_max_rel_err_vs_fp64_tol1e-10": err_bk,
