@@ -297,3 +297,51 @@ def test_golden_laminate_fixture():
     ms = W.laminate(tuple(g["N"]), g["layers_axis0"])
     res = O.solve_AH(ms.full_field(), ms.N, tol=1e-14)
     np.testing.assert_allclose(res["AH"], np.array(g["AH"]), rtol=1e-12, atol=1e-13)
+
+
+def _smooth_field(N, a_of_x):
+    """Isotropic a(x) I sampled at x_k = 2 k / N (one period of the cell
+    [-1, 1]^d, up to a shift, which leaves A_H unchanged)."""
+    d = len(N)
+    xs = np.meshgrid(*[2.0 * np.arange(n) / n for n in N], indexing="ij")
+    a = a_of_x(*xs)
+    A = np.zeros((d, d) + tuple(N))
+    for i in range(d):
+        A[i, i] = a
+    return A
+
+
+def test_smooth_laminate_converges_to_continuous_closed_form():
+    """Prop. GaNi (Sec. 4.3): for smooth coefficients the GaNi solution
+    converges to the continuous one.  For a(x) = 2 + sin(pi x_1) the cell
+    problem is a laminate: continuous A_H = diag(harmonic mean, arithmetic
+    mean) = diag(sqrt(3), 2), since (1/2pi) int dt / (2 + sin t) = 1/sqrt(3).
+    The error falls geometrically with N (trapezoidal rule on an analytic
+    periodic integrand)."""
+    errs = []
+    for n in (3, 5, 9, 15):
+        A = _smooth_field((n, 7), lambda x, y: 2.0 + np.sin(np.pi * x))
+        AH = O.solve_AH(A, (n, 7), tol=1e-13)["AH"]
+        assert abs(AH[1, 1] - 2.0) < 1e-12 and abs(AH[0, 1]) < 1e-12
+        errs.append(abs(AH[0, 0] - np.sqrt(3.0)))
+    assert errs[-1] < 1e-8
+    assert all(e2 < 0.5 * e1 for e1, e2 in zip(errs, errs[1:]) if e1 > 1e-14)
+
+
+def test_smooth_2d_medium_grid_refinement_is_cauchy():
+    """Prop. GaNi (Sec. 4.3): a smooth, genuinely 2D medium; A_H(N) forms a
+    Cauchy sequence as the grid is refined (differences between successive
+    odd grids shrink rapidly), stays symmetric and between the Voigt and
+    Reuss bounds of the sampled medium."""
+    a = lambda x, y: 3.0 + np.sin(np.pi * x) * np.cos(np.pi * y) + 0.5 * np.cos(2 * np.pi * x)
+    AHs = []
+    for n in (9, 15, 27, 45):
+        A = _smooth_field((n, n), a)
+        AH = O.solve_AH(A, (n, n), tol=1e-13)["AH"]
+        np.testing.assert_allclose(AH, AH.T, atol=1e-12)
+        av = A[0, 0]
+        assert np.mean(av) - 1e-12 >= AH[0, 0] >= 1.0 / np.mean(1.0 / av) - 1e-12
+        AHs.append(AH)
+    diffs = [np.max(np.abs(b - a_)) for a_, b in zip(AHs, AHs[1:])]
+    assert diffs[-1] < 1e-9
+    assert diffs[1] < 0.1 * diffs[0] and diffs[2] < 0.1 * diffs[1]
