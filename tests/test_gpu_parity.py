@@ -419,3 +419,21 @@ def test_resetting_coefficients_between_solves(hg, ctx):
             r = g.solve(o)
             assert rel_max(r["AH"], ref) <= (1e-8 if prec == hg.HG_FP64 else 1e-6)
     g.close()
+
+
+def test_smooth_laminate_continuous_closed_form(hg, ctx):
+    """a(x) = 2 + sin(pi x_1): the GaNi A_H on a 15 x 7 grid equals the
+    continuous laminate's diag(sqrt(3), 2) to roundoff (Prop. GaNi, Sec. 4.3;
+    the trapezoidal rule is exact to 2e-16 here), FP64 and mixed."""
+    N = (15, 7)
+    x = np.meshgrid(2.0 * np.arange(15) / 15, 2.0 * np.arange(7) / 7, indexing="ij")[0]
+    A = np.zeros((2, 2) + N)
+    A[0, 0] = A[1, 1] = 2.0 + np.sin(np.pi * x)
+    g = ctx.grid(N)
+    g.set_coeffs_field(A)
+    exact = np.diag([np.sqrt(3.0), 2.0])
+    r = g.solve(hg.default_opts(tol=1e-12))
+    np.testing.assert_allclose(r["AH"], exact, atol=1e-11)
+    r = g.solve(hg.default_opts(tol=1e-10, prec=hg.HG_MIXED))
+    np.testing.assert_allclose(r["AH"], exact, atol=1e-7)
+    g.close()
