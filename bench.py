@@ -62,6 +62,9 @@ def parse():
                     help="batched: CG iterations per captured graph chunk (host status check between chunks)")
     ap.add_argument("--duration", type=float, default=20.0, help="serving: arrival window (s)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--batch-once", action="store_true",
+                    help="batched workload: tune, one warm-up and one timed hg_solve_batch call only, "
+                         "printing the kernel launches made before the timed call (an ncu -s value)")
     ap.add_argument("--passes-once", action="store_true",
                     help="launch every CG pass twice (FP32 then FP64) on the workload and exit "
                          "(a short command for ncu captures)")
@@ -919,10 +922,55 @@ def run_ga(args):
     return 0
 
 
+def run_batch_once(args):
+    """The 256-problem batched workload through one hg_solve_batch call, for
+    profiling: autotuning (cached per size), a warm-up call, then the timed
+    call; prints the launches made before it."""
+    import tempfile
+    import paper_1311_0089_gb300 as hg
+    import workloads as W
+    hg.load()
+    probs = W.batch_2d()
+    ctx = hg.Context(0, use_torch_stream=False)
+    grids = []
+    for ms in probs:
+        g = ctx.grid(ms.N)
+        g.set_coeffs_phase(ms.phase, ms.table)
+        grids.append(g)
+    cache = os.path.join(tempfile.mkdtemp(), "hg_tune.txt")
+    for g in grids:
+        g.tune(hg.HG_MIXED, reps=10, cache_path=cache)
+        g.tune(hg.HG_FP64, reps=10, cache_path=cache)
+    o = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=max(0.5 * args.tol, 1e-6),
+                        check_every=args.check_every)
+    ctx.solve_batch(grids, o)
+    n0 = ctx.launches()
+    try:
+        import torch
+        nvtx = torch.cuda.nvtx
+    except Exception:   # pragma: no cover
+        nvtx = None
+    if nvtx:
+        nvtx.range_push("timed_batch")   # ncu --nvtx --nvtx-include "timed_batch/"
+    t0 = time.perf_counter()
+    ctx.solve_batch(grids, o)
+    t = time.perf_counter() - t0
+    if nvtx:
+        nvtx.range_pop()
+    print("launches before the timed call: %d; launches in it: %d; %.1f ms, %.1f solves/s"
+          % (n0, ctx.launches() - n0, t * 1e3, len(grids) / t), flush=True)
+    for g in grids:
+        g.close()
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.passes_once:
         return run_passes_once(args)
+    if args.batch_once:
+        return run_batch_once(args)
     if args.impl == "ours" and args.workload == "batched":
         return run_batched(args)
     if args.impl == "ours" and args.workload == "serving":

@@ -335,7 +335,8 @@ typedef struct {
  * events on the context stream, best of three), on the grid's own
  * coefficients with steady-state CG scalars, and sets the fastest (the
  * default unless another is at least 3% faster: closer timings are within the
- * run-to-run spread).  cache_path (NULL: no cache) is a text file of one
+ * run-to-run spread; and the default again unless the whole iteration with
+ * the chosen combination beats it).  cache_path (NULL: no cache) is a text file of one
  * record per line, "hg-tune-v2 <device> <SMs> <prec> <d> <N0> <N1> <N2> <rb>
  * <lb> <lanes0> <lanes1> <ms> <order0> <order1> <order2>", device = its name
  * with blanks as '_', order_a = the radix order of axis a as digits ("357"),

@@ -441,6 +441,13 @@ int hg_tune(hg_grid* g, int prec, int reps, const char* cache_path, hg_tune_resu
     if ((st = apply_cfg(g, pr, best))) return st;
     if (!same_cfg(best, heur)) {
         if ((st = time_passes(g, pr, all, reps, &res.ms_chosen))) return st;
+        // the passes were tuned one group at a time: keep the combination only
+        // if the whole iteration is faster too
+        if (!(res.ms_chosen < res.ms_heuristic)) {
+            best = heur;
+            res.ms_chosen = res.ms_heuristic;
+            if ((st = apply_cfg(g, pr, best))) return st;
+        }
     } else {
         res.ms_chosen = res.ms_heuristic;
     }
