@@ -137,6 +137,17 @@ typedef struct {
                             anisotropy can save many iterations).  A0[0] = 0
                             (default): A0 = lambda_ref I.  Not SPD:
                             HG_ERR_NOT_SPD; with HG_MS or HG_DUAL: HG_ERR_ARG */
+    int batch_tiles;     /* hg_solve_batch only.  1 (default): the last-axis
+                            passes of each grid shape use the largest row tile
+                            (all loads, the most grid rows per CTA) that still
+                            gives at least two CTAs per SM over the shape's
+                            problems: few large CTAs pay off when many problems
+                            share a launch, many small ones for a single
+                            problem.  Iterates then equal a single solve's up to
+                            the rounding of the CTA partial sums.  0: each shape
+                            runs its first grid's launch geometry, and every
+                            problem's iterates equal those of its own
+                            hg_solve_AH bitwise.                              */
 } hg_solve_opts;
 
 typedef struct {
@@ -223,9 +234,9 @@ int hg_solve_AH(hg_grid* grid, const hg_solve_opts* opts, double* AH_out, hg_res
  * groups run concurrently and one graph launch steps every problem; each
  * problem keeps its own convergence status, so converged problems drop out of
  * the launches.  HG_MIXED: each problem's FP64 refinement step runs as soon as
- * its inner FP32 solve stops, beside the next graph launch; every problem's
- * iterates equal those of its own hg_solve_AH.  A group runs with the launch
- * geometry of its first grid.
+ * its inner FP32 solve stops, beside the next graph launch.  A group runs the
+ * strided passes with the launch geometry of its first grid, and the
+ * last-axis passes with the row tile opts->batch_tiles selects.
  * results[p] (n entries) is the result of grids[p]; device_ms and wall_ms are
  * those of the whole batch.  Each problem solves its own d loads (those in
  * loads_mask).  Supports HG_CG, HG_PRIMAL, A0 = I, HG_FP64 and HG_MIXED,

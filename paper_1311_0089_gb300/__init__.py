@@ -53,7 +53,7 @@ class SolveOpts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("time_pass", ctypes.c_int),
                 ("method", ctypes.c_int), ("formulation", ctypes.c_int),
-                ("A0", ctypes.c_double * 9)]
+                ("A0", ctypes.c_double * 9), ("batch_tiles", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):

@@ -102,11 +102,13 @@ int upload_items(Arena& ar, const std::vector<PassArgs>& pas, cudaStream_t s, Ba
 }
 
 // The launches of one operator application for all P problems.
-int launch_batch(hg_grid* g0, int prec, const BatchItems& it, int P, cudaStream_t s) {
+// rc: the row tile of the last-axis passes (the group's), the strided passes
+// run g0's geometry.
+int launch_batch(hg_grid* g0, const RowCfg& rc, int prec, const BatchItems& it, int P, cudaStream_t s) {
     const GridDev& gd = g0->gd;
     const int last = gd.d - 1;
     const int L = it.first.fa.L;
-    HG_CU(launch_row_fwd_batch(prec, gd, g0->plan[last], g0->tw[prec], g0->rowcfg[prec], it.fa, P, L, s));
+    HG_CU(launch_row_fwd_batch(prec, gd, g0->plan[last], g0->tw[prec], rc, it.fa, P, L, s));
     g0->ctx->launches++;
     for (int k = 0; k < it.first.nstr; ++k) {
         const StrArgs& a = it.first.sa[k];
@@ -114,7 +116,7 @@ int launch_batch(hg_grid* g0, int prec, const BatchItems& it, int P, cudaStream_
                                    P, L, a.n, a.inner, a.outer, s));
         g0->ctx->launches++;
     }
-    HG_CU(launch_row_inv_batch(prec, gd, g0->plan[last], g0->tw[prec], g0->rowcfg[prec], it.ia, P, L, s));
+    HG_CU(launch_row_inv_batch(prec, gd, g0->plan[last], g0->tw[prec], rc, it.ia, P, L, s));
     g0->ctx->launches++;
     return HG_OK;
 }
@@ -124,6 +126,7 @@ struct Group {
     std::vector<hg_grid*> gs;
     std::vector<int> pos;        // their positions in the batch
     int P = 0, L = 0;
+    RowCfg rc[2];                // row tile of the last-axis passes, per precision
     BatchItems refine[3];        // items of the refinement launches (FP32 projection,
                                  // FP64 projection, FP64 residual), capacity P
     cudaStream_t side = nullptr; // capture branch of this group
@@ -230,7 +233,7 @@ int make_cg_graph(Batch& b, int prec, const std::vector<char>& member, int* capt
             e = cudaStreamWaitEvent(ss, b.fork, 0);
         }
         for (int i = 0; i < chunk && e == cudaSuccess && st == HG_OK; ++i)
-            st = launch_batch(gr.gs[0], prec, its[k], cnt[k], ss);
+            st = launch_batch(gr.gs[0], gr.rc[prec], prec, its[k], cnt[k], ss);
         if (ss != cs && e == cudaSuccess) e = cudaEventRecord(gr.join, ss);
     }
     for (size_t k = 0; k < G && e == cudaSuccess; ++k)
@@ -271,7 +274,7 @@ int refine_due(Batch& b, const std::vector<char>& due, cudaStream_t s) {
         for (int i = 0; i < n; ++i)
             matvec_args(sub[i], 1, L, sub[i]->work[1].x, false, false, nullptr, nullptr, INV_PROJ, nullptr, 1,
                         sub[i]->work[0].sc, &pas[i]);
-        if ((st = copy_items(pas, s, &gr.refine[0])) || (st = launch_batch(gr.gs[0], 1, gr.refine[0], n, s)))
+        if ((st = copy_items(pas, s, &gr.refine[0])) || (st = launch_batch(gr.gs[0], gr.rc[1], 1, gr.refine[0], n, s)))
             return st;
         for (hg_grid* g : sub) {
             HG_CU(launch_outer_update(g->gd, L, (double*)g->work[0].x, (const float*)g->work[1].x, g->work[0].sc,
@@ -282,13 +285,13 @@ int refine_due(Batch& b, const std::vector<char>& due, cudaStream_t s) {
             for (int i = 0; i < n; ++i)
                 matvec_args(sub[i], 0, L, sub[i]->work[0].x, false, false, nullptr, nullptr, INV_PROJ, nullptr, 1,
                             nullptr, &pas[i]);
-            if ((st = copy_items(pas, s, &gr.refine[1])) || (st = launch_batch(gr.gs[0], 0, gr.refine[1], n, s)))
+            if ((st = copy_items(pas, s, &gr.refine[1])) || (st = launch_batch(gr.gs[0], gr.rc[0], 0, gr.refine[1], n, s)))
                 return st;
         }
         for (int i = 0; i < n; ++i)
             matvec_args(sub[i], 0, L, sub[i]->work[0].x, true, true, nullptr, nullptr, INV_RESID, nullptr, 1, nullptr,
                         &pas[i]);
-        if ((st = copy_items(pas, s, &gr.refine[2])) || (st = launch_batch(gr.gs[0], 0, gr.refine[2], n, s)))
+        if ((st = copy_items(pas, s, &gr.refine[2])) || (st = launch_batch(gr.gs[0], gr.rc[0], 0, gr.refine[2], n, s)))
             return st;
     }
     return HG_OK;
@@ -394,7 +397,7 @@ int start_rhs(Batch& b, bool fp32) {
         BatchItems it;
         if (!fp32) {
             if ((st = make_items(b, gr, &it, 0, nullptr, true, true, INV_RHS, false))) return st;
-            if ((st = launch_batch(gr.gs[0], 0, it, gr.P, b.s))) return st;
+            if ((st = launch_batch(gr.gs[0], gr.rc[0], 0, it, gr.P, b.s))) return st;
             if (b.prec == 0) continue;
             for (hg_grid* g : gr.gs) {
                 const GridDev& gd = g->gd;
@@ -409,7 +412,7 @@ int start_rhs(Batch& b, bool fp32) {
         for (hg_grid* g : gr.gs)
             HG_CU(cudaMemsetAsync(g->work[0].x, 0, sizeof(double) * (size_t)gr.L * g->gd.d * g->gd.M, b.s));
         if ((st = make_items(b, gr, &it, 1, nullptr, true, true, INV_RHS, true))) return st;
-        if ((st = launch_batch(gr.gs[0], 1, it, gr.P, b.s))) return st;
+        if ((st = launch_batch(gr.gs[0], gr.rc[1], 1, it, gr.P, b.s))) return st;
         for (hg_grid* g : gr.gs) {
             HG_CU(launch_inner_init(g->gd, gr.L, nullptr, nullptr, nullptr, nullptr, g->work[0].sc, g->work[1].sc,
                                     b.o.inner_tol, b.o.max_iter, 64, grid_weight(g), g->partial, g->counters + 4,
@@ -445,17 +448,42 @@ int map_status(int s) {
     }
 }
 
+// Row tile of the last-axis passes for P problems of lead's shape in one
+// launch: all loads per CTA and the most grid rows per CTA the kernels accept
+// while the launch still has at least two CTAs per SM (a batched launch has P
+// times the CTAs of a single one, so larger tiles, which stage their twiddles,
+// coefficient table and reduction once for more voxels, pay off).  Falls back
+// to lead's own tile.
+RowCfg batch_row_cfg(const hg_grid* lead, int prec, int P, int sms) {
+    const GridDev& gd = lead->gd;
+    const int d = gd.d, L = d;
+    const size_t csize = prec == 0 ? 16 : 8;
+    for (int RB = MAX_REAL_ROWS_HOST; RB >= 1; --RB) {
+        RowCfg c{};
+        if (!make_row_cfg(prec, gd.Nl, d, L, RB, L, min_radix(lead->plan[d - 1]), csize, lead->ctx->max_smem,
+                          gd.rows, c))
+            continue;
+        if ((long long)P * c.nbx * c.nby >= 2LL * sms) return c;
+    }
+    return lead->rowcfg[prec];
+}
+
 int solve_batch(Batch& b, hg_result* results) {
     hg_grid* g0 = b.gs[0];
     hg_ctx* c = g0->ctx;
     const double t0 = wall_ms();
     const long long launches0 = c->launches.load();
     int st;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     for (Group& gr : b.groups) {
-        // every problem of a group runs its first problem's launch geometry:
-        // its reduction slots must hold that many CTAs
+        // every problem of a group runs the group's launch geometry: its
+        // reduction slots must hold that many CTAs
         hg_grid* lead = gr.gs[0];
-        const long long nbx = std::max(lead->rowcfg[0].nbx, lead->rowcfg[1].nbx);
+        for (int p = 0; p < 2; ++p)
+            gr.rc[p] = b.o.batch_tiles ? batch_row_cfg(lead, p, gr.P, std::max(sms, 1)) : lead->rowcfg[p];
+        const long long nbx = std::max(std::max(lead->rowcfg[0].nbx, lead->rowcfg[1].nbx),
+                                       std::max(gr.rc[0].nbx, gr.rc[1].nbx));
         for (hg_grid* g : gr.gs) {
             if ((st = grid_alloc_common(g))) return st;
             if ((st = grid_ensure_partial(g, nbx))) return st;
@@ -568,6 +596,7 @@ extern "C" int hg_solve_batch(hg_grid* const* grids, int n, const hg_solve_opts*
             if (grids[q] == g) return HG_ERR_ARG;   // each problem needs its own buffers
     }
     if (o.method != HG_CG || o.formulation != HG_PRIMAL || o.A0[0] != 0.0 || o.time_pass != -1) return HG_ERR_ARG;
+    if (o.batch_tiles != 0 && o.batch_tiles != 1) return HG_ERR_ARG;
     // loads beyond a problem's d are ignored per problem (its own d loads)
     cudaSetDevice(c->device);
     std::lock_guard<std::recursive_mutex> lk(c->mu);

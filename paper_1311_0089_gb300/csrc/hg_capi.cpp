@@ -197,6 +197,7 @@ void hg_default_opts(hg_solve_opts* o) {
     o->method = HG_CG;
     o->formulation = HG_PRIMAL;
     for (int i = 0; i < 9; ++i) o->A0[i] = 0.0;
+    o->batch_tiles = 1;
 }
 
 const char* hg_strerror(int s) {

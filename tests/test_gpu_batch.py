@@ -41,7 +41,7 @@ def test_batch_equals_single_solves(hg, ctx, prec):
         g = ctx.grid(m.N)
         g.set_coeffs_phase(m.phase, m.table)
         grids.append(g)
-    o = hg.default_opts(tol=1e-7, prec=pr, max_iter=20000)
+    o = hg.default_opts(tol=1e-7, prec=pr, max_iter=20000, batch_tiles=0)
     batch = ctx.solve_batch(grids, o)
     fields = [g.field(1) for g in grids]
     for g, b, f in zip(grids, batch, fields):
@@ -87,7 +87,7 @@ def test_batch_with_a_homogeneous_problem_and_loads_mask(hg, ctx):
     h = ctx.grid(N)
     h.set_coeffs_phase(np.zeros(N, np.uint8), A0[None])
     grids.append(h)
-    o = hg.default_opts(tol=1e-8, prec=hg.HG_MIXED)
+    o = hg.default_opts(tol=1e-8, prec=hg.HG_MIXED, batch_tiles=0)
     res = ctx.solve_batch(grids, o)
     assert res[-1]["iters"] == [0, 0]
     np.testing.assert_allclose(res[-1]["AH"], A0, atol=1e-13)
@@ -126,16 +126,22 @@ def test_batch_of_mixed_shapes_equals_single_solves(hg, ctx, prec):
         else:
             g.set_coeffs_field(c[1])
         grids.append(g)
-    o = hg.default_opts(tol=1e-8, prec=pr, max_iter=20000)
+    o = hg.default_opts(tol=1e-8, prec=pr, max_iter=20000, batch_tiles=0)
     batch = ctx.solve_batch(grids, o)
     for g, b, (N, c) in zip(grids, batch, probs):
         assert b["status"] == 0 and b["AH"].shape == (len(N), len(N))
         single = g.solve(o)
         assert b["iters"] == single["iters"] and b["outer"] == single["outer"]
         np.testing.assert_array_equal(b["AH"], single["AH"])
-    for g, b, (N, c) in list(zip(grids, batch, probs))[5:8]:
+    # batch row tiles (the default): the same solutions up to rounding
+    tiled = ctx.solve_batch(grids, hg.default_opts(tol=1e-8, prec=pr, max_iter=20000))
+    bound = 1e-6 if prec == "mixed" else 1e-7
+    for g, b, t, (N, c) in zip(grids, batch, tiled, probs):
+        assert t["status"] == 0
+        assert np.max(np.abs(t["AH"] - b["AH"])) <= bound * np.max(np.abs(b["AH"]))
+        assert all(abs(x - y) <= 3 for x, y in zip(t["iters"], b["iters"]))
+    for g, b, (N, c) in list(zip(grids, tiled, probs))[5:8]:
         ref = O.solve_AH(c[1], N, tol=1e-11)["AH"]
-        bound = 1e-6 if prec == "mixed" else 1e-7
         assert np.max(np.abs(b["AH"] - ref)) <= bound * np.max(np.abs(ref))
     for g in grids:
         g.close()
@@ -155,6 +161,7 @@ def test_batch_errors(hg, ctx):
     assert lib.hg_solve_batch(hs1, 1, ctypes.byref(hg.default_opts(formulation=hg.HG_DUAL)), res) == -1
     assert lib.hg_solve_batch(hs1, 1, ctypes.byref(hg.default_opts(A0=2.0 * np.eye(2))), res) == -1
     assert lib.hg_solve_batch(hs1, 0, ctypes.byref(hg.default_opts()), res) == -1
+    assert lib.hg_solve_batch(hs1, 1, ctypes.byref(hg.default_opts(batch_tiles=2)), res) == -1
     other = hg.Context(0)
     b = other.grid((15, 15))
     b.set_coeffs_phase(m.phase, m.table)
@@ -163,3 +170,32 @@ def test_batch_errors(hg, ctx):
     a.close()
     b.close()
     other.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_tiles_many_problems_against_oracle(hg, ctx, prec):
+    """Default batch row tiles on groups large enough to take them (24 x 45^2,
+    12 x 75^2, 6 x 27^3): every A_H within the path's tolerance of the oracle,
+    iteration counts within 3 of the single solves."""
+    pr = hg.HG_MIXED if prec == "mixed" else hg.HG_FP64
+    bound = 1e-6 if prec == "mixed" else 1e-8
+    rng = np.random.default_rng(77)
+    probs = [((45, 45), W.random_spd_field((45, 45), rng, 1.0, 40.0)) for _ in range(24)]
+    probs += [((75, 75), W.random_spd_field((75, 75), rng, 1.0, 40.0)) for _ in range(12)]
+    probs += [((27, 27, 27), W.random_spd_field((27, 27, 27), rng, 1.0, 40.0)) for _ in range(6)]
+    grids = []
+    for N, A in probs:
+        g = ctx.grid(N)
+        g.set_coeffs_field(A)
+        grids.append(g)
+    o = hg.default_opts(tol=1e-10, prec=pr)
+    res = ctx.solve_batch(grids, o)
+    for k, ((N, A), g, r) in enumerate(zip(probs, grids, res)):
+        assert r["status"] == 0
+        if k % 6 == 0:
+            ref = O.solve_AH(A, N, tol=1e-11)["AH"]
+            assert np.max(np.abs(r["AH"] - ref)) <= bound * np.max(np.abs(ref)), (N, k)
+            single = g.solve(o)
+            assert all(abs(x - y) <= 3 for x, y in zip(r["iters"], single["iters"]))
+    for g in grids:
+        g.close()

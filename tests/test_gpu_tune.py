@@ -154,7 +154,7 @@ def test_batch_runs_a_tuned_lead_geometry_on_untuned_problems(hg, ctx):
         grids.append(g)
     grids[0].set_launch_cfg(hg.HG_MIXED, 1, 1, [1, 0])
     grids[0].set_launch_cfg(hg.HG_FP64, 1, 1, [1, 0])
-    o = hg.default_opts(tol=1e-9, prec=hg.HG_MIXED)
+    o = hg.default_opts(tol=1e-9, prec=hg.HG_MIXED, batch_tiles=0)
     res = ctx.solve_batch(grids, o)
     for m, r in zip(ms, res):
         A = np.moveaxis(np.moveaxis(m.table[m.phase.astype(np.intp)], -1, 0), -1, 0)
