@@ -297,6 +297,17 @@ int refine_due(Batch& b, const std::vector<char>& due, cudaStream_t s) {
     return HG_OK;
 }
 
+// A_H (energy and flux forms) of a problem whose iteration has ended, and its
+// copy to the host, on stream s.
+int finish_one(Batch& b, hg_grid* g, cudaStream_t s) {
+    const GridDev& gd = g->gd;
+    HG_CU(launch_energy(gd, gd.d, coeffs_for(g, 0, true), (const double*)g->work[0].x,
+                        b.o.loads_mask & ((1u << gd.d) - 1u), g->partial, g->counters + 5, g->d_AH, s));
+    g->ctx->launches++;
+    HG_CU(cudaMemcpyAsync(g->h_AH, g->d_AH, sizeof(double) * 2 * gd.d * gd.d, cudaMemcpyDeviceToHost, s));
+    return HG_OK;
+}
+
 int restart_due(Batch& b, const std::vector<char>& due, cudaStream_t s) {
     for (int p = 0; p < b.P; ++p) {
         if (!due[p]) continue;
@@ -326,7 +337,7 @@ int run_batch(Batch& b) {
     if ((st = make_cg_graph(b, b.prec, member, &captured))) return st;
     const long long max_chunks =
         (mixed ? (long long)std::max(1, b.o.max_outer) : 1LL) * ((long long)b.o.max_iter / chunk + 3) + 2;
-    std::vector<char> due(b.P, 0), refining(b.P, 0);
+    std::vector<char> due(b.P, 0), refining(b.P, 0), finished(b.P, 0);
     int nrefining = 0;
     for (long long k = 0;; ++k) {
         HG_CU(cudaGraphLaunch(b.cg_exec, b.s));
@@ -363,20 +374,33 @@ int run_batch(Batch& b) {
         }
         refining.swap(due);
         nrefining = ndue;
-        if (nrefining) {
+        // problems whose iteration ended in this chunk: their A_H on the side
+        // stream, beside the chunks of the others
+        bool any_new = false;
+        for (int p = 0; p < b.P; ++p) any_new |= !member[p] && !finished[p];
+        if (nrefining || any_new) {
             // after this chunk's reads, before the next chunk
             HG_CU(cudaEventRecord(b.refined, b.s));
             HG_CU(cudaStreamWaitEvent(b.side, b.refined, 0));
-            if ((st = refine_due(b, refining, b.side))) return st;
         }
+        for (int p = 0; p < b.P; ++p) {
+            if (member[p] || finished[p]) continue;
+            finished[p] = 1;
+            if ((st = finish_one(b, b.gs[p], b.side))) return st;
+        }
+        if (nrefining && (st = refine_due(b, refining, b.side))) return st;
         if (running == 0 || k + 1 >= max_chunks) break;
         if (4 * running <= 3 * captured && (st = make_cg_graph(b, b.prec, member, &captured))) return st;
     }
-    if (nrefining) {
-        // stopped at the chunk limit with refinements in flight
-        HG_CU(cudaEventRecord(b.refined, b.side));
-        HG_CU(cudaStreamWaitEvent(b.s, b.refined, 0));
-    }
+    // A_H of the problems still running at the chunk limit; then the side
+    // stream's work (refinements in flight, A_H) joins the main stream
+    for (int p = 0; p < b.P; ++p)
+        if (!finished[p]) {
+            finished[p] = 1;
+            if ((st = finish_one(b, b.gs[p], b.side))) return st;
+        }
+    HG_CU(cudaEventRecord(b.refined, b.side));
+    HG_CU(cudaStreamWaitEvent(b.s, b.refined, 0));
     return HG_OK;
 }
 
@@ -524,14 +548,7 @@ int solve_batch(Batch& b, hg_result* results) {
             if (any_load(b, p, false, ST_RHS_RECHECK) && (st = restart_rhs64(b, b.gs[p]))) return st;
     }
     if ((st = run_batch(b))) return st;
-    // A_H per problem, then every problem's outer scalars
-    for (hg_grid* g : b.gs) {
-        const GridDev& gd = g->gd;
-        HG_CU(launch_energy(gd, gd.d, coeffs_for(g, 0, true), (const double*)g->work[0].x,
-                            b.o.loads_mask & ((1u << gd.d) - 1u), g->partial, g->counters + 5, g->d_AH, b.s));
-        c->launches++;
-        HG_CU(cudaMemcpyAsync(g->h_AH, g->d_AH, sizeof(double) * 2 * gd.d * gd.d, cudaMemcpyDeviceToHost, b.s));
-    }
+    // (run_batch has enqueued every problem's A_H and joined its side stream)
     HG_CU(cudaEventRecord(g0->ev1, b.s));
     if ((st = read_scalars(b, false))) return st;   // outer scalars hold the inner totals
     float dms = 0.f;
