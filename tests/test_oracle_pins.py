@@ -401,3 +401,42 @@ def test_moulinec_suquet_contracts_at_the_optimal_rate(rho):
         errs.append(math.sqrt(O.inner(e - estar, e - estar)))
         assert errs[-1] <= q ** i * d0 * (1 + 1e-9) + 1e-13, (i, errs[-1] / d0, q ** i)
     assert errs[-1] / errs[-2] > 0.5 * q
+
+
+@pytest.mark.parametrize("N,Y,perm", [((9, 15), (1.0, 2.5), (1, 0)),
+                                      ((5, 9, 7), (1.0, 0.5, 2.0), (2, 0, 1)),
+                                      ((5, 9, 7), (1.0, 1.0, 1.0), (1, 2, 0))])
+def test_axis_permutation_equivariance(N, Y, perm):
+    """Relabelling the axes of the cell (grid, cell sizes Y and tensor
+    components together) relabels A_H: A_H' = P A_H P^T.  Exact for GaNi
+    (Sec. 4.1 grid, xi_a = m_a / Y_a of Sec. 2); catches an axis mixed up in
+    the frequency map, in Y or in the component order."""
+    d = len(N)
+    A = W.random_spd_field(N, np.random.default_rng(sum(N)), 1.0, 20.0)
+    AH = O.solve_AH(A, N, Y=Y, tol=1e-13)["AH"]
+    Np = tuple(N[p] for p in perm)
+    Yp = tuple(Y[p] for p in perm)
+    Ap = np.transpose(A, (0, 1) + tuple(2 + p for p in perm))       # grid axes
+    Ap = Ap[np.ix_(perm, perm)]                                       # components
+    AHp = O.solve_AH(np.ascontiguousarray(Ap), Np, Y=Yp, tol=1e-13)["AH"]
+    np.testing.assert_allclose(AHp, AH[np.ix_(perm, perm)], atol=1e-10 * np.max(np.abs(AH)))
+
+
+def test_reflection_equivariance_and_scalings():
+    """x_a -> -x_a (grid index k -> -k mod N_a) with A -> R A R, R = diag(+-1),
+    gives A_H -> R A_H R; c A gives c A_H; a common factor on every Y_a leaves
+    A_H unchanged (Gamma_hat depends on xi only through its direction)."""
+    N = (9, 7)
+    A = W.random_spd_field(N, np.random.default_rng(21), 1.0, 20.0)
+    AH = O.solve_AH(A, N, tol=1e-13)["AH"]
+    R = np.diag([-1.0, 1.0])
+    idx = (-np.arange(9)) % 9
+    Ar = A[:, :, idx, :] * np.outer(np.diag(R), np.diag(R))[:, :, None, None]
+    AHr = O.solve_AH(np.ascontiguousarray(Ar), N, tol=1e-13)["AH"]
+    np.testing.assert_allclose(AHr, R @ AH @ R, atol=1e-10 * np.max(np.abs(AH)))
+    np.testing.assert_allclose(O.solve_AH(3.5 * A, N, tol=1e-13)["AH"], 3.5 * AH,
+                               atol=1e-10 * np.max(np.abs(AH)))
+    np.testing.assert_allclose(O.solve_AH(A, N, Y=(1.7, 1.7), tol=1e-13)["AH"], AH,
+                               atol=1e-10 * np.max(np.abs(AH)))
+    # an anisotropic cell is not a common factor: A_H changes
+    assert np.max(np.abs(O.solve_AH(A, N, Y=(1.0, 3.0), tol=1e-13)["AH"] - AH)) > 1e-4
