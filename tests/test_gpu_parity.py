@@ -437,3 +437,29 @@ def test_smooth_laminate_continuous_closed_form(hg, ctx):
     r = g.solve(hg.default_opts(tol=1e-10, prec=hg.HG_MIXED))
     np.testing.assert_allclose(r["AH"], exact, atol=1e-7)
     g.close()
+
+
+@pytest.mark.parametrize("N,Y", [((45, 27), (1.0, 2.5)), ((15, 9, 25), (1.0, 0.5, 2.0))])
+def test_anisotropic_cell_solve_and_axis_relabelling(hg, ctx, N, Y):
+    """Solves on a cell with unequal Y_a (xi_a = m_a / Y_a, Sec. 2) against the
+    oracle, FP64 and mixed, and the same medium with its axes relabelled
+    (grid, Y and tensor components together) giving P A_H P^T."""
+    d = len(N)
+    A = W.random_spd_field(N, np.random.default_rng(sum(N) + 1), 1.0, 20.0)
+    ref = O.solve_AH(A, N, Y=Y, tol=1e-12)["AH"]
+    g = ctx.grid(N, Y)
+    g.set_coeffs_field(A)
+    r64 = g.solve(hg.default_opts(tol=1e-11))
+    r32 = g.solve(hg.default_opts(tol=1e-10, prec=hg.HG_MIXED))
+    g.close()
+    assert rel_max(r64["AH"], ref) < 1e-8
+    assert rel_max(r32["AH"], ref) < 1e-6
+    perm = tuple(range(1, d)) + (0,)
+    Np = tuple(N[p] for p in perm)
+    Yp = tuple(Y[p] for p in perm)
+    Ap = np.ascontiguousarray(np.transpose(A, (0, 1) + tuple(2 + p for p in perm))[np.ix_(perm, perm)])
+    gp = ctx.grid(Np, Yp)
+    gp.set_coeffs_field(Ap)
+    rp = gp.solve(hg.default_opts(tol=1e-11))
+    gp.close()
+    assert rel_max(rp["AH"], r64["AH"][np.ix_(perm, perm)]) < 1e-8
