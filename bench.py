@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="c2: skip the 135^3 and batched sub-records of the default line")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the library's default launch geometry (no hg_tune before the warm-up)")
     ap.add_argument("--tol", type=float, default=TOL)
@@ -199,6 +201,29 @@ def pass_bytes(N, L, prec_bytes, n_phases_bytes=1):
     return [3 * vec + M * n_phases_bytes + spec] + [2 * spec] * nstr + [spec + 5 * vec]
 
 
+def resident_bytes(N, iters, prec_bytes=4):
+    """Algorithmic bytes (the fused pass schedule's count) of the iterations a
+    resident launch ran: per load and iteration the three passes' vector and
+    spectrum words (pass_bytes with one load, no phase byte), plus the phase
+    map once per iteration (all loads read it together)."""
+    M = int(np.prod(N))
+    per_load = sum(pass_bytes(N, 1, prec_bytes, 0))
+    return sum(iters) * per_load + max(iters) * M
+
+
+def resident_moved_bytes(N, iters, prec_bytes=4):
+    """Bytes the resident kernel itself moves through L2/HBM per its iterations:
+    the half spectra (written by the row phase, read and written by the column
+    phase, read by the second row phase) and x (read and written); r, p and the
+    phase map stay in shared memory."""
+    d = len(N)
+    M = int(np.prod(N))
+    Ms = M // N[-1] * ((N[-1] + 1) // 2)
+    spec = d * Ms * 2 * prec_bytes
+    vec = d * M * prec_bytes
+    return sum(iters) * (4 * spec + 2 * vec)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -209,7 +234,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("hg_kernels.cuh", "hg_kernels.cu", "fft_device.cuh"):
+    for f in ("hg_kernels.cuh", "hg_kernels.cu", "fft_device.cuh", "hg_resident.cu"):
         with open(os.path.join(ROOT, "paper_1311_0089_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -234,9 +259,10 @@ def profiled_traffic(kernel_key, geometry=None):
 # ----------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------
-def oracle_sample(ms, seconds):
-    """Times the oracle's CG on load e1 of the workload for a bounded number of
-    iterations (chosen to take about `seconds`).  Returns (voxel-iter/s, desc)."""
+def oracle_sample(ms, seconds, load=0, barrier=None):
+    """Times the oracle's CG on load e_(load+1) of the workload for a bounded
+    number of iterations (chosen to take about `seconds`).  Returns
+    (voxel-iter/s, desc, iterations, seconds)."""
     import oracle as O
     A = ms.full_field()
     N = ms.N
@@ -246,15 +272,48 @@ def oracle_sample(ms, seconds):
     O.apply_K(A, u, N)
     t_apply = time.perf_counter() - t0
     iters = int(max(3, min(500, seconds / max(t_apply, 1e-6))))
+    E = np.zeros(len(N))
+    E[load % d] = 1.0
+    if barrier is not None:
+        barrier.wait()
     t0 = time.perf_counter()
-    E1 = np.zeros(len(N))
-    E1[0] = 1.0
-    out = O.cg(A, E1, N, tol=1e-30, maxiter=iters)
+    out = O.cg(A, E, N, tol=1e-30, maxiter=iters)
     t = time.perf_counter() - t0
     M = int(np.prod(N))
-    return M * out["iters"] / t, ("oracle CG (numpy FP64) on load e1 of the %s workload, "
+    return M * out["iters"] / t, ("oracle CG (numpy FP64) on load e%d of the %s workload, "
                                   "%d iterations incl. right-hand side and final true residual, %.1f s"
-                                  % ("x".join(map(str, N)), out["iters"], t)), out["iters"], t
+                                  % (load % d + 1, "x".join(map(str, N)), out["iters"], t)), out["iters"], t
+
+
+def _oracle_worker(name, seconds, load, barrier, queue):
+    sys.path.insert(0, ROOT)
+    ms, _ = workload(name)
+    v, desc, it, t = oracle_sample(ms, seconds, load, barrier)
+    queue.put((v, desc, it, t))
+
+
+def oracle_parallel(name, seconds, workers=None):
+    """The unmodified single-threaded oracle on every host core at once: one
+    spawned process per core, each timing its own bounded CG sample (loads
+    alternating), started together behind a barrier.  Throughput = the sum of
+    the processes' voxel-iterations/s over their (overlapping) timed samples."""
+    import multiprocessing as mp
+    workers = workers or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers)
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(name, seconds, i, barrier, queue), daemon=True)
+             for i in range(workers)]
+    for p in procs:
+        p.start()
+    outs = [queue.get(timeout=600) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+    total = float(sum(o[0] for o in outs))
+    t_max = max(o[3] for o in outs)
+    desc = ("%d concurrent processes (spawned, one per host core), each: %s; value = sum of their "
+            "rates" % (workers, outs[0][1]))
+    return total, desc, workers, t_max
 
 
 # ----------------------------------------------------------------------------
@@ -284,11 +343,13 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    ms, cfg = workload(args.workload if args.workload in ("c2", "c3") else "c2")
+    name = args.workload if args.workload in ("c2", "c3") else "c2"
+    ms, cfg = workload(name)
     vals, descs = [], []
-    per = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    per = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    cores = 1
     for i in range(args.warmup + args.steps):
-        v, desc, it, t = oracle_sample(ms, per)
+        v, desc, cores, t = oracle_parallel(name, per)
         if i >= args.warmup:
             vals.append((v, t))
             descs.append(desc)
@@ -299,7 +360,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": cfg,
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": descs[-1] + "; each step is one such bounded sample",
                          "host_cpus": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -352,18 +413,26 @@ def run_ours(args):
         e1.synchronize()
         return res, e0.elapsed_time(e1)
 
+    r_w = None
     for _ in range(args.warmup):
-        step(o_mixed)
-    # dominant pass of the CG iteration: one untimed solve per pass with the
-    # pass bracketed by CUDA events inside the captured graphs
+        r_w, _ = step(o_mixed)
+    # the FP32 inner solves run the resident kernel (one cooperative launch per
+    # inner solve) where the grid allows it, else the pass kernels
+    resident = bool(r_w and r_w["resident_ctas"] > 0)
     npass = g.num_passes()
     pass_avg = []
-    for p in range(npass):
-        o_p = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=o_mixed.inner_tol, time_pass=p)
-        r_p, _ = step(o_p)
-        pass_avg.append(r_p["pass_ms_total"] / max(1, r_p["pass_launches"]))
-    dom_pass = int(np.argmax(pass_avg))
-    o_mixed.time_pass = dom_pass
+    if resident:
+        dom_pass = -1
+        o_mixed.time_pass = 0      # brackets the resident launch itself
+    else:
+        # dominant pass of the CG iteration: one untimed solve per pass with the
+        # pass bracketed by CUDA events inside the captured graphs
+        for p in range(npass):
+            o_p = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=o_mixed.inner_tol, time_pass=p)
+            r_p, _ = step(o_p)
+            pass_avg.append(r_p["pass_ms_total"] / max(1, r_p["pass_launches"]))
+        dom_pass = int(np.argmax(pass_avg))
+        o_mixed.time_pass = dom_pass
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -371,7 +440,7 @@ def run_ours(args):
     sampler.start()
     launches0 = ctx.launches()
     times, vox, results = [], 0, []
-    dom_ms, dom_n = 0.0, 0
+    dom_ms, dom_n, dom_bytes, dom_moved, dom_iters = 0.0, 0, 0, 0, 0
     for _ in range(args.steps):
         res, ms_ = step(o_mixed)
         times.append(ms_)
@@ -379,6 +448,10 @@ def run_ours(args):
         results.append(res)
         dom_ms += res["pass_ms_total"]
         dom_n += res["pass_launches"]
+        if resident:
+            dom_bytes += resident_bytes(ms.N, res["iters"])
+            dom_moved += resident_moved_bytes(ms.N, res["iters"])
+            dom_iters += max(res["iters"])
     torch.cuda.synchronize()
     launches = ctx.launches() - launches0
     clocks = sampler.stop()
@@ -446,28 +519,60 @@ def run_ours(args):
     for p in range(npass):
         t_ms, name = g.time_pass(p, hg.HG_FP64, reps=10 if d == 2 else 3)
         passes64.append({"kernel": name, "ms_isolated": t_ms, "GBs": pb64[p] / (t_ms * 1e-3) / 1e9})
-    dom = passes[dom_pass]
     dom_avg_ms = dom_ms / max(1, dom_n)
-    achieved = dom["bytes"] / (dom_avg_ms * 1e-3) / 1e9
-    roof = {
-        "bound": "hbm", "kernel": dom["kernel"], "achieved": achieved,
-        "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-        "peak_kind": peak_kind, "traffic": profiled_traffic("fp32_" + keys[dom_pass] + ("" if d == 2 else "_3d"),
-                                     g.launch_cfg(hg.HG_MIXED)),
-        "bytes_per_launch": dom["bytes"], "ms_per_launch": dom_avg_ms, "launches_timed": dom_n,
-        "timing": "CUDA events around this pass in the first iteration of every graph chunk (8 iterations) "
-                  "inside the captured graphs of the timed solves, on the stream the kernels run on",
-        "note": ("working set of one solve (~45 MB FP32) is L2-resident between passes" if d == 2
-                 else "working set (about 1 GB) exceeds L2"),
-        "passes_fp32": passes,
-        "passes_fp64": passes64,
-    }
+    if resident:
+        achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+        moved = dom_moved / (dom_ms * 1e-3) / 1e9
+        roof = {
+            "bound": "hbm", "kernel": "k_cg_resident<%d>" % ms.N[0], "achieved": achieved,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+            "peak_kind": peak_kind, "traffic": profiled_traffic("fp32_resident"),
+            "bytes_per_launch": dom_bytes / max(1, dom_n), "ms_per_launch": dom_avg_ms, "launches_timed": dom_n,
+            "iterations_per_launch": dom_iters / max(1, dom_n),
+            "us_per_iteration": 1e3 * dom_ms / max(1, dom_iters),
+            "ctas": results[-1]["resident_ctas"],
+            "bytes_basis": "algorithmic bytes of the fused pass schedule per load and iteration (read r, p; "
+                           "write p; write, read+write, read the half spectrum; read x, r, p; write x, r) "
+                           "plus the phase map per iteration, times the iterations of the launch",
+            "moved_bytes_per_launch": dom_moved / max(1, dom_n),
+            "achieved_moved": moved, "frac_moved": moved / peaks["hbm_gbs"],
+            "moved_basis": "bytes the kernel itself moves outside the SMs (half spectra 4x, x 2x per load "
+                           "and iteration; r, p and the phase map stay in shared memory)",
+            "timing": "CUDA events around each resident launch (one per inner FP32 solve) in the timed "
+                      "solves, on the stream the kernel runs on",
+            "note": "one cooperative launch per inner solve, one CTA per SM; working set of the "
+                    "exchange (half spectra, x: ~17 MB) is L2-resident",
+            "passes_fp32": passes,
+            "passes_fp64": passes64,
+        }
+        # the same solve with the pass kernels (three launches per iteration in CUDA graphs)
+        o_mp = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=o_mixed.inner_tol, resident=0)
+        step(o_mp)
+        mp_t = [step(o_mp)[1] for _ in range(3)]
+        roof["pass_kernels_solve_ms"] = float(np.mean(mp_t))
+    else:
+        dom = passes[dom_pass]
+        achieved = dom["bytes"] / (dom_avg_ms * 1e-3) / 1e9
+        roof = {
+            "bound": "hbm", "kernel": dom["kernel"], "achieved": achieved,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+            "peak_kind": peak_kind, "traffic": profiled_traffic("fp32_" + keys[dom_pass] + ("" if d == 2 else "_3d"),
+                                         g.launch_cfg(hg.HG_MIXED)),
+            "bytes_per_launch": dom["bytes"], "ms_per_launch": dom_avg_ms, "launches_timed": dom_n,
+            "timing": "CUDA events around this pass in the first iteration of every graph chunk (8 iterations) "
+                      "inside the captured graphs of the timed solves, on the stream the kernels run on",
+            "note": ("working set of one solve (~45 MB FP32) is L2-resident between passes" if d == 2
+                     else "working set (about 1 GB) exceeds L2"),
+            "passes_fp32": passes,
+            "passes_fp64": passes64,
+        }
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
-        v, desc, it, t = oracle_sample(ms, args.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-               "host_cpus": os.cpu_count()}
+    if rank == 0 and not args.no_cpu and ws == 1:
+        v, desc, cores, t = oracle_parallel(args.workload, args.cpu_seconds)
+        v1, desc1, _, _ = oracle_sample(ms, min(args.cpu_seconds, 6.0))
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+               "host_cpus": os.cpu_count(), "one_core": {"value": v1, "sample": desc1}}
 
     lat = sorted(times)
     line = {
@@ -490,6 +595,11 @@ def run_ours(args):
         "launch_geometry": tuned if tuned else {"mixed": g.launch_cfg(hg.HG_MIXED),
                                                  "fp64": g.launch_cfg(hg.HG_FP64), "tuned": False},
     }
+    if rank == 0 and ws == 1 and args.workload == "c2" and not args.no_sub:
+        # the HBM-bound 3D configuration and the batched configuration, driver-timed
+        # beside the headline (each with its own clocks and plain-FP64 comparison)
+        line["c3"] = sub_c3(hg, torch, dev, args)
+        line["batched"] = sub_batched(hg, torch, dev, args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     g.close()
@@ -497,6 +607,141 @@ def run_ours(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def sub_c3(hg, torch, dev, args):
+    """135^3 (3D, state ~1 GB > L2): mixed solves, dominant pass roofline, A_H
+    against the oracle's golden value, one plain FP64 solve."""
+    ms, cfg = workload("c3")
+    N, d = ms.N, 3
+    M = int(np.prod(N))
+    stream = torch.cuda.current_stream(dev)
+    ctx = hg.Context(dev.index, stream=stream)
+    g = ctx.grid(N)
+    g.set_coeffs_phase(torch.from_numpy(ms.phase).to(dev), torch.from_numpy(ms.table).to(dev))
+    tuned = g.tune(hg.HG_MIXED, reps=4)
+    inner = max(0.5 * args.tol, 1e-6)
+    o = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=inner)
+
+    def step(opts):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = g.solve(opts)
+        e1.record(stream)
+        e1.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    step(o)
+    npass = g.num_passes()
+    pass_avg = []
+    for p in range(npass):
+        r_p, _ = step(hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=inner, time_pass=p))
+        pass_avg.append(r_p["pass_ms_total"] / max(1, r_p["pass_launches"]))
+    dom_pass = int(np.argmax(pass_avg))
+    o.time_pass = dom_pass
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    times, vox, dom_ms, dom_n, last = [], 0, 0.0, 0, None
+    for _ in range(3):
+        last, t = step(o)
+        times.append(t)
+        vox += M * sum(last["iters"])
+        dom_ms += last["pass_ms_total"]
+        dom_n += last["pass_launches"]
+    clocks = sampler.stop()
+    r64, t64 = step(hg.default_opts(tol=args.tol, prec=hg.HG_FP64))
+    gold_path = os.path.join(ROOT, "tests", "golden", "spheres_135_AH.json")
+    ref_kind, err, err64 = None, None, None
+    if os.path.exists(gold_path):
+        with open(gold_path) as f:
+            ref = np.array(json.load(f)["AH"])
+        ref_kind = "FP64 oracle at tol 1e-12 (tests/golden/spheres_135_AH.json)"
+        err, err64 = ah_err(last["AH"], ref), ah_err(r64["AH"], ref)
+    peaks, peak_kind = measured_peaks()
+    keys = ["row_fwd", "strided_a1", "strided_a0", "strided_a1i", "row_inv"]
+    pb = pass_bytes(N, d, 4)
+    dom_avg = dom_ms / max(1, dom_n)
+    achieved = pb[dom_pass] / (dom_avg * 1e-3) / 1e9
+    t_total = sum(times) / 1e3
+    out = {
+        "config": cfg,
+        "solves_per_s": len(times) / t_total, "voxel_iter_per_s": vox / t_total,
+        "ms_per_solve": float(np.mean(times)), "iters": last["iters"], "outer": last["outer"],
+        "AH_rel_err_vs_oracle": err, "AH_reference": ref_kind,
+        "fp64_plain": {"ms_per_solve": t64, "solves_per_s": 1e3 / t64, "iters": r64["iters"],
+                       "AH_rel_err_vs_oracle": err64, "launch_geometry": "default (not tuned)"},
+        "speedup_vs_fp64_plain_solves": t64 / float(np.mean(times)),
+        "roofline": {"bound": "hbm", "kernel": keys[dom_pass], "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
+                     "bytes_per_launch": pb[dom_pass], "ms_per_launch": dom_avg, "launches_timed": dom_n,
+                     "traffic": profiled_traffic("fp32_" + keys[dom_pass] + "_3d", g.launch_cfg(hg.HG_MIXED)),
+                     "pass_ms_in_solve": dict(zip(keys, pass_avg)),
+                     "iteration_ms": float(sum(pass_avg))},
+        "launch_geometry": tuned["chosen"],
+        "clocks": clocks,
+    }
+    g.close()
+    ctx.close()
+    return out
+
+
+def sub_batched(hg, torch, dev, args):
+    """A seeded 64-problem subset of the 256-problem batched workload in one
+    hg_solve_batch call, against plain per-request FP64 solves of the same 64."""
+    import workloads as W
+    probs = W.batch_2d()
+    rng = np.random.default_rng(20261311)
+    idx = sorted(rng.choice(len(probs), size=64, replace=False).tolist())
+    probs = [probs[i] for i in idx]
+    ctx = hg.Context(dev.index, use_torch_stream=False)
+    grids = []
+    for p in probs:
+        g = ctx.grid(p.N)
+        g.set_coeffs_phase(torch.from_numpy(p.phase).to(dev), torch.from_numpy(p.table).to(dev))
+        grids.append(g)
+    o = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=max(0.5 * args.tol, 1e-6))
+    ctx.solve_batch(grids, o)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    ts, vox, res = [], 0, None
+    for _ in range(3):
+        t0 = time.perf_counter()
+        res = ctx.solve_batch(grids, o)
+        ts.append(time.perf_counter() - t0)
+        vox += sum(int(np.prod(p.N)) * sum(r["iters"]) for p, r in zip(probs, res))
+    clocks = sampler.stop()
+    assert all(r["status"] == 0 for r in res)
+    tol64 = args.tol / 5      # 1e-6 in A_H at contrasts up to 1e4 needs it (see run_batched)
+    o64 = hg.default_opts(tol=tol64, prec=hg.HG_FP64)
+    grids[0].solve(o64)
+    t0 = time.perf_counter()
+    r64 = [g.solve(o64) for g in grids]
+    t64 = time.perf_counter() - t0
+    o_tight = hg.default_opts(tol=1e-10, prec=hg.HG_FP64)
+    err, err64 = 0.0, 0.0
+    for i in range(0, 64, 8):
+        tight = grids[i].solve(o_tight)["AH"]
+        err = max(err, ah_err(res[i]["AH"], tight))
+        err64 = max(err64, ah_err(r64[i]["AH"], tight))
+    sps = len(grids) * len(ts) / sum(ts)
+    out = {
+        "config": {"workload": "64 of the 256 batched problems (seeded subset): 2D two-phase ellipses, sizes "
+                               "{45,75,135,243,375}^2, contrast log-uniform [10,1e4], loads e1,e2, rel. "
+                               "residual %g; one hg_solve_batch call, default launch geometry" % args.tol,
+                   "sizes": {str(n): sum(1 for p in probs if p.N[0] == n) for n in (45, 75, 135, 243, 375)}},
+        "solves_per_s": sps, "voxel_iter_per_s": vox / sum(ts), "ms_per_batch": 1e3 * float(np.mean(ts)),
+        "AH_max_rel_err_vs_fp64_tol1e-10": err,
+        "plain_fp64_per_request": {"solves_per_s": len(grids) / t64, "tol": tol64,
+                                   "AH_max_rel_err_vs_fp64_tol1e-10": err64},
+        "speedup_vs_plain_fp64": sps * t64 / len(grids),
+        "clocks": clocks,
+    }
+    for g in grids:
+        g.close()
+    ctx.close()
+    return out
 
 
 def run_passes_once(args):

@@ -54,7 +54,8 @@ typedef enum {
     HG_ERR_NOT_SPD = -3,            /* a coefficient tensor is not symmetric PD  */
     HG_ERR_NO_MEMORY = -4,          /* device allocation or the ctx budget failed */
     HG_ERR_NOT_CONVERGED = -5,      /* max_iter reached; best iterate is kept     */
-    HG_ERR_DEVICE_TIMEOUT = -6,     /* a bounded device-side wait gave up         */
+    HG_ERR_DEVICE_TIMEOUT = -6,     /* a bounded device-side wait (a grid barrier
+                                       of the resident solver) gave up           */
     HG_ERR_BUSY = -7,               /* grid borrowed by a pending ticket          */
     HG_ERR_CUDA = -8,               /* a CUDA runtime call failed                 */
     HG_ERR_CANCELLED = -9,          /* the ticket was cancelled                   */
@@ -148,6 +149,21 @@ typedef struct {
                             runs its first grid's launch geometry, and every
                             problem's iterates equal those of its own
                             hg_solve_AH bitwise.                              */
+    int resident;        /* HG_MIXED on a square 2D grid of side 45, 75, 81,
+                            135, 243, 375 or 729: run each inner FP32 solve as
+                            ONE cooperative launch whose CTAs (one per SM) keep
+                            the residual and the search direction of their grid
+                            rows in shared memory for all its iterations, with
+                            bounded grid-wide barriers between the row, column
+                            and row phases of an iteration.  -1 (default): when
+                            the state fits on chip; 0: never (the pass kernels,
+                            check_every iterations per CUDA graph); > 0: with at
+                            most that many CTAs.  The iterates equal those of
+                            the pass kernels up to the rounding of the partial
+                            sums.  time_pass >= 0 then times that launch (one
+                            per inner solve).  hg_solve_AH only: hg_submit and
+                            hg_solve_batch run the pass kernels.  A barrier wait
+                            that gives up returns HG_ERR_DEVICE_TIMEOUT.       */
 } hg_solve_opts;
 
 typedef struct {
@@ -175,6 +191,13 @@ typedef struct {
     double CH[9];           /* HG_DUAL: compliance C_H[i][j] = (A_N^-1 s_j, s_i)
                                (energy form); AH = C_H^-1, AH_flux = the inverse
                                of the mean-field form <A_N^-1 s_j>_i           */
+    double true_rel_res[3]; /* ||b - G_N A_N e~|| / ||b|| recomputed in FP64 from
+                               the returned e~ at exit (the paper leaves the
+                               stopping rule of Sec. 5.3 open; this is the
+                               residual the recursion does not see), in the
+                               scalar product of the iteration; 0 for loads
+                               not solved or with a zero right-hand side      */
+    int resident_ctas;      /* CTAs of the resident FP32 solver (0: not used)  */
 } hg_result;
 
 /* Fill opts with the defaults listed above. */
@@ -281,7 +304,9 @@ int hg_spectrum(hg_grid* grid, const double* u, double* S_out, int prec, int on_
  * loops in which cudaMalloc/cudaFree and their synchronisation are not
  * allowed).  It needs no hg_ctx or hg_grid.
  *   d, N      : as hg_create_grid (N_a odd, factors 3/5/7, <= 1024).
- *   phase     : device pointer, |N| uint8 phase indices (< n_phases).
+ *   phase     : device pointer, |N| uint8 phase indices (< n_phases).  The
+ *               map is not checked (that would need a read-back): an index
+ *               >= n_phases is read as n_phases - 1, never past the table.
  *   table     : device pointer, n_phases x d x d doubles (SPD, not checked).
  *   u, out    : device pointers, d x |N| doubles each (component-major).
  *   cuda_stream: cudaStream_t to enqueue on (NULL = the legacy default stream).
@@ -363,6 +388,15 @@ int hg_tune(hg_grid* grid, int prec, int reps, const char* cache_path, hg_tune_r
  * NULL) receives the recorded time. */
 int hg_tune_cache_find(const char* cache_path, const char* device_name, int sm_count, int prec, int d,
                        const int* N, hg_launch_cfg* out, double* ms_out);
+
+/* Error-path check of the resident FP32 solver (not in the paper): an
+ * HG_MIXED hg_solve_AH in which CTA drop_cta (>= 1) of the resident launch
+ * leaves at once, so the other CTAs' barrier waits run out after their time
+ * limit (0.1 s here).  Returns HG_ERR_DEVICE_TIMEOUT when the grid runs the
+ * resident solver (the context stays usable; the grid's last result is
+ * meaningless), the plain solve's status otherwise; HG_ERR_ARG for
+ * drop_cta < 1, HG_FP64, resident = 0 or time_pass >= 0. */
+int hg_test_resident_timeout(hg_grid* grid, const hg_solve_opts* opts, int drop_cta, hg_result* info);
 
 /* Kernel launches made through this context so far (all entry points). */
 long long hg_launch_count(hg_ctx* ctx);

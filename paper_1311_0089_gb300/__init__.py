@@ -53,7 +53,7 @@ class SolveOpts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("time_pass", ctypes.c_int),
                 ("method", ctypes.c_int), ("formulation", ctypes.c_int),
-                ("A0", ctypes.c_double * 9), ("batch_tiles", ctypes.c_int)]
+                ("A0", ctypes.c_double * 9), ("batch_tiles", ctypes.c_int), ("resident", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -63,7 +63,8 @@ class Result(ctypes.Structure):
                 ("device_ms", ctypes.c_double), ("wall_ms", ctypes.c_double),
                 ("launches", ctypes.c_longlong), ("pass_ms_total", ctypes.c_double),
                 ("pass_launches", ctypes.c_int), ("lambda_ref", ctypes.c_double),
-                ("c_A", ctypes.c_double), ("C_A", ctypes.c_double), ("CH", ctypes.c_double * 9)]
+                ("c_A", ctypes.c_double), ("C_A", ctypes.c_double), ("CH", ctypes.c_double * 9),
+                ("true_rel_res", ctypes.c_double * 3), ("resident_ctas", ctypes.c_int)]
 
     def to_dict(self) -> dict:
         d = self.d
@@ -83,6 +84,8 @@ class Result(ctypes.Structure):
             "c_A": self.c_A,
             "C_A": self.C_A,
             "CH": np.array(self.CH[: d * d]).reshape(d, d),
+            "true_rel_res": list(self.true_rel_res[:d]),
+            "resident_ctas": self.resident_ctas,
         }
 
 
@@ -119,6 +122,7 @@ SIGNATURES = [
     ("hg_set_coeffs_phase", _I, [_VP, _VP, _I, _VP, _I]),
     ("hg_set_coeffs_exact", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), _VP, _I, _VP]),
     ("hg_solve_AH", _I, [_VP, ctypes.POINTER(SolveOpts), _VP, ctypes.POINTER(Result)]),
+    ("hg_test_resident_timeout", _I, [_VP, ctypes.POINTER(SolveOpts), _I, ctypes.POINTER(Result)]),
     ("hg_get_field", _I, [_VP, _I, _VP, _I]),
     ("hg_submit", _I, [_VP, _VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(ctypes.c_uint64)]),
     ("hg_poll", _I, [_VP, ctypes.c_uint64, ctypes.POINTER(Result), _I]),
@@ -342,6 +346,13 @@ class Grid:
         out = r.to_dict()
         out["status"] = st
         return out
+
+    def test_resident_timeout(self, drop_cta: int, opts: Optional[SolveOpts] = None) -> int:
+        """hg_test_resident_timeout: a mixed solve in which CTA drop_cta of the
+        resident launch leaves at once; returns the status code."""
+        r = Result()
+        o = opts if opts is not None else default_opts(prec=HG_MIXED)
+        return int(load().hg_test_resident_timeout(self.h, ctypes.byref(o), drop_cta, ctypes.byref(r)))
 
     def field(self, load_idx: int, out=None) -> np.ndarray:
         """e~ of load `load_idx` from the last solve, shape (d, *N)."""

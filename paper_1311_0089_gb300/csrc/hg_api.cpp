@@ -249,7 +249,9 @@ int grid_alloc_work(hg_grid* g, int prec) {
     const int L = gd.d;
     const size_t ts = prec == 0 ? 8 : 4;
     const size_t nv = (size_t)L * gd.d * gd.M;
-    const size_t ns = (size_t)L * gd.d * gd.Ms;
+    // the FP32 half spectra leave room for rows padded to an even length (the
+    // resident solver's layout, 16-byte aligned rows for bulk copies)
+    const size_t ns = (size_t)L * gd.d * (prec == 1 ? gd.rows * ((gd.H + 1) & ~1) : gd.Ms);
     Work& w = g->work[prec];
     int st;
     if ((st = dev_alloc(g->ctx, &w.x, nv * ts))) return st;
@@ -280,6 +282,7 @@ void grid_free_work(hg_grid* g) {
     dev_free(c, g->d_AH); g->d_AH = nullptr;
     dev_free(c, g->d_E); g->d_E = nullptr;
     dev_free(c, g->d_A0); g->d_A0 = nullptr;
+    dev_free(c, g->d_sc_aux); g->d_sc_aux = nullptr;
 }
 
 size_t ctx_reclaim(hg_ctx* ctx, hg_grid* keep) {
@@ -307,6 +310,7 @@ int grid_alloc_common(hg_grid* g) {
     for (int l = 0; l < gd.d; ++l) E[l * gd.d + l] = 1.0;
     HG_CU(cudaMemcpyAsync(g->d_E, E, sizeof(E), cudaMemcpyHostToDevice, g->ctx->stream));
     if ((st = dev_alloc(g->ctx, (void**)&g->d_A0, 16 * sizeof(double)))) return st;
+    if ((st = dev_alloc(g->ctx, (void**)&g->d_sc_aux, sizeof(Scalars) * MAXL))) return st;
     HG_CU(cudaStreamSynchronize(g->ctx->stream));
     (void)gd;
     return HG_OK;
@@ -578,6 +582,7 @@ static int map_status(int s) {
         case ST_CONVERGED: case ST_ZERO_RHS: case ST_IDLE: case ST_STAGNATED: return HG_OK;
         case ST_MAXITER: case ST_ACTIVE: return HG_ERR_NOT_CONVERGED;
         case ST_BREAKDOWN: return HG_ERR_BREAKDOWN;
+        case ST_TIMEOUT: return HG_ERR_DEVICE_TIMEOUT;
         default: return HG_ERR_CUDA;
     }
 }
@@ -606,8 +611,71 @@ static void job_collect_pass_times(Job& j) {
     j.prof_prev_iters = it;
 }
 
+// The resident FP32 solver (one cooperative launch for a whole inner solve,
+// r and p kept on chip; hg_resident.cu) when the job allows it and the grid's
+// state fits: square 2D grids of the resident lengths.  Returns 1 if it
+// launched, 0 if the pass kernels are to be used, < 0 on error.
+static int job_launch_resident(Job& j) {
+    hg_grid* g = j.g;
+    const GridDev& gd = g->gd;
+    if (!j.allow_resident || j.o.resident == 0 || gd.d != 2 || gd.N[0] != gd.N[1] ||
+        g->coeff_mode < 0 || !resident_length(gd.N[0]))
+        return 0;
+    ResCfg cfg;
+    if (!resident_cfg(gd.N[0], gd.d, j.o.resident > 0 ? j.o.resident : 0, g->ctx->nsm, g->ctx->max_smem, cfg))
+        return 0;
+    // barrier targets count 3 per iteration and CTA in 32 bits
+    if ((long long)j.o.max_iter * 3 * cfg.T >= (1LL << 31)) return 0;
+    if ((long long)2 * cfg.T * MAXL > g->partial_slots) return 0;
+    ResArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = gd;
+    a.co = coeffs_for(g, 1, true);
+    a.L = gd.d;
+    a.units = gd.N[0] * gd.d;
+    a.cunits = gd.H * gd.d;
+    a.umax = cfg.umax;
+    a.bufp = cfg.bufp;
+    a.r0 = static_cast<const float*>(g->work[1].r);
+    a.x = static_cast<float*>(g->work[1].x);
+    a.S = static_cast<float2*>(g->work[1].S);
+    a.tw = static_cast<const float2*>(g->tw[1]) + g->plan[0].tw_off;
+    a.sc = g->work[1].sc;
+    a.part = g->partial;
+    a.bar = g->counters + 8;
+    a.err = reinterpret_cast<int*>(g->counters + 9);
+    a.dual = g->form;
+    a.has_A0 = g->has_ref;
+    for (int i = 0; i < 4; ++i) a.A0[i] = (float)g->ref[i];
+    a.band[0] = g->band[0];
+    a.band[1] = g->band[1];
+    a.W = grid_weight(g);
+    a.drop_cta = j.res_drop_cta;
+    a.wait_ns = j.res_drop_cta > 0 ? 100000000ull : 1000000000ull;   // 1 s per barrier wait (0.1 s in the test)
+    HG_CU(cudaMemsetAsync(g->counters + 8, 0, 2 * sizeof(unsigned), j.s));
+    const bool timed = j.o.time_pass >= 0;
+    if (timed) {
+        for (int i = 0; i < 2; ++i)
+            if (!g->prof_ev[i]) HG_CU(cudaEventCreate(&g->prof_ev[i]));
+        HG_CU(cudaEventRecord(g->prof_ev[0], j.s));
+    }
+    HG_CU(launch_resident(gd.N[0], a, cfg, j.s));
+    if (timed) HG_CU(cudaEventRecord(g->prof_ev[1], j.s));
+    g->ctx->launches++;
+    j.res_ctas = cfg.T;
+    j.launched = (long long)j.o.max_iter + 4LL * j.chunk;   // the launch ran every iteration
+    j.cg_prec = 1;
+    HG_CU(cudaMemcpyAsync(g->h_sc, g->work[1].sc, sizeof(Scalars) * MAXL, cudaMemcpyDeviceToHost, j.s));
+    HG_CU(cudaEventRecord(j.tick, j.s));
+    return 1;
+}
+
 static int job_launch_chunk(Job& j, int prec) {
     hg_grid* g = j.g;
+    if (prec == 1) {
+        const int r = job_launch_resident(j);
+        if (r != 0) return r > 0 ? HG_OK : r;
+    }
     cudaGraphExec_t ge;
     int nk = 0;
     int st = get_cg_graph(g, prec, j.chunk, &ge, &nk, j.o.time_pass);
@@ -650,6 +718,16 @@ static int job_start_inner(Job& j) {
 static int job_finish_enqueue(Job& j) {
     hg_grid* g = j.g;
     const GridDev& gd = g->gd;
+    if (j.prec == 0) {
+        // FP64 recursive residuals drift from b - K x: recompute the residual of
+        // the returned iterate once (INV_RESID on scratch scalars that carry
+        // this solve's ||b||; the mixed path's last outer step already is it)
+        HG_CU(cudaMemcpyAsync(g->d_sc_aux, g->work[0].sc, sizeof(Scalars) * MAXL, cudaMemcpyDeviceToDevice, j.s));
+        const int st = enqueue_matvec(g, 0, gd.d, g->work[0].x, true, true, nullptr, nullptr, INV_RESID,
+                                      nullptr, 0, j.s, g->d_sc_aux);
+        if (st) return st;
+        HG_CU(cudaMemcpyAsync(g->h_sc + MAXL, g->d_sc_aux, sizeof(Scalars) * MAXL, cudaMemcpyDeviceToHost, j.s));
+    }
     CoeffsDev c64 = coeffs_for(g, 0, true);
     HG_CU(launch_energy(gd, gd.d, c64, (const double*)g->work[0].x, j.o.loads_mask, g->partial,
                         g->counters + 5, g->d_AH, j.s));
@@ -833,6 +911,7 @@ int job_begin(Job& j) {
     j.prof_prev_iters = 0;
     j.prof_ms = 0.0;
     j.prof_n = 0;
+    j.res_ctas = 0;
     if (g->coeff_mode < 0) return HG_ERR_NO_COEFFS;
     int st;
     if ((st = grid_alloc_common(g))) return st;
@@ -931,7 +1010,10 @@ int job_advance(Job& j, bool* done) {
                 }
                 if (ms != HG_OK && result == HG_OK) result = ms;
                 r.rel_res[l] = sc.relres;
+                const bool solved = sc.status != ST_IDLE && sc.status != ST_ZERO_RHS && sc.bnorm > 0.0;
+                r.true_rel_res[l] = !solved ? 0.0 : (j.prec == 0 ? g->h_sc[MAXL + l].relres : sc.relres);
             }
+            r.resident_ctas = j.res_ctas;
             r.status = result;
             r.device_ms = dms;
             r.wall_ms = now_ms() - j.t0;
@@ -955,11 +1037,13 @@ int job_advance(Job& j, bool* done) {
     }
 }
 
-int solve_impl(hg_grid* g, const hg_solve_opts* o, double* AH_out, hg_result* info) {
+int solve_impl(hg_grid* g, const hg_solve_opts* o, double* AH_out, hg_result* info, int res_drop_cta) {
     Job j;
     j.g = g;
     j.o = *o;
     j.s = g->ctx->stream;
+    j.allow_resident = true;
+    j.res_drop_cta = res_drop_cta;
     j.ev0 = g->ev0;
     j.ev1 = g->ev1;
     j.tick = g->ev_tick;

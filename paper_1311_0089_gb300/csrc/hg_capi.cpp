@@ -99,7 +99,8 @@ namespace hgrt {
 int validate_solve_opts(const hg_grid* g, hg_solve_opts* o) {
     if (!(o->tol > 0.0) || o->max_iter < 1 || (o->prec != HG_FP64 && o->prec != HG_MIXED) ||
         !(o->inner_tol > 0.0) || o->inner_tol >= 1.0 || (o->method != HG_CG && o->method != HG_MS) ||
-        !std::isfinite(o->lambda_ref) || (o->formulation != HG_PRIMAL && o->formulation != HG_DUAL))
+        !std::isfinite(o->lambda_ref) || (o->formulation != HG_PRIMAL && o->formulation != HG_DUAL) ||
+        o->resident < -1)
         return HG_ERR_ARG;
     if (o->A0[0] != 0.0) {
         if (o->method != HG_CG || o->formulation != HG_PRIMAL || g->exact) return HG_ERR_ARG;
@@ -198,6 +199,7 @@ void hg_default_opts(hg_solve_opts* o) {
     o->formulation = HG_PRIMAL;
     for (int i = 0; i < 9; ++i) o->A0[i] = 0.0;
     o->batch_tiles = 1;
+    o->resident = -1;
 }
 
 const char* hg_strerror(int s) {
@@ -250,6 +252,8 @@ int hg_create(hg_ctx** out, int device, size_t budget, void* stream) {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     c->max_smem = std::max(48 * 1024, optin - 4 * 1024);
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
+    if (c->nsm < 1) c->nsm = 1;
     cudaError_t e = configure_kernels(c->max_smem);
     if (e != cudaSuccess) {
         set_last_cuda_error(e, "cudaFuncSetAttribute");
@@ -307,7 +311,7 @@ int hg_create_grid(hg_ctx* c, int d, const int* N, const double* Y, hg_grid** ou
     gd.invMf = (float)gd.invM;
     int st = grid_init_plans(g);
     if (st == HG_OK) {
-        cudaError_t e = cudaMallocHost((void**)&g->h_sc, sizeof(Scalars) * MAXL);
+        cudaError_t e = cudaMallocHost((void**)&g->h_sc, sizeof(Scalars) * 2 * MAXL);
         if (e == cudaSuccess) e = cudaMallocHost((void**)&g->h_AH, sizeof(double) * 32);
         if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
         if (e == cudaSuccess) e = cudaEventCreate(&g->ev1);
@@ -556,6 +560,20 @@ int hg_solve_AH(hg_grid* g, const hg_solve_opts* opts, double* AH_out, hg_result
     DeviceGuard dg(c->device);
     std::lock_guard<std::recursive_mutex> lk(c->mu);
     return solve_impl(g, &o, AH_out, info);
+}
+
+int hg_test_resident_timeout(hg_grid* g, const hg_solve_opts* opts, int drop_cta, hg_result* info) {
+    if (!g || drop_cta < 1) return HG_ERR_ARG;
+    hg_solve_opts o;
+    if (opts) o = *opts; else hg_default_opts(&o);
+    const int vst = validate_solve_opts(g, &o);
+    if (vst) return vst;
+    if (o.prec != HG_MIXED || o.resident == 0 || o.time_pass >= 0) return HG_ERR_ARG;
+    if (g->borrowed.load() > 0) return HG_ERR_BUSY;
+    hg_ctx* c = g->ctx;
+    DeviceGuard dg(c->device);
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    return solve_impl(g, &o, nullptr, info, drop_cta);
 }
 
 int hg_get_field(hg_grid* g, int load, double* e_out, int on_device) {

@@ -20,8 +20,10 @@ enum {
     ST_BREAKDOWN = 4,
     ST_IDLE = 5,       // not part of this solve (load not requested)
     ST_STAGNATED = 6,  // inner FP32 solve stopped improving (refinement goes on)
-    ST_RHS_RECHECK = 7 // FP32 right-hand side too small to tell from zero: the
-                       // solve recomputes it in FP64
+    ST_RHS_RECHECK = 7, // FP32 right-hand side too small to tell from zero: the
+                        // solve recomputes it in FP64
+    ST_TIMEOUT = 8      // a bounded device-side wait (grid barrier of the
+                        // resident solver) gave up
 };
 
 // Per-system CG scalars kept on the device (written by the last CTA of a
@@ -152,6 +154,40 @@ struct RowInvArgs {
                                 //    the previous kernel (tables written only by copies)
     Weight W;                   // (r, r) of INV_CG / INV_RHS / INV_RESID in the product (W r, r)
 };
+
+// Resident FP32 CG solver for square 2D grids (hg_resident.cu): one
+// cooperative launch runs every iteration of the inner FP32 solve, with r and
+// p kept in the shared memory of a team of CTAs (one per SM) and grid-wide
+// barriers between the row, column and row phases of each iteration.
+struct ResArgs {
+    GridDev g;
+    CoeffsDev co;          // FP32 coefficients: mode 0 (phase map + table) or 1 (packed field)
+    int L;                 // systems (loads)
+    int units, cunits;     // row units N * L (grid row, load), column units H * L
+    int umax, bufp;        // most row units of a CTA; pencils of the transform buffer
+    const float* r0;       // initial residual [L][2][M]
+    float* x;              // [L][2][M] solution of the inner system (zeroed by the kernel)
+    float2* S;             // [L][2][N][H] half spectra (scratch)
+    const float2* tw;      // W_N^m, m < N
+    Scalars* sc;           // [L] inner scalars: read at start, written at exit
+    double* part;          // [2][team][MAXL] CTA partial sums
+    unsigned* bar;         // barrier counter, zero at launch
+    int* err;              // zero at launch; set when a barrier wait gives up
+    int dual, has_A0;
+    float A0[4];
+    int band[2];
+    Weight W;
+    int drop_cta;          // >= 0: that CTA leaves at once (exercises the bounded wait)
+    unsigned long long wait_ns;   // limit of one barrier wait
+};
+struct ResCfg { int T; int umax; int bufp; int smem; };
+// Whether square grids of side n have a resident kernel.
+bool resident_length(int n);
+// Team size and shared-memory layout for an n x n grid with L loads; T = 0
+// picks the default.  False if the state does not fit on chip.
+bool resident_cfg(int n, int L, int T, int nsm, int max_smem, ResCfg& cfg);
+cudaError_t launch_resident(int n, const ResArgs& a, const ResCfg& cfg, cudaStream_t s);
+cudaError_t configure_resident(int max_smem, const double* ctw);
 
 // Launchers (prec: 0 = double, 1 = float).  Return cudaGetLastError().
 cudaError_t launch_row_fwd(int prec, const GridDev& g, const AxisPlanH& pl, const void* tw,

@@ -183,20 +183,16 @@ template <typename T, int D>
 __device__ __forceinline__ void load_coeffs(const CoeffsDev& co, long long k, long long M, T (&a)[D][D],
                                             const T* tab) {
     if (co.mode == 0) {
-        const T* tb = tab + (int)co.phase[k] * D * D;
+        // an index past the table (possible only through hg_apply_noalloc,
+        // whose phase map is not checked on the host) reads the last entry
+        const T* tb = tab + min((int)co.phase[k], co.n_phases - 1) * D * D;
 #pragma unroll
         for (int i = 0; i < D; ++i)
 #pragma unroll
             for (int j = 0; j < D; ++j) a[i][j] = tb[i * D + j];
         return;
     }
-    if (co.mode == 0) {
-        const T* tb = static_cast<const T*>(co.table) + (int)co.phase[k] * D * D;
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-#pragma unroll
-            for (int j = 0; j < D; ++j) a[i][j] = __ldg(&tb[i * D + j]);
-    } else if (co.mode == 1) {
+    if (co.mode == 1) {
         const T* f = static_cast<const T*>(co.field);
         if (D == 2) {
             a[0][0] = f[k]; a[1][1] = f[M + k]; a[0][1] = a[1][0] = f[2 * M + k];

@@ -31,6 +31,7 @@ struct hg_ctx {
     std::atomic<int> ngrids{0};         // live grids (hg_destroy refuses while > 0)
     std::set<hg_grid*> grids;           // live grids (guarded by mu)
     int max_smem = 48 * 1024;
+    int nsm = 1;                        // streaming multiprocessors of the device
     std::recursive_mutex mu;            // serialises device work issued by callers
     hgrt::Scheduler* sched = nullptr;   // request scheduler (hg_submit / hg_poll)
 };
@@ -100,7 +101,9 @@ struct hg_grid {
     double* d_AH = nullptr;        // 32 doubles: [0, 18) A_H forms, [24, 26) bounds
     double* d_E = nullptr;
     double* d_A0 = nullptr;
-    hgk::Scalars* h_sc = nullptr;  // pinned: scalars of the last tick
+    hgk::Scalars* d_sc_aux = nullptr;   // FP64 true residual at exit (scratch scalars)
+    hgk::Scalars* h_sc = nullptr;  // pinned: scalars of the last tick [MAXL], then the
+                                   // true-residual scalars [MAXL]
     double* h_AH = nullptr;        // pinned: 2 d x d (energy, flux)
     hgrt::GraphCache graphs[2];
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_tick = nullptr;
@@ -171,6 +174,10 @@ struct Job {
     double zscale = 1.0;        // scale of the zero right-hand-side test
     double lambda = 0.0;
     int stall_max = 64;         // inner FP32 solves: iterations without a 4x drop
+    bool allow_resident = false;   // inner FP32 solves may run the resident kernel
+    int res_ctas = 0;           // CTAs of the last resident launch (0: none)
+    int res_drop_cta = -1;      // >= 1: that CTA of the resident launch leaves at once, so
+                                // the others' bounded barrier waits run out (error-path test)
     int prof_prev_iters = 0;    // time_pass: iterations done before the chunk in flight
     double prof_ms = 0.0;
     int prof_n = 0;
@@ -181,7 +188,7 @@ void grid_free_work(hg_grid* g);
 // Frees the solver state of every grid of ctx that no ticket holds (except
 // `keep`); returns the bytes released.  Caller holds ctx->mu.
 size_t ctx_reclaim(hg_ctx* ctx, hg_grid* keep);
-int solve_impl(hg_grid* g, const hg_solve_opts* o, double* AH_out, hg_result* info);
+int solve_impl(hg_grid* g, const hg_solve_opts* o, double* AH_out, hg_result* info, int res_drop_cta = -1);
 int validate_solve_opts(const hg_grid* g, hg_solve_opts* o);
 int ga_build_field(hg_grid* g, const int* Ntr, const int* P, const uint8_t* phase, const double* table,
                    double* out64, float* out32, cudaStream_t s);

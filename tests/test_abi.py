@@ -47,6 +47,7 @@ def test_strerror_and_defaults_without_gpu(built_lib):
     assert lib.hg_strerror(-2).decode().startswith("unsupported grid size")
     o = hg.default_opts()
     assert o.tol == 1e-10 and o.max_iter == 10000 and o.check_every == 8 and o.prec == 0
+    assert o.resident == -1
 
 
 def test_null_arguments_are_rejected_without_gpu(built_lib):

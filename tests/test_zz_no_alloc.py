@@ -67,3 +67,36 @@ def test_noalloc_rejects_oversize_grid(hg):
     st = lib.hg_apply_noalloc(2, (ctypes.c_int * 2)(4, 5), _dev(ph), 1, _dev(dummy), _dev(dummy),
                               _dev(dummy), None)
     assert st == -2
+
+
+def test_noalloc_out_of_range_phase_reads_last_entry(hg):
+    """The phase map of hg_apply_noalloc is a device buffer the library does not
+    read back: a byte >= n_phases must not read past the table; it is read as the
+    last phase, so the result equals the one with that byte set to n_phases - 1."""
+    import torch
+    lib = hg.load()
+    rng = np.random.default_rng(5)
+    N = (45, 75)
+    d = 2
+    phase = (rng.random(N) < 0.3).astype(np.uint8)
+    table = W.isotropic_table([1.0, 40.0], d)
+    bad = phase.copy()
+    bad[3, 7] = 200                      # out of range for a 2-entry table
+    fixed = phase.copy()
+    fixed[3, 7] = 1
+    u = rng.standard_normal((d,) + N)
+    dev = torch.device("cuda", 0)
+    tab_d = torch.from_numpy(table).to(dev)
+    u_d = torch.from_numpy(u).to(dev)
+    Narr = (ctypes.c_int * d)(*N)
+    stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    outs = []
+    for ph in (bad, fixed):
+        ph_d = torch.from_numpy(ph).to(dev)
+        out = torch.full((d,) + N, float("nan"), dtype=torch.float64, device=dev)
+        st = lib.hg_apply_noalloc(d, Narr, _dev(ph_d), 2, _dev(tab_d), _dev(u_d), _dev(out), stream)
+        assert st == 0, hg.STATUS.get(st, st)
+        torch.cuda.synchronize()
+        outs.append(out.cpu().numpy())
+    assert np.all(np.isfinite(outs[0]))
+    np.testing.assert_array_equal(outs[0], outs[1])
