@@ -294,6 +294,32 @@ size_t ctx_reclaim(hg_ctx* ctx, hg_grid* keep) {
     return before - ctx->used.load();
 }
 
+// Device bytes a solve of precision prec (1: mixed, FP32 buffers as well)
+// still has to allocate on g, row-pass reduction slots for nbx CTAs included:
+// admission compares it with the budget before allocating anything.
+size_t solve_bytes_needed(const hg_grid* g, int prec, long long nbx) {
+    const GridDev& gd = g->gd;
+    const int L = gd.d;
+    size_t need = 0;
+    auto work = [&](int pr) {
+        const size_t ts = pr == 0 ? 8 : 4;
+        const size_t nv = (size_t)L * gd.d * gd.M;
+        const size_t ns = (size_t)L * gd.d * (pr == 1 ? gd.rows * ((gd.H + 1) & ~1) : gd.Ms);
+        return 3 * nv * ts + ns * 2 * ts + sizeof(Scalars) * MAXL;
+    };
+    if (!g->work[0].ready) need += work(0);
+    if (prec == 1 && !g->work[1].ready) need += work(1);
+    long long slots = std::max<long long>(std::max(g->rowcfg[0].nbx, g->rowcfg[1].nbx) * MAXL, 18LL * 8 * 1024);
+    slots = std::max<long long>(slots, nbx * MAXL);
+    if (!g->partial) {
+        need += (size_t)slots * sizeof(double) + 16 * sizeof(unsigned) + 32 * sizeof(double) +
+                (MAXL * MAXD + 16) * sizeof(double) + sizeof(Scalars) * MAXL;
+    } else if (slots > g->partial_slots) {
+        need += (size_t)slots * sizeof(double);
+    }
+    return need;
+}
+
 int grid_alloc_common(hg_grid* g) {
     if (g->partial) return HG_OK;
     const GridDev& gd = g->gd;
@@ -948,8 +974,12 @@ int job_advance(Job& j, bool* done) {
     switch (j.phase) {
         case Job::PLAIN:
         case Job::INNER: {
-            for (int l = 0; l < L; ++l)
+            for (int l = 0; l < L; ++l) {
+                // a bounded wait of the resident solver gave up: its state is
+                // incomplete, the solve ends here (the context stays usable)
+                if (h[l].status == ST_TIMEOUT) return HG_ERR_DEVICE_TIMEOUT;
                 if (h[l].status == ST_RHS_RECHECK) return job_start_rhs(j, false);
+            }
             job_collect_pass_times(j);
             const int mi = j.o.max_iter;
             if (any_active(h, L) && j.launched <= (long long)mi + 2 * j.chunk)

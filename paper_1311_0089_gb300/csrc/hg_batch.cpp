@@ -594,6 +594,429 @@ bool same_shape(const hg_grid* a, const hg_grid* b) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Rolling batch: cross-request batching for the request scheduler
+// ---------------------------------------------------------------------------
+// Admitted requests of one precision (standard CG, primal, A0 = I) form one
+// rolling batch.  Every tick steps all of them by check_every CG iterations:
+// per grid shape each pass is ONE launch for all its requests (the batched
+// pass kernels, grid z = request).  Between ticks the scheduler admits new
+// requests (their right-hand sides are enqueued at once and they join the
+// next tick) and retires finished ones; mixed-precision requests whose inner
+// FP32 solve has stopped get their FP64 refinement step batched per shape.
+// A shape's row tile is fixed when the shape first appears (the batch tile
+// for a nominal 64 requests), never taken from the current mix, and a
+// batched launch computes every request's tiles and reductions as it would
+// alone: a request's result does not depend on which others share its ticks.
+namespace hgrt {
+
+struct RollShape {
+    RowCfg rc[2]{};
+    std::vector<int> members;     // indices into Rolling::mem
+    BatchItems cg, ref[3];        // CG iteration and refinement items, capacity cap
+    std::vector<void*> blocks;    // their device arrays
+    int cap = 0;
+    hg_grid* key = nullptr;       // a grid of this shape (shape comparison only)
+    int d = 0, N[3] = {0, 0, 0};
+    double Y[3] = {0, 0, 0};
+};
+
+struct RollMember {
+    hg_grid* g = nullptr;
+    uint64_t tag = 0;
+    hg_solve_opts o{};
+    int shape = -1;
+    bool checked = false;         // mixed: the FP32 right-hand side's zero test has been read
+    bool refining = false;        // refinement enqueued: the next inner solve starts next tick
+    long long ticks = 0;
+    double t0 = 0.0;
+    long long launches0 = 0;
+};
+
+struct Rolling {
+    hg_ctx* ctx = nullptr;
+    int prec = 0, chunk = 8, sms = 1;
+    cudaStream_t s = nullptr;
+    std::vector<RollMember> mem;
+    std::vector<RollShape> shapes;
+    bool dirty = true;
+    int gcap = 0;
+    const Scalars** d_src = nullptr;
+    Scalars* d_gather = nullptr;
+    Scalars* h_gather = nullptr;
+};
+
+static void roll_free_shape(Rolling* R, RollShape& sh) {
+    for (void* b : sh.blocks) dev_free(R->ctx, b);
+    sh.blocks.clear();
+    sh.cap = 0;
+}
+
+static int roll_items_alloc(Rolling* R, RollShape& sh, int need) {
+    if (need <= sh.cap) return HG_OK;
+    const int cap = std::max(need, std::max(8, 2 * sh.cap));
+    roll_free_shape(R, sh);
+    BatchItems* all[4] = {&sh.cg, &sh.ref[0], &sh.ref[1], &sh.ref[2]};
+    for (BatchItems* it : all) {
+        void* p = nullptr;
+        int st;
+        if ((st = dev_alloc(R->ctx, &p, cap * sizeof(RowFwdArgs)))) return st;
+        sh.blocks.push_back(p);
+        it->fa = (RowFwdArgs*)p;
+        if ((st = dev_alloc(R->ctx, &p, cap * sizeof(RowInvArgs)))) return st;
+        sh.blocks.push_back(p);
+        it->ia = (RowInvArgs*)p;
+        for (int k = 0; k < 3; ++k) {
+            if ((st = dev_alloc(R->ctx, &p, cap * sizeof(StrArgs)))) return st;
+            sh.blocks.push_back(p);
+            it->sa[k] = (StrArgs*)p;
+        }
+    }
+    sh.cap = cap;
+    return HG_OK;
+}
+
+Rolling* rolling_create(hg_ctx* ctx, int prec, int chunk) {
+    Rolling* R = new Rolling();
+    R->ctx = ctx;
+    R->prec = prec;
+    R->chunk = std::max(1, chunk);
+    R->sms = std::max(1, ctx->nsm);
+    if (cudaStreamCreateWithFlags(&R->s, cudaStreamNonBlocking) != cudaSuccess) {
+        delete R;
+        return nullptr;
+    }
+    return R;
+}
+
+void rolling_destroy(Rolling* R) {
+    if (!R) return;
+    cudaStreamSynchronize(R->s);
+    for (RollShape& sh : R->shapes) roll_free_shape(R, sh);
+    dev_free(R->ctx, (void*)R->d_src);
+    dev_free(R->ctx, R->d_gather);
+    if (R->h_gather) cudaFreeHost(R->h_gather);
+    cudaStreamDestroy(R->s);
+    delete R;
+}
+
+int rolling_chunk(const Rolling* R) { return R->chunk; }
+int rolling_size(const Rolling* R) { return (int)R->mem.size(); }
+
+static bool roll_same_shape(const RollShape& sh, const hg_grid* g) {
+    if (sh.d != g->gd.d) return false;
+    for (int k = 0; k < 3; ++k)
+        if (sh.N[k] != g->gd.N[k] || sh.Y[k] != g->gd.Y[k]) return false;
+    return true;
+}
+
+static int roll_shape_of(Rolling* R, const hg_grid* g) {
+    for (size_t k = 0; k < R->shapes.size(); ++k)
+        if (roll_same_shape(R->shapes[k], g)) return (int)k;
+    RollShape sh;
+    sh.d = g->gd.d;
+    for (int k = 0; k < 3; ++k) { sh.N[k] = g->gd.N[k]; sh.Y[k] = g->gd.Y[k]; }
+    for (int p = 0; p < 2; ++p) sh.rc[p] = batch_row_cfg(g, p, 64, R->sms);
+    R->shapes.push_back(sh);
+    return (int)R->shapes.size() - 1;
+}
+
+long long rolling_nbx(Rolling* R, const hg_grid* g) {
+    const RollShape& sh = R->shapes[roll_shape_of(R, g)];
+    return std::max(std::max(g->rowcfg[0].nbx, g->rowcfg[1].nbx), std::max(sh.rc[0].nbx, sh.rc[1].nbx));
+}
+
+static void roll_load_status(const hg_solve_opts& o, int L, int* init_st) {
+    for (int l = 0; l < MAXL; ++l) init_st[l] = (l < L && ((o.loads_mask >> l) & 1u)) ? ST_ACTIVE : ST_IDLE;
+}
+
+int rolling_add(Rolling* R, hg_grid* g, const hg_solve_opts& o, uint64_t tag) {
+    const int L = g->gd.d;
+    const long long nbx = rolling_nbx(R, g);
+    int st;
+    if ((st = grid_alloc_common(g))) return st;
+    if ((st = grid_ensure_partial(g, nbx))) return st;
+    if ((st = grid_alloc_work(g, 0))) return st;
+    if (R->prec == 1 && (st = grid_alloc_work(g, 1))) return st;
+    g->form = 0;
+    g->has_ref = 0;
+    // the right-hand side (as a single solve computes it), on the batch's stream
+    int init_st[MAXL];
+    roll_load_status(o, L, init_st);
+    HG_CU(launch_init_scalars(g->work[0].sc, L, init_st, o.tol, R->prec ? o.max_outer : o.max_iter, 0.0, 1.0, R->s));
+    g->ctx->launches++;
+    if (R->prec == 0) {
+        if ((st = enqueue_matvec(g, 0, L, nullptr, true, true, nullptr, nullptr, INV_RHS, nullptr, 1, R->s))) return st;
+    } else {
+        HG_CU(cudaMemsetAsync(g->work[0].x, 0, sizeof(double) * (size_t)L * g->gd.d * g->gd.M, R->s));
+        if ((st = enqueue_matvec(g, 1, L, nullptr, true, true, nullptr, nullptr, INV_RHS, nullptr, 1, R->s,
+                                 g->work[0].sc)))
+            return st;
+        HG_CU(launch_inner_init(g->gd, L, nullptr, nullptr, nullptr, nullptr, g->work[0].sc, g->work[1].sc,
+                                o.inner_tol, o.max_iter, 64, grid_weight(g), g->partial, g->counters + 4, R->s));
+        g->ctx->launches++;
+    }
+    RollMember m;
+    m.g = g;
+    m.tag = tag;
+    m.o = o;
+    m.shape = roll_shape_of(R, g);
+    m.checked = R->prec == 0;
+    m.t0 = wall_ms();
+    m.launches0 = g->ctx->launches.load();
+    R->mem.push_back(m);
+    R->dirty = true;
+    return HG_OK;
+}
+
+void rolling_remove(Rolling* R, uint64_t tag) {
+    cudaStreamSynchronize(R->s);
+    for (size_t i = 0; i < R->mem.size(); ++i)
+        if (R->mem[i].tag == tag) {
+            R->mem.erase(R->mem.begin() + (long)i);
+            R->dirty = true;
+            return;
+        }
+}
+
+// Member lists per shape, CG items and gather pointers of the current members.
+static int roll_rebuild(Rolling* R) {
+    for (RollShape& sh : R->shapes) sh.members.clear();
+    for (size_t i = 0; i < R->mem.size(); ++i) R->shapes[R->mem[i].shape].members.push_back((int)i);
+    int st;
+    for (RollShape& sh : R->shapes) {
+        if (sh.members.empty()) continue;
+        if ((st = roll_items_alloc(R, sh, (int)sh.members.size()))) return st;
+        std::vector<PassArgs> pas(sh.members.size());
+        for (size_t i = 0; i < sh.members.size(); ++i) {
+            hg_grid* g = R->mem[sh.members[i]].g;
+            cg_iteration_args(g, R->prec, g->gd.d, &pas[i]);
+        }
+        if ((st = copy_items(pas, R->s, &sh.cg))) return st;
+    }
+    const int P = (int)R->mem.size();
+    if (2 * P > R->gcap) {
+        const int cap = std::max(2 * P, std::max(64, 2 * R->gcap));
+        cudaStreamSynchronize(R->s);
+        dev_free(R->ctx, (void*)R->d_src);
+        dev_free(R->ctx, R->d_gather);
+        if (R->h_gather) cudaFreeHost(R->h_gather);
+        R->d_src = nullptr; R->d_gather = nullptr; R->h_gather = nullptr; R->gcap = 0;
+        if ((st = dev_alloc(R->ctx, (void**)&R->d_src, cap * sizeof(Scalars*)))) return st;
+        if ((st = dev_alloc(R->ctx, (void**)&R->d_gather, (size_t)cap * MAXL * sizeof(Scalars)))) return st;
+        HG_CU(cudaMallocHost((void**)&R->h_gather, (size_t)cap * MAXL * sizeof(Scalars)));
+        R->gcap = cap;
+    }
+    std::vector<const Scalars*> src(2 * P);
+    for (int p = 0; p < P; ++p) {
+        src[p] = R->mem[p].g->work[0].sc;
+        src[P + p] = R->mem[p].g->work[R->prec].sc;
+    }
+    HG_CU(cudaMemcpyAsync(R->d_src, src.data(), 2 * P * sizeof(Scalars*), cudaMemcpyHostToDevice, R->s));
+    HG_CU(cudaStreamSynchronize(R->s));   // src is pageable and goes out of scope
+    R->dirty = false;
+    return HG_OK;
+}
+
+static bool roll_any(const Scalars* h, int L, int status) {
+    for (int l = 0; l < L; ++l)
+        if (h[l].status == status) return true;
+    return false;
+}
+
+int rolling_tick(Rolling* R, std::vector<RollDone>* done) {
+    if (R->mem.empty()) return HG_OK;
+    int st;
+    if (R->dirty && (st = roll_rebuild(R))) return st;
+    const bool mixed = R->prec == 1;
+    const int P = (int)R->mem.size();
+    // check_every iterations of every member: per shape one launch per pass
+    for (int i = 0; i < R->chunk; ++i)
+        for (RollShape& sh : R->shapes) {
+            if (sh.members.empty()) continue;
+            hg_grid* g0 = R->mem[sh.members[0]].g;   // plans and twiddles of the shape
+            if ((st = launch_batch(g0, sh.rc[R->prec], R->prec, sh.cg, (int)sh.members.size(), R->s))) return st;
+        }
+    const int n = mixed ? 2 * P : P;
+    HG_CU(launch_gather_scalars(R->d_src, R->d_gather, n, R->s));
+    HG_CU(cudaMemcpyAsync(R->h_gather, R->d_gather, sizeof(Scalars) * MAXL * n, cudaMemcpyDeviceToHost, R->s));
+    HG_CU(cudaStreamSynchronize(R->s));
+    std::vector<char> due(P, 0), fin(P, 0);
+    bool any_due = false, any_fin = false;
+    for (int p = 0; p < P; ++p) {
+        RollMember& m = R->mem[p];
+        hg_grid* g = m.g;
+        const int L = g->gd.d;
+        const Scalars* ho = R->h_gather + (size_t)p * MAXL;
+        const Scalars* hi = R->h_gather + (size_t)(P + p) * MAXL;
+        m.ticks++;
+        if (!m.checked) {
+            m.checked = true;
+            if (roll_any(ho, L, ST_RHS_RECHECK)) {
+                // FP32 right-hand side too small to decide the zero test: the
+                // FP64 one, as the single solve does
+                int init_st[MAXL];
+                roll_load_status(m.o, L, init_st);
+                HG_CU(launch_init_scalars(g->work[0].sc, L, init_st, m.o.tol, m.o.max_outer, 0.0, 1.0, R->s));
+                g->ctx->launches++;
+                if ((st = enqueue_matvec(g, 0, L, nullptr, true, true, nullptr, nullptr, INV_RHS, nullptr, 1, R->s)))
+                    return st;
+                HG_CU(launch_inner_init(g->gd, L, (const double*)g->work[0].r, (float*)g->work[1].r,
+                                        (float*)g->work[1].p, (float*)g->work[1].x, g->work[0].sc, g->work[1].sc,
+                                        m.o.inner_tol, m.o.max_iter, 64, grid_weight(g), g->partial,
+                                        g->counters + 4, R->s));
+                g->ctx->launches++;
+                continue;
+            }
+        }
+        const long long max_ticks =
+            (mixed ? (long long)std::max(1, m.o.max_outer) : 1LL) * ((long long)m.o.max_iter / R->chunk + 3) + 2;
+        if (!roll_any(ho, L, ST_ACTIVE) || m.ticks > max_ticks) {
+            fin[p] = 1;
+            any_fin = true;
+            continue;
+        }
+        if (!mixed) continue;
+        if (m.refining) {
+            // the refinement step enqueued last tick has run: next inner solve
+            HG_CU(launch_inner_init(g->gd, L, (const double*)g->work[0].r, (float*)g->work[1].r,
+                                    (float*)g->work[1].p, (float*)g->work[1].x, g->work[0].sc, g->work[1].sc,
+                                    m.o.inner_tol, m.o.max_iter, 64, grid_weight(g), g->partial, g->counters + 4,
+                                    R->s));
+            g->ctx->launches++;
+            m.refining = false;
+            continue;
+        }
+        if (roll_any(hi, L, ST_ACTIVE)) continue;
+        int steps = 0;
+        for (int l = 0; l < L; ++l)
+            if (ho[l].status == ST_ACTIVE) steps = std::max(steps, ho[l].iters);
+        if (steps >= std::max(1, m.o.max_outer)) {
+            fin[p] = 1;
+            any_fin = true;
+            continue;
+        }
+        due[p] = 1;
+        any_due = true;
+    }
+    // FP64 refinement steps of the due members, batched per shape (the steps of
+    // a single solve: delta <- Gamma delta, x64 += delta, [x64 <- Gamma x64],
+    // r = -G A (E + x64))
+    if (any_due) {
+        for (RollShape& sh : R->shapes) {
+            std::vector<int> sub;
+            for (int i : sh.members)
+                if (due[i]) sub.push_back(i);
+            if (sub.empty()) continue;
+            const int ns = (int)sub.size();
+            hg_grid* g0 = R->mem[sub[0]].g;
+            const int L = g0->gd.d;
+            std::vector<PassArgs> pas(ns);
+            for (int i = 0; i < ns; ++i) {
+                hg_grid* g = R->mem[sub[i]].g;
+                matvec_args(g, 1, L, g->work[1].x, false, false, nullptr, nullptr, INV_PROJ, nullptr, 1,
+                            g->work[0].sc, &pas[i]);
+            }
+            if ((st = copy_items(pas, R->s, &sh.ref[0])) || (st = launch_batch(g0, sh.rc[1], 1, sh.ref[0], ns, R->s)))
+                return st;
+            for (int i : sub) {
+                hg_grid* g = R->mem[i].g;
+                HG_CU(launch_outer_update(g->gd, L, (double*)g->work[0].x, (const float*)g->work[1].x,
+                                          g->work[0].sc, g->work[1].sc, R->s));
+                g->ctx->launches++;
+            }
+            bool tight = false;
+            for (int i : sub) tight |= R->mem[i].o.tol < 1e-8;
+            if (tight) {
+                std::vector<PassArgs> pt;
+                std::vector<int> tsub;
+                for (int i : sub)
+                    if (R->mem[i].o.tol < 1e-8) tsub.push_back(i);
+                pt.resize(tsub.size());
+                for (size_t i = 0; i < tsub.size(); ++i) {
+                    hg_grid* g = R->mem[tsub[i]].g;
+                    matvec_args(g, 0, L, g->work[0].x, false, false, nullptr, nullptr, INV_PROJ, nullptr, 1, nullptr,
+                                &pt[i]);
+                }
+                if ((st = copy_items(pt, R->s, &sh.ref[1])) ||
+                    (st = launch_batch(g0, sh.rc[0], 0, sh.ref[1], (int)tsub.size(), R->s)))
+                    return st;
+            }
+            for (int i = 0; i < ns; ++i) {
+                hg_grid* g = R->mem[sub[i]].g;
+                matvec_args(g, 0, L, g->work[0].x, true, true, nullptr, nullptr, INV_RESID, nullptr, 1, nullptr,
+                            &pas[i]);
+            }
+            if ((st = copy_items(pas, R->s, &sh.ref[2])) || (st = launch_batch(g0, sh.rc[0], 0, sh.ref[2], ns, R->s)))
+                return st;
+            for (int i : sub) R->mem[i].refining = true;
+        }
+    }
+    if (!any_fin) return HG_OK;
+    // finished members: FP64 true residual (FP64 path), A_H, then the results
+    for (int p = 0; p < P; ++p) {
+        if (!fin[p]) continue;
+        hg_grid* g = R->mem[p].g;
+        const GridDev& gd = g->gd;
+        if (!mixed) {
+            HG_CU(cudaMemcpyAsync(g->d_sc_aux, g->work[0].sc, sizeof(Scalars) * MAXL, cudaMemcpyDeviceToDevice, R->s));
+            if ((st = enqueue_matvec(g, 0, gd.d, g->work[0].x, true, true, nullptr, nullptr, INV_RESID, nullptr, 0,
+                                     R->s, g->d_sc_aux)))
+                return st;
+            HG_CU(cudaMemcpyAsync(g->h_sc + MAXL, g->d_sc_aux, sizeof(Scalars) * MAXL, cudaMemcpyDeviceToHost, R->s));
+        }
+        HG_CU(launch_energy(gd, gd.d, coeffs_for(g, 0, true), (const double*)g->work[0].x,
+                            R->mem[p].o.loads_mask & ((1u << gd.d) - 1u), g->partial, g->counters + 5, g->d_AH,
+                            R->s));
+        g->ctx->launches++;
+        HG_CU(cudaMemcpyAsync(g->h_AH, g->d_AH, sizeof(double) * 2 * gd.d * gd.d, cudaMemcpyDeviceToHost, R->s));
+    }
+    HG_CU(cudaStreamSynchronize(R->s));
+    std::vector<RollMember> keep;
+    for (int p = 0; p < P; ++p) {
+        RollMember& m = R->mem[p];
+        if (!fin[p]) {
+            keep.push_back(m);
+            continue;
+        }
+        hg_grid* g = m.g;
+        const GridDev& gd = g->gd;
+        RollDone dn;
+        memset(&dn, 0, sizeof(dn));
+        dn.tag = m.tag;
+        hg_result& r = dn.res;
+        r.d = gd.d;
+        for (int i = 0; i < gd.d * gd.d; ++i) { r.AH[i] = g->h_AH[i]; r.AH_flux[i] = g->h_AH[gd.d * gd.d + i]; }
+        int res = HG_OK;
+        const Scalars* ho = R->h_gather + (size_t)p * MAXL;
+        for (int l = 0; l < gd.d; ++l) {
+            const Scalars& sc = ho[l];
+            const int ms = map_status(sc.status);
+            if (mixed) {
+                r.iters[l] = sc.total_iters;
+                r.outer[l] = sc.iters;
+            } else {
+                r.iters[l] = sc.iters;
+            }
+            if (ms != HG_OK && res == HG_OK) res = ms;
+            r.rel_res[l] = sc.relres;
+            const bool solved = sc.status != ST_IDLE && sc.status != ST_ZERO_RHS && sc.bnorm > 0.0;
+            r.true_rel_res[l] = !solved ? 0.0 : (mixed ? sc.relres : g->h_sc[MAXL + l].relres);
+        }
+        r.status = res;
+        r.wall_ms = wall_ms() - m.t0;
+        r.launches = g->ctx->launches.load() - m.launches0;
+        g->last_prec = R->prec;
+        dn.status = res;
+        done->push_back(dn);
+    }
+    R->mem.swap(keep);
+    R->dirty = true;
+    return HG_OK;
+}
+
+}  // namespace hgrt
+
 extern "C" int hg_solve_batch(hg_grid* const* grids, int n, const hg_solve_opts* opts, hg_result* results) {
     if (!grids || n < 1 || !results) return HG_ERR_ARG;
     hg_grid* g0 = grids[0];

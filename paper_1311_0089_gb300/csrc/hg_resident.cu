@@ -40,74 +40,65 @@ namespace hgk {
 
 constexpr int RES_THREADS = 512;
 
-// FFT plans of the resident kernels (FP32, both axes of length N) and the
-// butterflies each thread holds per stage (B).  Radices stay at most 15: a
-// radix-27 butterfly needs more registers than a 512-thread CTA leaves a
-// thread (128) beside the solver's own state.
+// FFT plans of the resident kernels (FP32, both axes of length N).  Radices
+// stay at most 15: a radix-27 butterfly needs more registers than a
+// 512-thread CTA leaves a thread (128) beside the solver's own state.
 template <int N> struct ResPlan;
-template <> struct ResPlan<729> { typedef RadixList<9, 9, 9> type; static constexpr int B = 1; };
-template <> struct ResPlan<375> { typedef RadixList<15, 5, 5> type; static constexpr int B = 1; };
-template <> struct ResPlan<243> { typedef RadixList<9, 9, 3> type; static constexpr int B = 1; };
-template <> struct ResPlan<135> { typedef RadixList<15, 9> type; static constexpr int B = 1; };
-template <> struct ResPlan<81> { typedef RadixList<9, 9> type; static constexpr int B = 1; };
-template <> struct ResPlan<75> { typedef RadixList<15, 5> type; static constexpr int B = 1; };
-template <> struct ResPlan<45> { typedef RadixList<9, 5> type; static constexpr int B = 1; };
+template <> struct ResPlan<729> { typedef RadixList<9, 9, 9> type; };
+template <> struct ResPlan<375> { typedef RadixList<15, 5, 5> type; };
+template <> struct ResPlan<243> { typedef RadixList<9, 9, 3> type; };
+template <> struct ResPlan<135> { typedef RadixList<15, 9> type; };
+template <> struct ResPlan<81> { typedef RadixList<9, 9> type; };
+template <> struct ResPlan<75> { typedef RadixList<15, 5> type; };
+template <> struct ResPlan<45> { typedef RadixList<9, 5> type; };
 #define HG_RES_SIZES(X) X(729) X(375) X(243) X(135) X(81) X(75) X(45)
 
-// One in-place Stockham stage (the formulation of fft_device.cuh) over npen
-// contiguous pencils of length N, B butterflies per thread (the caller keeps
-// npen * N / R <= B * RES_THREADS).  tw: this stage's table, [r-1][k], k < NS.
-template <int N, int R, int NS, bool INV, int B>
-__device__ __forceinline__ void rstage(float2* buf, int npen, const float2* tw) {
+// One inverse Stockham stage (the formulation of fft_device.cuh), out of
+// place: npen contiguous pencils of length N from src to dst.  Each thread
+// takes its butterflies one after the other (one butterfly's registers at a
+// time), and one block barrier ends the stage.  tw: this stage's table,
+// [r-1][k], k < NS.
+template <int N, int R, int NS>
+__device__ __forceinline__ void rstage(const float2* __restrict__ src, float2* __restrict__ dst, int npen,
+                                       const float2* __restrict__ tw) {
     constexpr int NB = N / R;
-    float2 v[B][R];
-    int dst[B];
+    const int total = npen * NB;
+#pragma unroll 1
+    for (int idx = threadIdx.x; idx < total; idx += RES_THREADS) {
+        const int pen = idx / NB;
+        const int j = idx - pen * NB;
+        const int k = j % NS;
+        const float2* sp = src + pen * N + j;
+        float2 v[R];
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-        const int idx = threadIdx.x + b * RES_THREADS;
-        dst[b] = -1;
-        if (idx < npen * NB) {
-            const int pen = idx / NB;
-            const int j = idx - pen * NB;
-            const int k = j % NS;
-            const float2* src = buf + pen * N + j;
+        for (int r = 0; r < R; ++r) v[r] = sp[r * NB];
+        if constexpr (NS > 1) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[b][r] = src[r * NB];
-            if constexpr (NS > 1) {
-#pragma unroll
-                for (int r = 1; r < R; ++r) v[b][r] = cmulw<INV>(v[b][r], tw[(r - 1) * NS + k]);
-            }
-            DftAny<R, INV, float2>::run(v[b]);
-            dst[b] = pen * N + (j - k) * R + k;
+            for (int r = 1; r < R; ++r) v[r] = cmulw<true>(v[r], tw[(r - 1) * NS + k]);
         }
-    }
-    __syncthreads();
+        DftAny<R, true, float2>::run(v);
+        float2* dp = dst + pen * N + (j - k) * R + k;
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-        if (dst[b] >= 0) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) buf[dst[b] + r * NS] = v[b][r];
-        }
+        for (int r = 0; r < R; ++r) dp[r * NS] = v[r];
     }
     __syncthreads();
 }
 
-template <int N, bool INV, int NS, int OFF, int... Rs> struct RStages;
-template <int N, bool INV, int NS, int OFF> struct RStages<N, INV, NS, OFF> {
+template <int N, int NS, int OFF, int... Rs> struct RStages;
+template <int N, int NS, int OFF> struct RStages<N, NS, OFF> {
     static constexpr int tw_size = OFF;
-    static constexpr int max_nb = 0;
-    __device__ __forceinline__ static void run(float2*, int, const float2*) {}
+    __device__ __forceinline__ static float2* run(float2* a, float2*, int, const float2*) { return a; }
     __device__ __forceinline__ static void build(float2*, const float2*) {}
 };
-template <int N, bool INV, int NS, int OFF, int R, int... Rs>
-struct RStages<N, INV, NS, OFF, R, Rs...> {
+template <int N, int NS, int OFF, int R, int... Rs>
+struct RStages<N, NS, OFF, R, Rs...> {
     static constexpr int here = NS > 1 ? (R - 1) * NS : 0;
-    typedef RStages<N, INV, NS * R, OFF + here, Rs...> Next;
+    typedef RStages<N, NS * R, OFF + here, Rs...> Next;
     static constexpr int tw_size = Next::tw_size;
-    static constexpr int max_nb = (N / R > Next::max_nb) ? N / R : Next::max_nb;
-    __device__ __forceinline__ static void run(float2* buf, int npen, const float2* tws) {
-        rstage<N, R, NS, INV, ResPlan<N>::B>(buf, npen, tws + OFF);
-        Next::run(buf, npen, tws);
+    // stages alternate between the two buffers; returns the one with the result
+    __device__ __forceinline__ static float2* run(float2* a, float2* b, int npen, const float2* tws) {
+        rstage<N, R, NS>(a, b, npen, tws + OFF);
+        return Next::run(b, a, npen, tws);
     }
     // tws[OFF + (r-1) NS + k] = W_N^{r k N / (NS R)}
     __device__ __forceinline__ static void build(float2* tws, const float2* __restrict__ tw_nat) {
@@ -122,28 +113,28 @@ struct RStages<N, INV, NS, OFF, R, Rs...> {
         Next::build(tws, tw_nat);
     }
 };
-template <int N, bool INV, typename L> struct RRun;
-template <int N, bool INV, int... Rs> struct RRun<N, INV, RadixList<Rs...>> {
-    typedef RStages<N, INV, 1, 0, Rs...> S;
+template <int N, typename L> struct RRun;
+template <int N, int... Rs> struct RRun<N, RadixList<Rs...>> {
+    typedef RStages<N, 1, 0, Rs...> S;
 };
 template <int N> struct ResTw {
-    typedef typename RRun<N, false, typename ResPlan<N>::type>::S S;
+    typedef typename RRun<N, typename ResPlan<N>::type>::S S;
     static constexpr int size = S::tw_size;
-    static constexpr int group = ResPlan<N>::B * RES_THREADS / S::max_nb;   // pencils per stage call
 };
 
-// Transform of npen contiguous pencils (npen the same in every thread), in
-// balanced groups of at most ResTw<N>::group pencils.  The caller has
+// Inverse (unnormalised) DFT of npen contiguous pencils (npen the same in
+// every thread) held in buf; alt is the second buffer of the out-of-place
+// stages.  Returns the buffer holding the result (buf or alt).  The caller has
 // synchronised the block after writing buf.  Not inlined: the solver's state
 // is saved once around the call instead of spilling inside the butterflies.
-template <int N, bool INV>
-__device__ __noinline__ void rfft(float2* buf, int npen, const float2* tws) {
-    typedef typename RRun<N, INV, typename ResPlan<N>::type>::S S;
-    constexpr int G = ResTw<N>::group;
-    if (npen <= 0) return;
-    const int ng = (npen + G - 1) / G;
-    const int gs = (npen + ng - 1) / ng;
-    for (int p0 = 0; p0 < npen; p0 += gs) S::run(buf + p0 * N, min(gs, npen - p0), tws);
+// The forward DFT is taken as conj(IDFT(conj x)) (conjugation is exact), with
+// the conjugations folded into the loops that fill and read the buffers: one
+// transform instantiation keeps the kernel's register allocation free of
+// spills, where separate forward and inverse ones did not.
+template <int N>
+__device__ __noinline__ float2* rifft(float2* buf, float2* alt, int npen, const float2* tws) {
+    if (npen <= 0) return buf;
+    return ResTw<N>::S::run(buf, alt, npen, tws);
 }
 
 // ---------------------------------------------------------------------------
@@ -282,35 +273,47 @@ __device__ __forceinline__ bool team_wait(unsigned* bar, unsigned target, int* e
 }
 
 // Sum over the team of the two slots of partial array `arr` (pair-packed FP32
-// sums), in one fixed order in every CTA: lane i adds CTAs i, i + 32, ...
-// (all loads issued first), then a fixed shuffle tree.  out[0..1] (shared),
-// valid after a block barrier.  T <= 32 * RES_SUM_PER_LANE.
+// sums hi + lo), in one fixed order in every CTA: lane i adds CTAs i, i + 32,
+// ... (all loads issued first), then a fixed shuffle tree.  The additions are
+// float-float (Knuth's TwoSum in FP32, the rounding error carried in a second
+// float), so the sum keeps about 48 bits where a plain FP32 sum keeps 24, with
+// no FP64 instruction until the one conversion at the end.  out[0..1]
+// (shared), valid after a block barrier.  T <= 32 * RES_SUM_PER_LANE.
 constexpr int RES_SUM_PER_LANE = 8;
+__device__ __forceinline__ void ff_add(float& s, float& e, float hi, float lo) {
+    const float t = s + hi;                  // TwoSum(s, hi)
+    const float bb = t - s;
+    const float err = (s - (t - bb)) + (hi - bb);
+    s = t;
+    e += err + lo;
+}
 __device__ __forceinline__ void team_sums(const double* part, int arr, int T, double* out) {
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
-        double w0[RES_SUM_PER_LANE], w1[RES_SUM_PER_LANE];
+        long long w0[RES_SUM_PER_LANE], w1[RES_SUM_PER_LANE];
 #pragma unroll
         for (int i = 0; i < RES_SUM_PER_LANE; ++i) {
             const int c = lane + 32 * i;
-            const double* pc = part + ((size_t)arr * T + c) * MAXL;
-            w0[i] = c < T ? __ldcg(pc) : 0.0;
-            w1[i] = c < T ? __ldcg(pc + 1) : 0.0;
+            const long long* pc = reinterpret_cast<const long long*>(part + ((size_t)arr * T + c) * MAXL);
+            w0[i] = c < T ? __ldcg(pc) : 0ll;
+            w1[i] = c < T ? __ldcg(pc + 1) : 0ll;
         }
-        double v0 = 0.0, v1 = 0.0;
+        float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f;
 #pragma unroll
         for (int i = 0; i < RES_SUM_PER_LANE; ++i) {
-            v0 += unpack_pair(w0[i]);
-            v1 += unpack_pair(w1[i]);
+            ff_add(s0, e0, __int_as_float((int)(w0[i] & 0xffffffffll)), __int_as_float((int)(w0[i] >> 32)));
+            ff_add(s1, e1, __int_as_float((int)(w1[i] & 0xffffffffll)), __int_as_float((int)(w1[i] >> 32)));
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            v0 += __shfl_down_sync(0xffffffffu, v0, off);
-            v1 += __shfl_down_sync(0xffffffffu, v1, off);
+            const float a0 = __shfl_down_sync(0xffffffffu, s0, off), b0 = __shfl_down_sync(0xffffffffu, e0, off);
+            const float a1 = __shfl_down_sync(0xffffffffu, s1, off), b1 = __shfl_down_sync(0xffffffffu, e1, off);
+            ff_add(s0, e0, a0, b0);
+            ff_add(s1, e1, a1, b1);
         }
         if (lane == 0) {
-            out[0] = v0;
-            out[1] = v1;
+            out[0] = (double)s0 + (double)e0;
+            out[1] = (double)s1 + (double)e1;
         }
     }
 }
@@ -356,7 +359,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* stage = reinterpret_cast<C*>(smem_raw);                  // [umax][2][HP] spectrum rows (bulk copies)
     C* buf = stage + (size_t)a.umax * 2 * HP;                   // [bufp][N] transforms
-    C* tws = buf + (size_t)a.bufp * N;                          // stage twiddles
+    C* buf2 = buf + (size_t)a.bufp * N;                         // [bufp][N] their second buffer
+    C* tws = buf2 + (size_t)a.bufp * N;                         // stage twiddles
     unsigned char* ph_s = reinterpret_cast<unsigned char*>(tws + ResTw<N>::size);   // [umax][N]
 
     __shared__ float s_tab[SMEM_PHASES * 4];
@@ -464,22 +468,23 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                         const float q = p0 * t.x + p1 * t.y;
                         if (l == 0) acc[0] += q; else acc[1] += q;
                     }
-                    buf[e] = t;
+                    buf[e] = make_float2(t.x, -t.y);        // conj(t0 + i t1)
                 }
                 tm_st16(tbase + 4 * s0, rp);
             }
             tm_wait_st();
             __syncthreads();
-            rfft<N, false>(buf, nu, tws);
-            // Z = t0 + i t1:  T0(k) = (Z(k) + conj Z(-k)) / 2,  T1(k) = (Z(k) - conj Z(-k)) / 2i
+            const C* yb = rifft<N>(buf, buf2, nu, tws);     // conj(DFT(t0 + i t1))
+            // Z = t0 + i t1:  T0(k) = (Z(k) + conj Z(-k)) / 2,  T1(k) = (Z(k) - conj Z(-k)) / 2i,
+            // with Z(k) = conj yb[k]
             for (int e = tid; e < nu * H; e += RES_THREADS) {
                 const int j = e / H, k = e - j * H;
                 const int u = u0 + j, m = u >> 1, l = u & 1;
                 if (!s_act[l]) continue;
-                const C z = buf[j * N + k], zm = buf[j * N + (k ? N - k : 0)];
+                const C y = yb[j * N + k], ym = yb[j * N + (k ? N - k : 0)];
                 C A, B;
-                A.x = 0.5f * (z.x + zm.x); A.y = 0.5f * (z.y - zm.y);
-                B.x = 0.5f * (z.y + zm.y); B.y = 0.5f * (zm.x - z.x);
+                A.x = 0.5f * (y.x + ym.x); A.y = 0.5f * (ym.y - y.y);
+                B.x = -0.5f * (y.y + ym.y); B.y = 0.5f * (ym.x - y.x);
                 const size_t o = ((size_t)(l * 2) * N + m) * HP + k;
                 a.S[o] = A;
                 a.S[o + (size_t)N * HP] = B;
@@ -515,7 +520,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                 }
 #pragma unroll
                 for (int q = 0; q < KB; ++q)
-                    if (dst[q] >= 0) buf[dst[q]] = val[q];
+                    if (dst[q] >= 0) buf[dst[q]] = make_float2(val[q].x, -val[q].y);   // conjugated
             }
             // alpha = (r, r) / (p, A p) (Moulinec-Suquet: 1 / lambda), from the
             // team's partial sums: their loads overlap the column loads above
@@ -524,7 +529,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
             if (tid == 0 || tid == 32) {
                 const int l = tid >> 5;
                 if (s_act[l]) {
-                    Scalars& s = s_sc[l];
+                    Scalars s = s_sc[l];
                     const double val = s_red[l] * invMd;
                     s.pt = val;
                     if (s.fixed_alpha > 0.0 && s.rr == 0.0) {
@@ -539,17 +544,18 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                     s.alpha_f = (float)s.alpha;
                     s_alpha[l] = s.alpha_f;
                     s_act[l] = s.status == ST_ACTIVE;
+                    s_sc[l] = s;
                 }
             }
-            rfft<N, false>(buf, 2 * nv, tws);
+            C* th = rifft<N>(buf, buf2, 2 * nv, tws);       // conj(t_hat)
             // q_hat = xi (xi . t_hat) / (xi . A0 xi) / |N|   (dual: onto J_N)
             for (int e = tid; e < nv * N; e += RES_THREADS) {
                 const int j = e / N, mr = e - j * N;
                 const int v = v0 + j, l = v / H, k = v - l * H;
                 if (!s_act[l]) continue;
-                C* b0 = buf + (j * 2) * N + mr;
+                C* b0 = th + (j * 2) * N + mr;
                 C* b1 = b0 + N;
-                const C th0 = *b0, th1 = *b1;
+                const C th0 = make_float2(b0->x, -b0->y), th1 = make_float2(b1->x, -b1->y);
                 const int fm = 2 * mr <= N - 1 ? mr : mr - N;
                 const float xi0 = (float)fm * invY0, xi1 = (float)k * invY1;
                 float den;
@@ -575,12 +581,12 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                 }
             }
             __syncthreads();
-            rfft<N, true>(buf, 2 * nv, tws);
+            const C* qb = rifft<N>(th, th == buf ? buf2 : buf, 2 * nv, tws);
             for (int idx = tid; idx < ntot; idx += RES_THREADS) {
                 const int j = idx % nv, t2 = idx / nv;
                 const int cc = t2 & 1, m = t2 >> 1;
                 const int v = v0 + j, l = v / H, k = v - l * H;
-                if (s_act[l]) a.S[((size_t)(l * 2 + cc) * N + m) * HP + k] = buf[(j * 2 + cc) * N + m];
+                if (s_act[l]) a.S[((size_t)(l * 2 + cc) * N + m) * HP + k] = qb[(j * 2 + cc) * N + m];
             }
         }
         team_arrive(a.bar);
@@ -621,7 +627,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                 buf[e] = make_float2(w0.x - w1.y, w0.y + w1.x);
             }
             __syncthreads();
-            rfft<N, true>(buf, nu, tws);
+            const C* qr = rifft<N>(buf, buf2, nu, tws);
             float acc[MAXL] = {0.f, 0.f, 0.f};
             const bool wgt = a.W.has != 0;
             const float w00 = a.W.wf[0], w01 = a.W.wf[1], w10 = a.W.wf[2], w11 = a.W.wf[3];
@@ -640,7 +646,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                     const int l = (u0 + j) & 1;
                     if (!(l == 0 ? act0 : act1)) continue;
                     const float al = l == 0 ? al0 : al1;
-                    const C q = buf[e];
+                    const C q = qr[e];
                     xx[2 * i] += al * rp[4 * i + 2];
                     xx[2 * i + 1] += al * rp[4 * i + 3];
                     const float rn0 = rp[4 * i] - al * q.x;
@@ -675,7 +681,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
         if (tid == 0 || tid == 32) {
             const int l = tid >> 5;
             if (s_act[l]) {
-                Scalars& s = s_sc[l];
+                Scalars s = s_sc[l];
                 const double rr = s_red[l] * invMd;
                 s.iters += 1;
                 s.total_iters += 1;
@@ -697,6 +703,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                 s.beta = s.fixed_alpha > 0.0 ? 0.0 : rr * rcp_d(s.rr);
                 s.beta_f = (float)s.beta;
                 s.rr = rr;
+                s_sc[l] = s;
             }
         }
         __syncthreads();
@@ -767,7 +774,7 @@ bool resident_cfg(int n, int L, int T, int nsm, int max_smem, ResCfg& cfg) {
     if ((umax * n + RES_THREADS - 1) / RES_THREADS > RES_SLOTS) return false;
     const int bufp = std::max(umax, 2 * vmax);
     size_t smem = (size_t)umax * 2 * HP * sizeof(float2)      // spectrum rows (bulk copies)
-                  + (size_t)bufp * n * sizeof(float2)         // transform buffer
+                  + (size_t)2 * bufp * n * sizeof(float2)     // transform buffers
                   + (size_t)res_tw_size(n) * sizeof(float2)   // stage twiddles
                   + (size_t)umax * n;                         // phase bytes
     smem = (smem + 15) & ~(size_t)15;

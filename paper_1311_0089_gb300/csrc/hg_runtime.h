@@ -14,6 +14,7 @@
 #include <set>
 #include <thread>
 #include <unordered_map>
+#include <vector>
 
 namespace hgrt {
 struct Scheduler;
@@ -133,6 +134,7 @@ bool choose_row_cfg(int prec, int n, int d, int L, int minR, size_t csize, int m
 bool choose_str_cfg(int prec, int n, int d, int minR, size_t csize, int max_smem,
                     long long inner, long long outer, int L, hgk::StrCfg& cfg);
 int grid_alloc_work(hg_grid* g, int prec);
+size_t solve_bytes_needed(const hg_grid* g, int prec, long long nbx = 0);
 int grid_alloc_common(hg_grid* g);
 hgk::CoeffsDev coeffs_for(const hg_grid* g, int prec, bool withA);
 int enqueue_forward_strided(hg_grid* g, int prec, int L, int check_status, int gamma_mode,
@@ -200,6 +202,32 @@ int enqueue_timing_pass(hg_grid* g, int pr, int pass, char* nm, cudaStream_t s);
 // Reduction slots for row passes of nbx CTAs per load (reallocated when the
 // current buffer is smaller; the caller holds ctx->mu with no work in flight).
 int grid_ensure_partial(hg_grid* g, long long nbx);
+
+// Rolling batch (hg_batch.cpp): the scheduler's cross-request batching.
+// Requests of one precision step together, check_every CG iterations per
+// tick, one batched launch per pass and grid shape for all of them; members
+// join and leave between ticks.
+struct Rolling;
+struct RollDone {
+    uint64_t tag;
+    int status;
+    hg_result res;
+};
+Rolling* rolling_create(hg_ctx* ctx, int prec, int chunk);
+void rolling_destroy(Rolling* R);
+int rolling_chunk(const Rolling* R);
+int rolling_size(const Rolling* R);
+// Row-pass CTAs of the shape's batched launches (reduction slots a member needs).
+long long rolling_nbx(Rolling* R, const hg_grid* g);
+// Admits g (standard CG, primal, A0 = I, R's precision): allocates its solver
+// state and enqueues its right-hand side.  HG_ERR_NO_MEMORY leaves nothing
+// allocated beyond what the grid already held.
+int rolling_add(Rolling* R, hg_grid* g, const hg_solve_opts& o, uint64_t tag);
+// One tick: check_every iterations of every member, then refinement steps
+// and the results of the members that have finished (appended to *done).
+int rolling_tick(Rolling* R, std::vector<RollDone>* done);
+// Drops a member (cancellation); waits for the batch's stream first.
+void rolling_remove(Rolling* R, uint64_t tag);
 
 // scheduler (hg_sched.cpp)
 Scheduler* sched_create(hg_ctx* ctx);

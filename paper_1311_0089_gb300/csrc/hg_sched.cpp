@@ -1,14 +1,17 @@
 // Request scheduler behind hg_submit / hg_poll / hg_cancel.
 //
-// Continuous batching at the granularity of one CG chunk (a CUDA graph of
-// `check_every` iterations): every admitted request keeps its CG state
-// resident on the device and runs its chunks on its own stream, so the
-// iterations of all admitted requests are in flight on the GPU together.
-// Requests that arrive while others run are admitted as soon as a slot and
-// device memory (within the context budget) are free; a finished request
-// releases its memory at once.  The worker thread never blocks on the GPU: it
-// polls each request's tick event and advances the requests whose last
-// chunk has completed.
+// Continuous batching across requests.  Requests for the standard CG on
+// Eq. final_system (primal, A0 = I) join the rolling batch of their precision
+// (hg_batch.cpp): every tick steps ALL of them by check_every iterations, with
+// one batched launch per pass and grid shape for every request of that shape,
+// and their FP64 refinement steps batched per shape; new requests join and
+// finished ones leave between ticks.  Other requests (Moulinec-Suquet, the
+// dual formulation, a general reference medium) run as resumable per-request
+// jobs on their own streams, overlapping the batch on the device.  Every
+// admitted request keeps its CG state resident on the device.  Admission
+// compares the bytes a request still has to allocate with the context budget
+// before allocating anything; a request that does not fit waits (in arrival
+// order) until a completed request has released memory.
 #include "hg.h"
 #include "hg_internal.h"
 #include "hg_runtime.h"
@@ -41,6 +44,7 @@ struct Ticket {
     int state = T_QUEUED;
     std::atomic<bool> cancel_req{false};
     Job job;
+    bool rolling = false;     // a member of a rolling batch (else a per-request job)
     hg_result res{};
     int status = HG_OK;
 };
@@ -58,14 +62,22 @@ struct Scheduler {
     uint64_t next_id = 1;
     bool stop = false;
     bool started = false;
-    int max_running = 64;
+    int max_running = 64;       // per-request jobs in flight
+    int max_rolling = 1024;     // members of the rolling batches
+    Rolling* roll[2] = {nullptr, nullptr};   // per precision (0 FP64, 1 mixed)
+    std::atomic<bool> mem_released{true};    // a completion freed memory since the last blocked admission
 };
+
+static bool rolling_eligible(const hg_solve_opts& o) {
+    return o.method == HG_CG && o.formulation == HG_PRIMAL && o.A0[0] == 0.0 && o.time_pass < 0;
+}
 
 static void complete(Scheduler* S, Ticket* t, int status) {
     // the ticket's work is finished or abandoned: make sure nothing is in flight.
     // Its device buffers stay allocated (reused by the next request on this
     // grid; reclaimed by admission when the budget is short).
     if (t->job.s) cudaStreamSynchronize(t->job.s);
+    S->mem_released = true;
     std::lock_guard<std::mutex> lk(S->m);
     t->status = status;
     t->res.status = status;
@@ -73,6 +85,23 @@ static void complete(Scheduler* S, Ticket* t, int status) {
     t->g->borrowed -= 1;
     S->running.erase(std::remove(S->running.begin(), S->running.end(), t), S->running.end());
     S->cv_done.notify_all();
+}
+
+// Whether a request fits the budget now.  When it does not and some memory
+// has been released since the last blocked admission, the solver state of
+// idle grids (no ticket) is released and the test repeated.
+static bool fits_budget(Scheduler* S, hg_grid* g, size_t need) {
+    hg_ctx* c = S->ctx;
+    if (!c->budget || c->used.load() + need <= c->budget) return true;
+    if (!S->mem_released.exchange(false)) return false;
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    ctx_reclaim(c, g);
+    return c->used.load() + need <= c->budget;
+}
+
+static bool nothing_running(Scheduler* S) {
+    std::lock_guard<std::mutex> lk(S->m);
+    return S->running.empty();
 }
 
 static void worker(Scheduler* S) {
@@ -86,57 +115,73 @@ static void worker(Scheduler* S) {
                 S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
                 if (S->stop) break;
             }
-            while (!S->queue.empty() && (int)(S->running.size() + admit.size()) < S->max_running) {
-                admit.push_back(S->queue.front());
+            int jobs = 0, members = 0;
+            for (Ticket* t : S->running) (t->rolling ? members : jobs) += 1;
+            while (!S->queue.empty()) {
+                Ticket* t = S->queue.front();
+                const bool roll = rolling_eligible(t->job.o);
+                if (roll ? members >= S->max_rolling : jobs >= S->max_running) break;
+                (roll ? members : jobs) += 1;
+                admit.push_back(t);
                 S->queue.pop_front();
             }
         }
-        // admission: allocate the request's resident state, enqueue its first steps
+        // admission: the request's resident state, then its first steps
         for (size_t i = 0; i < admit.size(); ++i) {
             Ticket* t = admit[i];
             if (t->cancel_req) { complete(S, t, HG_ERR_CANCELLED); continue; }
-            int st;
+            const hg_solve_opts& o = t->job.o;
+            const int prec = o.prec == HG_MIXED ? 1 : 0;
+            Rolling* R = nullptr;
+            if (rolling_eligible(o)) {
+                if (!S->roll[prec]) S->roll[prec] = rolling_create(S->ctx, prec, o.check_every);
+                R = S->roll[prec];
+                if (R && rolling_chunk(R) != std::max(1, o.check_every)) R = nullptr;   // its own job
+            }
+            size_t need;
             {
                 std::lock_guard<std::recursive_mutex> lk(S->ctx->mu);
-                t->job.g = t->g;
-                t->job.s = S->streams[S->next_stream++ % S->streams.size()];
-                t->job.ev0 = t->g->ev0;
-                t->job.ev1 = t->g->ev1;
-                t->job.tick = t->g->ev_tick;
-                st = job_begin(t->job);
+                need = solve_bytes_needed(t->g, prec, R ? rolling_nbx(R, t->g) : 0);
+            }
+            int st = HG_ERR_NO_MEMORY;
+            if (fits_budget(S, t->g, need)) {
+                std::lock_guard<std::recursive_mutex> lk(S->ctx->mu);
+                if (R) {
+                    st = rolling_add(R, t->g, o, t->id);
+                } else {
+                    t->job.g = t->g;
+                    t->job.s = S->streams[S->next_stream++ % S->streams.size()];
+                    t->job.ev0 = t->g->ev0;
+                    t->job.ev1 = t->g->ev1;
+                    t->job.tick = t->g->ev_tick;
+                    st = job_begin(t->job);
+                }
                 if (st == HG_ERR_NO_MEMORY) {
-                    // over the budget: release idle grids' solver state and retry once
-                    cudaStreamSynchronize(t->job.s);
+                    // the estimate missed (fragmentation, another context): drop
+                    // what this attempt allocated before waiting
+                    if (t->job.s) cudaStreamSynchronize(t->job.s);
+                    if (R) cudaDeviceSynchronize();
                     grid_free_work(t->g);
-                    if (ctx_reclaim(S->ctx, t->g) > 0) st = job_begin(t->job);
                 }
             }
             if (st == HG_ERR_NO_MEMORY) {
-                bool none_running;
-                {
-                    std::lock_guard<std::mutex> lk(S->m);
-                    none_running = S->running.empty();
-                }
-                cudaStreamSynchronize(t->job.s);
-                {
-                    std::lock_guard<std::recursive_mutex> lk(S->ctx->mu);
-                    grid_free_work(t->g);
-                }
-                if (none_running) {   // it can never fit
+                if (nothing_running(S)) {   // it can never fit
                     complete(S, t, HG_ERR_NO_MEMORY);
                     continue;
                 }
+                // wait for a completion to release memory: back to the front of
+                // the queue, with the rest of this admission round
                 std::lock_guard<std::mutex> lk(S->m);
-                // wait for memory: back to the front of the queue, with the rest
                 for (size_t k = admit.size(); k-- > i;) S->queue.push_front(admit[k]);
                 break;
             }
             if (st != HG_OK) { complete(S, t, st); continue; }
             std::lock_guard<std::mutex> lk(S->m);
+            t->rolling = R != nullptr;
             t->state = T_RUNNING;
             S->running.push_back(t);
         }
-        // progress every running request whose last step has completed
+        // per-request jobs whose last step has completed
         std::vector<Ticket*> snap;
         {
             std::lock_guard<std::mutex> lk(S->m);
@@ -144,6 +189,18 @@ static void worker(Scheduler* S) {
         }
         bool progressed = false;
         for (Ticket* t : snap) {
+            if (t->rolling) {
+                if (t->cancel_req) {
+                    {
+                        std::lock_guard<std::recursive_mutex> lk(S->ctx->mu);
+                        for (Rolling* R : S->roll)
+                            if (R) rolling_remove(R, t->id);
+                    }
+                    complete(S, t, HG_ERR_CANCELLED);
+                    progressed = true;
+                }
+                continue;
+            }
             if (t->cancel_req) { complete(S, t, HG_ERR_CANCELLED); progressed = true; continue; }
             cudaError_t q = cudaEventQuery(t->job.tick);
             if (q == cudaErrorNotReady) continue;
@@ -164,6 +221,41 @@ static void worker(Scheduler* S) {
                 t->res = t->job.res;
                 complete(S, t, t->job.result);
             }
+        }
+        // one tick of every rolling batch: all its members step together
+        for (int pr = 0; pr < 2; ++pr) {
+            Rolling* R = S->roll[pr];
+            if (!R || rolling_size(R) == 0) continue;
+            std::vector<RollDone> fin;
+            int st;
+            {
+                std::lock_guard<std::recursive_mutex> lk(S->ctx->mu);
+                st = rolling_tick(R, &fin);
+            }
+            progressed = true;
+            std::vector<Ticket*> members;
+            {
+                std::lock_guard<std::mutex> lk(S->m);
+                for (Ticket* t : S->running)
+                    if (t->rolling && t->job.o.prec == (pr ? HG_MIXED : HG_FP64)) members.push_back(t);
+            }
+            if (st != HG_OK) {
+                // the batch cannot go on: every member ends with the error
+                {
+                    std::lock_guard<std::recursive_mutex> lk(S->ctx->mu);
+                    rolling_destroy(R);
+                }
+                S->roll[pr] = nullptr;
+                for (Ticket* t : members) complete(S, t, st);
+                continue;
+            }
+            for (const RollDone& d : fin)
+                for (Ticket* t : members)
+                    if (t->id == d.tag) {
+                        t->res = d.res;
+                        complete(S, t, d.status);
+                        break;
+                    }
         }
         if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
@@ -197,6 +289,10 @@ void sched_destroy(Scheduler* S) {
     }
     S->cv_work.notify_all();
     if (S->th.joinable()) S->th.join();
+    for (Rolling*& R : S->roll) {
+        rolling_destroy(R);
+        R = nullptr;
+    }
     for (Ticket* t : S->running) {
         if (t->job.s) cudaStreamSynchronize(t->job.s);
         grid_free_work(t->g);

@@ -258,7 +258,9 @@ def test_submit_poll_matches_blocking(hg, ctx):
     out = [ctx.poll(t, timeout_us=-1) for t in tickets]
     for a, b in zip(out, blocking):
         assert a["status"] == 0
-        assert rel_max(a["AH"], b["AH"]) < 1e-12
+        # the scheduler batches requests with per-shape launch tiles: the same
+        # iteration up to the rounding of the partial sums
+        assert rel_max(a["AH"], b["AH"]) < 1e-10
     for g in grids:
         g.close()
 
@@ -303,7 +305,9 @@ def test_scheduler_admission_by_memory_budget(hg):
     out = [ctx.poll(t, timeout_us=-1) for t in ts]
     for k in range(2):
         assert out[k]["status"] == 0
-        np.testing.assert_allclose(out[k]["AH"], want[k], rtol=1e-12)
+        # blocking mixed solves of square grids run the resident kernel, the
+        # scheduler the batched pass kernels: equal to the method's tolerance
+        assert rel_max(out[k]["AH"], want[k]) < 1e-6
     big = ctx.grid((405, 405))
     big.set_coeffs_phase(np.zeros((405, 405), np.uint8), np.eye(2)[None])
     t = ctx.submit(big, hg.default_opts())
@@ -373,6 +377,29 @@ def test_full_size_135_cubed_sampled_and_properties(hg, ctx):
     reuss = np.linalg.inv((1 - f) * np.linalg.inv(ms.table[0]) + f * np.linalg.inv(ms.table[1]))
     assert np.min(np.linalg.eigvalsh(voigt - AH)) > -1e-8 * np.max(np.abs(AH))
     assert np.min(np.linalg.eigvalsh(AH - reuss)) > -1e-8 * np.max(np.abs(AH))
+    g.close()
+
+
+def test_full_size_135_cubed_against_oracle_golden(hg, ctx):
+    """The 135^3 workload (60 spheres, two random SPD phases, contrast 1000)
+    against the oracle's A_H at tol 1e-12 (tests/golden/spheres_135_AH.json,
+    written by make_golden.py --large3d): every entry of the FP64 path at tol
+    1e-10 within 1e-8 and of the mixed path at bench.py's settings (tol 1e-5)
+    within 1e-6, both relative to max |A_H| (Sec. 5.2 Eq. final_system)."""
+    gold = json.load(open(os.path.join(HERE, "golden", "spheres_135_AH.json")))
+    ref = np.array(gold["AH"])
+    ms = W.spheres_3d()
+    assert list(ms.N) == gold["N"] and abs(ms.meta["vf"] - gold["vf"]) < 1e-12
+    g = ctx.grid(ms.N)
+    g.set_coeffs_phase(ms.phase, ms.table)
+    g.tune(hg.HG_MIXED, reps=4)    # the launch geometry bench.py runs
+    fp64 = g.solve(hg.default_opts(tol=1e-10, prec=hg.HG_FP64))
+    mixed = g.solve(hg.default_opts(tol=1e-5, prec=hg.HG_MIXED, inner_tol=5e-6))
+    assert fp64["status"] == 0 and mixed["status"] == 0
+    assert rel_max(fp64["AH"], ref) < 1e-8
+    assert rel_max(mixed["AH"], ref) < 1e-6
+    # the oracle's iteration counts at tol 1e-12 bound the FP64 path's at 1e-10
+    assert all(a <= b + 2 for a, b in zip(fp64["iters"], gold["iters"]))
     g.close()
 
 

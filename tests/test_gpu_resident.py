@@ -189,25 +189,35 @@ def test_resident_time_pass_times_the_launch(hg, ctx):
 
 @pytest.mark.parametrize("N,prec", [((15, 15), 0), ((45, 75), 0), ((15, 15), 1), ((45, 75), 1), ((81, 81), 1)])
 def test_true_residual_matches_oracle(hg, ctx, N, prec):
-    """hg_result.true_rel_res = ||b - G A x|| / ||b|| recomputed in FP64 at exit,
-    against the oracle's recomputed residual of its own iterate at the same
-    tolerance (Sec. 5.3 stopping rule reading)."""
+    """hg_result.true_rel_res = ||b - G A x|| / ||b|| recomputed in FP64 at exit
+    (the stopping rule of Sec. 5.3 is the paper's open point): it equals the
+    oracle's recomputation of that residual from the returned e~ (hg_get_field),
+    and for the FP64 path with the oracle's own iteration count also the
+    oracle's true residual of its own iterate."""
     rng = np.random.default_rng(N[0] * 7 + prec)
     ph = (rng.random(N) < 0.3).astype(np.uint8)
     table = W.isotropic_table([1.0, 20.0], 2)
     ms = W.Microstructure(N, ph, table)
+    A = ms.full_field()
     tol = 1e-7
-    ref = O.solve_AH(ms.full_field(), N, tol=tol)
+    ref = O.solve_AH(A, N, tol=tol)
     g = ctx.grid(N)
     g.set_coeffs_phase(ph, table)
     r = g.solve(hg.default_opts(tol=tol, prec=prec))
     assert r["status"] == 0
     for j in range(2):
-        assert 0.0 < r["true_rel_res"][j] <= 2 * tol
-        assert abs(r["true_rel_res"][j] - ref["true_rel_res"][j]) < 1e-8
+        E = np.zeros((2,) + (1,) * 2)
+        E[j] = 1.0
+        b = -O.apply_K(A, E * np.ones((2,) + N), N)
+        x = g.field(j)
+        res = b - O.apply_K(A, x, N)
+        want = np.sqrt(O.inner(res, res) / O.inner(b, b))
+        got = r["true_rel_res"][j]
+        assert 0.0 < got <= 2 * tol
+        assert abs(got - want) <= 1e-10 + 1e-3 * want
         if prec == 0 and r["iters"][j] == ref["iters"][j]:
-            # the same FP64 iterate up to rounding: the same residual to 0.1%
-            assert abs(r["true_rel_res"][j] - ref["true_rel_res"][j]) <= 1e-3 * ref["true_rel_res"][j]
+            # the same FP64 iterate up to rounding: the oracle's own residual
+            assert abs(got - ref["true_rel_res"][j]) <= 1e-3 * ref["true_rel_res"][j]
             # and the FP64 recursion has not drifted from it
-            assert abs(r["true_rel_res"][j] - r["rel_res"][j]) <= 1e-3 * r["rel_res"][j]
+            assert abs(got - r["rel_res"][j]) <= 1e-3 * r["rel_res"][j]
     g.close()
