@@ -519,7 +519,7 @@ def run_ours(args):
     for p in range(npass):
         t_ms, name = g.time_pass(p, hg.HG_MIXED, reps=50 if d == 2 else 10)
         passes.append({"pass": p, "kernel": name, "ms_isolated": t_ms,
-                       "ms_in_solve": pass_avg[p], "bytes": pb[p]})
+                       "ms_in_solve": pass_avg[p] if pass_avg else None, "bytes": pb[p]})
     for p in range(npass):
         t_ms, name = g.time_pass(p, hg.HG_FP64, reps=10 if d == 2 else 3)
         passes64.append({"kernel": name, "ms_isolated": t_ms, "GBs": pb64[p] / (t_ms * 1e-3) / 1e9})

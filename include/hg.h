@@ -149,8 +149,9 @@ typedef struct {
                             runs its first grid's launch geometry, and every
                             problem's iterates equal those of its own
                             hg_solve_AH bitwise.                              */
-    int resident;        /* HG_MIXED on a square 2D grid of side 45, 75, 81,
-                            135, 243, 375 or 729: run each inner FP32 solve as
+    int resident;        /* HG_MIXED on a square 2D grid of side 15, 27, 45,
+                            75, 81, 135, 243, 375 or 729: run each inner FP32
+                            solve as
                             ONE cooperative launch whose CTAs (one per SM) keep
                             the residual and the search direction of their grid
                             rows in shared memory for all its iterations, with

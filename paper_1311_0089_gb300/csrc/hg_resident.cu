@@ -51,7 +51,9 @@ template <> struct ResPlan<135> { typedef RadixList<15, 9> type; };
 template <> struct ResPlan<81> { typedef RadixList<9, 9> type; };
 template <> struct ResPlan<75> { typedef RadixList<15, 5> type; };
 template <> struct ResPlan<45> { typedef RadixList<9, 5> type; };
-#define HG_RES_SIZES(X) X(729) X(375) X(243) X(135) X(81) X(75) X(45)
+template <> struct ResPlan<27> { typedef RadixList<9, 3> type; };
+template <> struct ResPlan<15> { typedef RadixList<15> type; };
+#define HG_RES_SIZES(X) X(729) X(375) X(243) X(135) X(81) X(75) X(45) X(27) X(15)
 
 // One inverse Stockham stage (the formulation of fft_device.cuh), out of
 // place: npen contiguous pencils of length N from src to dst.  Each thread

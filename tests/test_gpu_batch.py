@@ -4,7 +4,9 @@ shape, one CUDA graph for all shapes) against single solves and the oracle.
 A batched launch runs, for each problem, the same tile bodies with the same
 tile-to-CTA map and fixed-order reductions as that problem's own launch, so
 each problem's iterates, iteration counts and A_H equal its single solve
-bitwise.
+bitwise (single solves with the pass kernels, resident = 0: a mixed single
+solve of a square 2D grid otherwise runs the resident kernel, whose partial
+sums are grouped differently).
 """
 import numpy as np
 import pytest
@@ -41,7 +43,7 @@ def test_batch_equals_single_solves(hg, ctx, prec):
         g = ctx.grid(m.N)
         g.set_coeffs_phase(m.phase, m.table)
         grids.append(g)
-    o = hg.default_opts(tol=1e-7, prec=pr, max_iter=20000, batch_tiles=0)
+    o = hg.default_opts(tol=1e-7, prec=pr, max_iter=20000, batch_tiles=0, resident=0)
     batch = ctx.solve_batch(grids, o)
     fields = [g.field(1) for g in grids]
     for g, b, f in zip(grids, batch, fields):
@@ -87,7 +89,7 @@ def test_batch_with_a_homogeneous_problem_and_loads_mask(hg, ctx):
     h = ctx.grid(N)
     h.set_coeffs_phase(np.zeros(N, np.uint8), A0[None])
     grids.append(h)
-    o = hg.default_opts(tol=1e-8, prec=hg.HG_MIXED, batch_tiles=0)
+    o = hg.default_opts(tol=1e-8, prec=hg.HG_MIXED, batch_tiles=0, resident=0)
     res = ctx.solve_batch(grids, o)
     assert res[-1]["iters"] == [0, 0]
     np.testing.assert_allclose(res[-1]["AH"], A0, atol=1e-13)
@@ -126,7 +128,7 @@ def test_batch_of_mixed_shapes_equals_single_solves(hg, ctx, prec):
         else:
             g.set_coeffs_field(c[1])
         grids.append(g)
-    o = hg.default_opts(tol=1e-8, prec=pr, max_iter=20000, batch_tiles=0)
+    o = hg.default_opts(tol=1e-8, prec=pr, max_iter=20000, batch_tiles=0, resident=0)
     batch = ctx.solve_batch(grids, o)
     for g, b, (N, c) in zip(grids, batch, probs):
         assert b["status"] == 0 and b["AH"].shape == (len(N), len(N))
