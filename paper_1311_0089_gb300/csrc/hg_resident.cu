@@ -289,17 +289,26 @@ __device__ __forceinline__ void ff_add(float& s, float& e, float hi, float lo) {
     s = t;
     e += err + lo;
 }
-__device__ __forceinline__ void team_sums(const double* part, int arr, int T, double* out) {
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        long long w0[RES_SUM_PER_LANE], w1[RES_SUM_PER_LANE];
+// Split in two so that the loads can be issued early (team_load, warp 0) and
+// their latency overlap other work before the sums are needed (team_reduce).
+struct TeamPart {
+    long long w0[RES_SUM_PER_LANE], w1[RES_SUM_PER_LANE];
+};
+__device__ __forceinline__ void team_load(const double* part, int arr, int T, TeamPart& tp) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-        for (int i = 0; i < RES_SUM_PER_LANE; ++i) {
-            const int c = lane + 32 * i;
-            const long long* pc = reinterpret_cast<const long long*>(part + ((size_t)arr * T + c) * MAXL);
-            w0[i] = c < T ? __ldcg(pc) : 0ll;
-            w1[i] = c < T ? __ldcg(pc + 1) : 0ll;
-        }
+    for (int i = 0; i < RES_SUM_PER_LANE; ++i) {
+        const int c = lane + 32 * i;
+        const long long* pc = reinterpret_cast<const long long*>(part + ((size_t)arr * T + c) * MAXL);
+        tp.w0[i] = c < T ? __ldcg(pc) : 0ll;
+        tp.w1[i] = c < T ? __ldcg(pc + 1) : 0ll;
+    }
+}
+__device__ __forceinline__ void team_reduce(const TeamPart& tp, double* out) {
+    {
+        const int lane = threadIdx.x & 31;
+        const long long* w0 = tp.w0;
+        const long long* w1 = tp.w1;
         float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f;
 #pragma unroll
         for (int i = 0; i < RES_SUM_PER_LANE; ++i) {
@@ -317,6 +326,13 @@ __device__ __forceinline__ void team_sums(const double* part, int arr, int T, do
             out[0] = (double)s0 + (double)e0;
             out[1] = (double)s1 + (double)e1;
         }
+    }
+}
+__device__ __forceinline__ void team_sums(const double* part, int arr, int T, double* out) {
+    if (threadIdx.x < 32) {
+        TeamPart tp;
+        team_load(part, arr, T, tp);
+        team_reduce(tp, out);
     }
 }
 
@@ -503,6 +519,9 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
 
         // ---- phase B: column DFT, Gamma_hat, inverse column DFT ----
         {
+            // the team's (p, A p) partials: loaded now, summed after the column loads
+            TeamPart tp;
+            if (tid < 32) team_load(a.part, 0, T, tp);
             const int ntot = nv * 2 * N;
             for (int i0 = tid; i0 < ntot; i0 += KB * RES_THREADS) {
                 C val[KB];
@@ -525,8 +544,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                     if (dst[q] >= 0) buf[dst[q]] = make_float2(val[q].x, -val[q].y);   // conjugated
             }
             // alpha = (r, r) / (p, A p) (Moulinec-Suquet: 1 / lambda), from the
-            // team's partial sums: their loads overlap the column loads above
-            team_sums(a.part, 0, T, s_red);
+            // team's partial sums: their loads overlapped the column loads above
+            if (tid < 32) team_reduce(tp, s_red);
             __syncthreads();
             if (tid == 0 || tid == 32) {
                 const int l = tid >> 5;
