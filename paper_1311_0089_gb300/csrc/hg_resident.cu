@@ -1,28 +1,30 @@
 // Resident FP32 conjugate-gradient solver for square 2D grids (sm_103a).
 //
 // The inner FP32 solve of the mixed-precision path (CG on Eq. final_system,
-// Sec. 5.3 Lemma; the operator G_N A_N of Eq. FFT_matrices with Gamma_hat of
-// Eq. Gamma_hat) as ONE cooperative launch that runs every iteration.  A team
-// of CTAs, one per SM, splits the grid into row units (grid row m, load l):
-// each CTA keeps the residual r, the search direction p and the iterate x of
-// its row units in tensor memory (TMEM, 256 KB per SM, which this path does
-// not otherwise use) for the whole solve, so r, p and x never travel to HBM;
-// shared memory holds the transforms.  One iteration is three phases
-// separated by grid-wide barriers:
+// Sec. 5.3 Lemma; the operator K = G_N A_N of Eq. FFT_matrices with Gamma_hat
+// of Eq. Gamma_hat) as ONE cooperative launch that runs every iteration.  A
+// team of CTAs, one per SM, splits the grid into row units (grid row m, load
+// l): each CTA keeps r, p, x and s = K p of its row units in tensor memory
+// (TMEM, 256 KB per SM, which this path does not otherwise use) for the whole
+// solve, so they never travel to HBM; shared memory holds the transforms.
+// The iteration is CG in the form of Chronopoulos and Gear (the same iterates
+// in exact arithmetic, with w = K r computed in place of K p), so that both
+// dot products of an iteration come from one reduction and an iteration is
+// two phases of row work and one of column work separated by two grid-wide
+// barriers:
 //
-//   A  (rows)     p <- r + beta p;  t = A_N p (Sec. 5.1);  (p, t) partial sums;
+//   A  (rows)     t = A_N r (Sec. 5.1);  (r, r) and (A r, r) partial sums
+//                 ((K r, r) = (A r, r) for r in E_N, Lemma FD_projection);
 //                 forward DFT of t along the contiguous axis (the two
 //                 components packed as one complex row); half spectra -> S.
-//   B  (columns)  alpha = (r, r) / (p, A p) from the team's partial sums;
-//                 forward DFT along axis 0, q_hat = Gamma_hat t_hat / |N|,
-//                 inverse DFT along axis 0, for the CTA's column units.
+//   B  (columns)  the stopping tests on r and the step scalars beta, alpha
+//                 from the team's sums; forward DFT along axis 0,
+//                 q_hat = Gamma_hat t_hat / |N|, inverse DFT along axis 0, for
+//                 the CTA's column units.
 //   C  (rows)     the CTA's rows of S by bulk async copies (one mbarrier);
-//                 inverse DFT along the contiguous axis -> q = G_N A_N p;
-//                 x += alpha p;  r -= alpha q;  (r, r) partial sums;  beta and
-//                 the convergence test from the team's sums.
+//                 inverse DFT along the contiguous axis -> w = K r;
+//                 p = r + beta p, s = w + beta s, x += alpha p, r -= alpha s.
 //
-// As in the pass kernels, alpha uses (p, G A p) = (p, A p) (Lemma
-// FD_projection (iii),(v); Sec. 5.3), so q is consumed where it is made.
 // Every CTA sums the team's partial sums itself in one fixed order, so all
 // CTAs take the same decisions (step sizes, convergence) without another
 // exchange, and the result does not depend on timing.
@@ -142,13 +144,15 @@ __device__ __noinline__ float2* rifft(float2* buf, float2* alt, int npen, const 
 // ---------------------------------------------------------------------------
 // tensor memory (TMEM) as per-thread storage, bulk async copies, mbarriers
 // ---------------------------------------------------------------------------
-// r, p and x of a thread's voxels live in TMEM (256 KB per SM, otherwise
-// unused on this path): warp w reaches TMEM lanes 32 (w mod 4) .. + 31, and
-// warps w, w + 4, w + 8, w + 12 use disjoint column groups of 128.  Slot s of
-// a thread (voxel e = tid + 512 s of its CTA) keeps (r0, r1, p0, p1) in
-// columns 4 s .. 4 s + 3 and (x0, x1) in columns 80 + 2 s, 80 + 2 s + 1.
-constexpr int RES_SLOTS = 20;                 // slots per thread (multiple of 4)
+// r, p, x and s = K p of a thread's voxels live in TMEM (256 KB per SM,
+// otherwise unused on this path): warp w reaches TMEM lanes 32 (w mod 4) ..
+// + 31, and warps w, w + 4, w + 8, w + 12 use disjoint column groups of 128.
+// Slot s of a thread (voxel e = tid + 512 s of its CTA) keeps (r0, r1, p0, p1)
+// in columns 4 s .. 4 s + 3, (x0, x1) in columns 64 + 2 s, 64 + 2 s + 1 and
+// (s0, s1) in columns 96 + 2 s, 96 + 2 s + 1.
+constexpr int RES_SLOTS = 16;                 // slots per thread (multiple of 4)
 constexpr int RES_XCOL = 4 * RES_SLOTS;       // first x column of a group
+constexpr int RES_SCOL = RES_XCOL + 2 * RES_SLOTS;   // first s column of a group
 constexpr int RES_TMEM_COLS = 512;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -289,51 +293,32 @@ __device__ __forceinline__ void ff_add(float& s, float& e, float hi, float lo) {
     s = t;
     e += err + lo;
 }
-// Split in two so that the loads can be issued early (team_load, warp 0) and
-// their latency overlap other work before the sums are needed (team_reduce).
+// Split in two so that the loads can be issued early (team_load) and their
+// latency overlap other work before the sums are needed (team_reduce).  Warp k
+// (k < 4) sums slot k of the CTAs' partials.
 struct TeamPart {
-    long long w0[RES_SUM_PER_LANE], w1[RES_SUM_PER_LANE];
+    long long w[RES_SUM_PER_LANE];
 };
-__device__ __forceinline__ void team_load(const double* part, int arr, int T, TeamPart& tp) {
+__device__ __forceinline__ void team_load(const double* part, int k, int T, TeamPart& tp) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int i = 0; i < RES_SUM_PER_LANE; ++i) {
         const int c = lane + 32 * i;
-        const long long* pc = reinterpret_cast<const long long*>(part + ((size_t)arr * T + c) * MAXL);
-        tp.w0[i] = c < T ? __ldcg(pc) : 0ll;
-        tp.w1[i] = c < T ? __ldcg(pc + 1) : 0ll;
+        tp.w[i] = c < T ? __ldcg(reinterpret_cast<const long long*>(part + (size_t)c * 4 + k)) : 0ll;
     }
 }
 __device__ __forceinline__ void team_reduce(const TeamPart& tp, double* out) {
-    {
-        const int lane = threadIdx.x & 31;
-        const long long* w0 = tp.w0;
-        const long long* w1 = tp.w1;
-        float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f;
+    const int lane = threadIdx.x & 31;
+    float s0 = 0.f, e0 = 0.f;
 #pragma unroll
-        for (int i = 0; i < RES_SUM_PER_LANE; ++i) {
-            ff_add(s0, e0, __int_as_float((int)(w0[i] & 0xffffffffll)), __int_as_float((int)(w0[i] >> 32)));
-            ff_add(s1, e1, __int_as_float((int)(w1[i] & 0xffffffffll)), __int_as_float((int)(w1[i] >> 32)));
-        }
+    for (int i = 0; i < RES_SUM_PER_LANE; ++i)
+        ff_add(s0, e0, __int_as_float((int)(tp.w[i] & 0xffffffffll)), __int_as_float((int)(tp.w[i] >> 32)));
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float a0 = __shfl_down_sync(0xffffffffu, s0, off), b0 = __shfl_down_sync(0xffffffffu, e0, off);
-            const float a1 = __shfl_down_sync(0xffffffffu, s1, off), b1 = __shfl_down_sync(0xffffffffu, e1, off);
-            ff_add(s0, e0, a0, b0);
-            ff_add(s1, e1, a1, b1);
-        }
-        if (lane == 0) {
-            out[0] = (double)s0 + (double)e0;
-            out[1] = (double)s1 + (double)e1;
-        }
+    for (int off = 16; off > 0; off >>= 1) {
+        const float a0 = __shfl_down_sync(0xffffffffu, s0, off), b0 = __shfl_down_sync(0xffffffffu, e0, off);
+        ff_add(s0, e0, a0, b0);
     }
-}
-__device__ __forceinline__ void team_sums(const double* part, int arr, int T, double* out) {
-    if (threadIdx.x < 32) {
-        TeamPart tp;
-        team_load(part, arr, T, tp);
-        team_reduce(tp, out);
-    }
+    if (lane == 0) *out = (double)s0 + (double)e0;
 }
 
 // FP64 1/x and sqrt(x) by Newton-Raphson from FP32 seeds (two steps each:
@@ -385,13 +370,13 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
     __shared__ Scalars s_sc[L];
     __shared__ float s_alpha[L], s_beta[L];
     __shared__ int s_act[L];
-    __shared__ double s_red[L];
+    __shared__ double s_red[4];
     __shared__ uint32_t s_taddr;
     __shared__ __align__(8) uint64_t s_mbar;
 
     if (a.drop_cta == c) return;
 
-    // ---- set-up: TMEM, twiddles, coefficients, r = r0, p = 0, x = 0 ----
+    // ---- set-up: TMEM, twiddles, coefficients, r = r0, p = s = x = 0 ----
     const int warp = tid >> 5;
     if (warp == 0) tm_alloc(&s_taddr, RES_TMEM_COLS);
     if (tid == 0) mbar_init(&s_mbar, 1);
@@ -416,7 +401,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
     // this thread's TMEM: lane quarter of its warp, column group of its warp quarter
     const uint32_t tbase = s_taddr + ((uint32_t)(32 * (warp & 3)) << 16) + 128u * (uint32_t)(warp >> 2);
     for (int s0 = 0; s0 < nslot; s0 += 4) {
-        float rp[16], xx[8];
+        float rp[16], zz[8];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int e = tid + (s0 + i) * RES_THREADS;
@@ -429,10 +414,11 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                 r1 = a.r0[o + M];
             }
             rp[4 * i] = r0; rp[4 * i + 1] = r1; rp[4 * i + 2] = 0.f; rp[4 * i + 3] = 0.f;
-            xx[2 * i] = 0.f; xx[2 * i + 1] = 0.f;
+            zz[2 * i] = 0.f; zz[2 * i + 1] = 0.f;
         }
         tm_st16(tbase + 4 * s0, rp);
-        tm_st8(tbase + RES_XCOL + 2 * s0, xx);
+        tm_st8(tbase + RES_XCOL + 2 * s0, zz);
+        tm_st8(tbase + RES_SCOL + 2 * s0, zz);
     }
     tm_wait_st();
 
@@ -443,19 +429,24 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
     unsigned seq = 0, mphase = 0;
     bool ok = true;
 
+    // CG in the form of Chronopoulos and Gear (the iterates of Sec. 5.3's CG in
+    // exact arithmetic, with w = K r in place of q = K p): both dot products of
+    // an iteration, gamma = (r, r) and delta = (K r, r) = (A r, r) (r in E_N,
+    // Lemma FD_projection), come from the same reduction, so beta = gamma /
+    // gamma_old and alpha = gamma / (delta - beta gamma / alpha_old) are known
+    // before the last phase, which updates p = r + beta p, s = w + beta s
+    // (s = K p), x += alpha p, r -= alpha s: two grid barriers per iteration.
     for (;;) {
-        if (tid < L) {
-            s_act[tid] = s_sc[tid].status == ST_ACTIVE;
-            s_beta[tid] = s_sc[tid].beta_f;
-        }
+        if (tid < L) s_act[tid] = s_sc[tid].status == ST_ACTIVE;
         __syncthreads();
         if (!(s_act[0] | s_act[1])) break;
 
-        // ---- phase A: p = r + beta p, t = A p, (p, t), row DFT -> S ----
+        // ---- phase A: t = A r; (r, r), (A r, r); row DFT of t -> S ----
         {
-            float acc[MAXL] = {0.f, 0.f, 0.f};
-            const float be0 = s_beta[0], be1 = s_beta[1];
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};       // (r, r) loads 0, 1; (A r, r) loads 0, 1
             const int act0 = s_act[0], act1 = s_act[1];
+            const bool wgt = a.W.has != 0;
+            const float w00 = a.W.wf[0], w01 = a.W.wf[1], w10 = a.W.wf[2], w11 = a.W.wf[3];
             for (int s0 = 0; s0 < nslot; s0 += 4) {
                 float rp[16];
                 tm_ld16(tbase + 4 * s0, rp);
@@ -468,11 +459,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                     const int u = u0 + j, l = u & 1;
                     C t = make_float2(0.f, 0.f);
                     if (l == 0 ? act0 : act1) {
-                        const float be = l == 0 ? be0 : be1;
-                        const float p0 = rp[4 * i] + be * rp[4 * i + 2];
-                        const float p1 = rp[4 * i + 1] + be * rp[4 * i + 3];
-                        rp[4 * i + 2] = p0;
-                        rp[4 * i + 3] = p1;
+                        const float r0 = rp[4 * i], r1 = rp[4 * i + 1];
                         float a00, a01, a10, a11;
                         if (a.co.mode == 0) {
                             const float* tb = tab + min((int)ph_s[e], nph1) * 4;
@@ -481,16 +468,21 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                             const size_t mk = (size_t)(u >> 1) * N + k;
                             a00 = __ldg(fld + mk); a11 = __ldg(fld + M + mk); a01 = a10 = __ldg(fld + 2 * M + mk);
                         }
-                        t.x = a00 * p0 + a01 * p1;
-                        t.y = a10 * p0 + a11 * p1;
-                        const float q = p0 * t.x + p1 * t.y;
-                        if (l == 0) acc[0] += q; else acc[1] += q;
+                        t.x = a00 * r0 + a01 * r1;
+                        t.y = a10 * r0 + a11 * r1;
+                        // (r, r) in the scalar product of the iteration, (W r, r)
+                        float wr0 = r0, wr1 = r1;
+                        if (wgt) {
+                            wr0 = w00 * r0 + w01 * r1;
+                            wr1 = w10 * r0 + w11 * r1;
+                        }
+                        const float g = r0 * wr0 + r1 * wr1;
+                        const float dl = r0 * t.x + r1 * t.y;
+                        if (l == 0) { acc[0] += g; acc[2] += dl; } else { acc[1] += g; acc[3] += dl; }
                     }
                     buf[e] = make_float2(t.x, -t.y);        // conj(t0 + i t1)
                 }
-                tm_st16(tbase + 4 * s0, rp);
             }
-            tm_wait_st();
             __syncthreads();
             const C* yb = rifft<N>(buf, buf2, nu, tws);     // conj(DFT(t0 + i t1))
             // Z = t0 + i t1:  T0(k) = (Z(k) + conj Z(-k)) / 2,  T1(k) = (Z(k) - conj Z(-k)) / 2i,
@@ -507,21 +499,20 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                 a.S[o] = A;
                 a.S[o + (size_t)N * HP] = B;
             }
-            double pk[MAXL];
-            block_sum_t<float, MAXL>(acc, pk);
-            if (tid == 0) {
-                a.part[((size_t)0 * T + c) * MAXL + 0] = pk[0];
-                a.part[((size_t)0 * T + c) * MAXL + 1] = pk[1];
-            }
+            double pk[4];
+            block_sum_t<float, 4>(acc, pk);
+            if (tid == 0)
+                for (int k = 0; k < 4; ++k) a.part[(size_t)c * 4 + k] = pk[k];
         }
         team_arrive(a.bar);
         if (!(ok = team_wait(a.bar, ++seq * (unsigned)T, a.err, a.wait_ns))) break;
 
-        // ---- phase B: column DFT, Gamma_hat, inverse column DFT ----
+        // ---- phase B: the step scalars; column DFT, Gamma_hat, inverse column DFT ----
         {
-            // the team's (p, A p) partials: loaded now, summed after the column loads
+            // the team's partials: loaded now (warps 0..3, one sum each), summed
+            // after the column loads
             TeamPart tp;
-            if (tid < 32) team_load(a.part, 0, T, tp);
+            if (tid < 128) team_load(a.part, warp, T, tp);
             const int ntot = nv * 2 * N;
             for (int i0 = tid; i0 < ntot; i0 += KB * RES_THREADS) {
                 C val[KB];
@@ -543,31 +534,67 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                 for (int q = 0; q < KB; ++q)
                     if (dst[q] >= 0) buf[dst[q]] = make_float2(val[q].x, -val[q].y);   // conjugated
             }
-            // alpha = (r, r) / (p, A p) (Moulinec-Suquet: 1 / lambda), from the
-            // team's partial sums: their loads overlapped the column loads above
-            if (tid < 32) team_reduce(tp, s_red);
+            if (tid < 128) team_reduce(tp, &s_red[warp]);
             __syncthreads();
+            // stopping tests on r_i (the iterate x_i is final when they hold), then
+            // beta_i, alpha_i (Moulinec-Suquet: beta = 0, alpha = 1 / lambda)
             if (tid == 0 || tid == 32) {
                 const int l = tid >> 5;
                 if (s_act[l]) {
-                    Scalars s = s_sc[l];
-                    const double val = s_red[l] * invMd;
-                    s.pt = val;
-                    if (s.fixed_alpha > 0.0 && s.rr == 0.0) {
-                        s.status = ST_CONVERGED;
-                        s.alpha = 0.0;
-                    } else if (!(val > 0.0) || !isfinite(val)) {
-                        s.status = ST_BREAKDOWN;
-                        s.alpha = 0.0;
-                    } else {
-                        s.alpha = s.fixed_alpha > 0.0 ? s.fixed_alpha : s.rr * rcp_d(val);
+                    Scalars sc = s_sc[l];
+                    const double g = s_red[l] * invMd;
+                    const double dl = s_red[2 + l] * invMd;
+                    const double ib = rcp_d(sc.bnorm);
+                    if (sc.iters > 0) {
+                        const double rel = sqrt_d(g) * ib;
+                        sc.relres = rel;
+                        // Moulinec-Suquet stops on the step just taken, x_i - x_{i-1} =
+                        // r_{i-1} / lambda (the tolerance was rescaled at the right-hand side)
+                        const double crit = sc.fixed_alpha > 0.0 ? sqrt_d(sc.rr) * ib : rel;
+                        if (!isfinite(g)) sc.status = ST_BREAKDOWN;
+                        else if (crit <= sc.tol) sc.status = ST_CONVERGED;
+                        else if (sc.iters >= sc.max_iter) sc.status = ST_MAXITER;
+                        if (sc.stall_max > 0 && sc.status == ST_ACTIVE) {
+                            if (g < 0.25 * sc.best_rr) {
+                                sc.best_rr = g;
+                                sc.stall = 0;
+                            } else if (++sc.stall >= sc.stall_max) {
+                                sc.status = ST_STAGNATED;
+                            }
+                        }
                     }
-                    s.alpha_f = (float)s.alpha;
-                    s_alpha[l] = s.alpha_f;
-                    s_act[l] = s.status == ST_ACTIVE;
-                    s_sc[l] = s;
+                    if (sc.status == ST_ACTIVE) {
+                        double beta = 0.0, alpha = 0.0, den = dl;
+                        if (sc.fixed_alpha > 0.0) {
+                            alpha = sc.fixed_alpha;
+                            if (g == 0.0) sc.status = ST_CONVERGED;   // the fixed point, exactly
+                        } else {
+                            if (sc.iters > 0) {
+                                beta = g * rcp_d(sc.rr);
+                                den = dl - beta * g * rcp_d(sc.alpha);
+                            }
+                            if (!(den > 0.0) || !isfinite(den)) sc.status = ST_BREAKDOWN;
+                            else alpha = g * rcp_d(den);
+                        }
+                        if (sc.status == ST_ACTIVE) {
+                            sc.iters += 1;
+                            sc.total_iters += 1;
+                        }
+                        sc.pt = den;
+                        sc.beta = beta;
+                        sc.alpha = alpha;
+                        sc.beta_f = (float)beta;
+                        sc.alpha_f = (float)alpha;
+                    }
+                    sc.rr = g;
+                    s_alpha[l] = sc.alpha_f;
+                    s_beta[l] = sc.beta_f;
+                    s_act[l] = sc.status == ST_ACTIVE;
+                    s_sc[l] = sc;
                 }
             }
+            __syncthreads();
+            if (!(s_act[0] | s_act[1])) break;     // every system has stopped at x_i
             C* th = rifft<N>(buf, buf2, 2 * nv, tws);       // conj(t_hat)
             // q_hat = xi (xi . t_hat) / (xi . A0 xi) / |N|   (dual: onto J_N)
             for (int e = tid; e < nv * N; e += RES_THREADS) {
@@ -613,7 +640,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
         team_arrive(a.bar);
         if (!(ok = team_wait(a.bar, ++seq * (unsigned)T, a.err, a.wait_ns))) break;
 
-        // ---- phase C: row inverse DFT -> q, x += alpha p, r -= alpha q, (r, r) ----
+        // ---- phase C: row inverse DFT -> w = K r; p, s, x, r updates ----
         {
             // the CTA's spectrum rows: one bulk copy per row, on the mbarrier
             if (tid == 0) {
@@ -648,16 +675,15 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                 buf[e] = make_float2(w0.x - w1.y, w0.y + w1.x);
             }
             __syncthreads();
-            const C* qr = rifft<N>(buf, buf2, nu, tws);
-            float acc[MAXL] = {0.f, 0.f, 0.f};
-            const bool wgt = a.W.has != 0;
-            const float w00 = a.W.wf[0], w01 = a.W.wf[1], w10 = a.W.wf[2], w11 = a.W.wf[3];
+            const C* wr = rifft<N>(buf, buf2, nu, tws);     // w = K r
             const float al0 = s_alpha[0], al1 = s_alpha[1];
+            const float be0 = s_beta[0], be1 = s_beta[1];
             const int act0 = s_act[0], act1 = s_act[1];
             for (int s0 = 0; s0 < nslot; s0 += 4) {
-                float rp[16], xx[8];
+                float rp[16], xx[8], ss[8];
                 tm_ld16(tbase + 4 * s0, rp);
                 tm_ld8(tbase + RES_XCOL + 2 * s0, xx);
+                tm_ld8(tbase + RES_SCOL + 2 * s0, ss);
                 tm_wait_ld();
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
@@ -667,67 +693,27 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                     const int l = (u0 + j) & 1;
                     if (!(l == 0 ? act0 : act1)) continue;
                     const float al = l == 0 ? al0 : al1;
-                    const C q = qr[e];
-                    xx[2 * i] += al * rp[4 * i + 2];
-                    xx[2 * i + 1] += al * rp[4 * i + 3];
-                    const float rn0 = rp[4 * i] - al * q.x;
-                    const float rn1 = rp[4 * i + 1] - al * q.y;
-                    rp[4 * i] = rn0;
-                    rp[4 * i + 1] = rn1;
-                    float wr0 = rn0, wr1 = rn1;
-                    if (wgt) {
-                        wr0 = w00 * rn0 + w01 * rn1;
-                        wr1 = w10 * rn0 + w11 * rn1;
-                    }
-                    const float qq = rn0 * wr0 + rn1 * wr1;
-                    if (l == 0) acc[0] += qq; else acc[1] += qq;
+                    const float be = l == 0 ? be0 : be1;
+                    const C w = wr[e];
+                    const float p0 = rp[4 * i] + be * rp[4 * i + 2];
+                    const float p1 = rp[4 * i + 1] + be * rp[4 * i + 3];
+                    const float s0v = w.x + be * ss[2 * i];
+                    const float s1v = w.y + be * ss[2 * i + 1];
+                    rp[4 * i + 2] = p0;
+                    rp[4 * i + 3] = p1;
+                    ss[2 * i] = s0v;
+                    ss[2 * i + 1] = s1v;
+                    xx[2 * i] += al * p0;
+                    xx[2 * i + 1] += al * p1;
+                    rp[4 * i] -= al * s0v;
+                    rp[4 * i + 1] -= al * s1v;
                 }
                 tm_st16(tbase + 4 * s0, rp);
                 tm_st8(tbase + RES_XCOL + 2 * s0, xx);
+                tm_st8(tbase + RES_SCOL + 2 * s0, ss);
             }
             tm_wait_st();
-            double pk[MAXL];
-            block_sum_t<float, MAXL>(acc, pk);
-            if (tid == 0) {
-                a.part[((size_t)1 * T + c) * MAXL + 0] = pk[0];
-                a.part[((size_t)1 * T + c) * MAXL + 1] = pk[1];
-            }
         }
-        team_arrive(a.bar);
-        if (!(ok = team_wait(a.bar, ++seq * (unsigned)T, a.err, a.wait_ns))) break;
-
-        // beta = (r, r)_new / (r, r)_old and the stopping tests (as k_row_inv)
-        team_sums(a.part, 1, T, s_red);
-        __syncthreads();
-        if (tid == 0 || tid == 32) {
-            const int l = tid >> 5;
-            if (s_act[l]) {
-                Scalars s = s_sc[l];
-                const double rr = s_red[l] * invMd;
-                s.iters += 1;
-                s.total_iters += 1;
-                const double ib = rcp_d(s.bnorm);
-                const double rel = sqrt_d(rr) * ib;
-                s.relres = rel;
-                const double crit = s.fixed_alpha > 0.0 ? sqrt_d(s.rr) * ib : rel;
-                if (!isfinite(rr)) s.status = ST_BREAKDOWN;
-                else if (crit <= s.tol) s.status = ST_CONVERGED;
-                else if (s.iters >= s.max_iter) s.status = ST_MAXITER;
-                if (s.stall_max > 0 && s.status == ST_ACTIVE) {
-                    if (rr < 0.25 * s.best_rr) {
-                        s.best_rr = rr;
-                        s.stall = 0;
-                    } else if (++s.stall >= s.stall_max) {
-                        s.status = ST_STAGNATED;
-                    }
-                }
-                s.beta = s.fixed_alpha > 0.0 ? 0.0 : rr * rcp_d(s.rr);
-                s.beta_f = (float)s.beta;
-                s.rr = rr;
-                s_sc[l] = s;
-            }
-        }
-        __syncthreads();
     }
 
     // x of the inner system back to global memory; scalars (CTA 0)
