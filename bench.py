@@ -884,8 +884,9 @@ def run_batched(args):
         "kernel_launches_per_batch": int(bk_launches),
         "AH_max_rel_err_vs_fp64_tol1e-10": err_bk,
         "scheduler": {"solves_per_s": solves_per_s, "voxel_iter_per_s": vox / t_total,
-                      "how": "the same 256 problems submitted together through hg_submit (continuous "
-                             "batching across per-request streams)",
+                      "how": "the same 256 problems submitted together through hg_submit: the scheduler's "
+                             "rolling batch steps all admitted requests each tick, one batched launch per "
+                             "pass and grid shape, refinement batched per shape",
                       "AH_max_rel_err_vs_fp64_tol1e-10": err, "clocks": clocks},
         "launch_geometry": tune_note,
         "plain_fp64_per_request": {"solves_per_s": 1.0 / t_fp64, "sample": "32 seeded problems",

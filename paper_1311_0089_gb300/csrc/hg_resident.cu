@@ -42,13 +42,13 @@ namespace hgk {
 
 constexpr int RES_THREADS = 512;
 
-// FFT plans of the resident kernels (FP32, both axes of length N).  Radices
-// stay at most 15: a radix-27 butterfly needs more registers than a
-// 512-thread CTA leaves a thread (128) beside the solver's own state.
+// FFT plans of the resident kernels (FP32, both axes of length N): the fewest
+// stages whose butterflies (register codelets up to radix 27) fit a thread's
+// 128 registers in the out-of-place stages.
 template <int N> struct ResPlan;
-template <> struct ResPlan<729> { typedef RadixList<9, 9, 9> type; };
-template <> struct ResPlan<375> { typedef RadixList<15, 5, 5> type; };
-template <> struct ResPlan<243> { typedef RadixList<9, 9, 3> type; };
+template <> struct ResPlan<729> { typedef RadixList<27, 27> type; };
+template <> struct ResPlan<375> { typedef RadixList<15, 25> type; };
+template <> struct ResPlan<243> { typedef RadixList<27, 9> type; };
 template <> struct ResPlan<135> { typedef RadixList<15, 9> type; };
 template <> struct ResPlan<81> { typedef RadixList<9, 9> type; };
 template <> struct ResPlan<75> { typedef RadixList<15, 5> type; };
@@ -321,6 +321,28 @@ __device__ __forceinline__ void team_reduce(const TeamPart& tp, double* out) {
     if (lane == 0) *out = (double)s0 + (double)e0;
 }
 
+// CTA sum of four per-thread FP32 partials: warp sums in FP32 (32 terms),
+// then thread v < 4 adds the 16 warp sums of value v as a float-float pair
+// (TwoSum) and writes it, pair-packed, to part[v] (global memory).
+__device__ __forceinline__ void block_sum4(const float (&v)[4], double* part) {
+    __shared__ float red[4][RES_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float x = v[i];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+        if (lane == 0) red[i][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int w = 0; w < RES_THREADS / 32; ++w) ff_add(hi, lo, red[threadIdx.x][w], 0.f);
+        part[threadIdx.x] = pack_pair(hi, lo);
+    }
+}
+
 // FP64 1/x and sqrt(x) by Newton-Raphson from FP32 seeds (two steps each:
 // 2^-24 -> 2^-48 -> FP64 rounding), a few FMAs on the slow FP64 pipe instead
 // of the full division and square-root sequences.
@@ -371,6 +393,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
     __shared__ float s_alpha[L], s_beta[L];
     __shared__ int s_act[L];
     __shared__ double s_red[4];
+    __shared__ double s_ib2[L];          // 1 / ||b||^2 of each system (the step scalars are
+                                         // formed in FP32 from quantities normalised by it)
     __shared__ uint32_t s_taddr;
     __shared__ __align__(8) uint64_t s_mbar;
 
@@ -394,7 +418,11 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
             const int j = e / N, k = e - j * N;
             ph_s[e] = a.co.phase[(size_t)((u0 + j) >> 1) * N + k];
         }
-    if (tid < L) s_sc[tid] = a.sc[tid];
+    if (tid < L) {
+        s_sc[tid] = a.sc[tid];
+        const double bn = a.sc[tid].bnorm;
+        s_ib2[tid] = bn > 0.0 ? 1.0 / (bn * bn) : 0.0;
+    }
     tm_fence_before();
     __syncthreads();
     tm_fence_after();
@@ -499,10 +527,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                 a.S[o] = A;
                 a.S[o + (size_t)N * HP] = B;
             }
-            double pk[4];
-            block_sum_t<float, 4>(acc, pk);
-            if (tid == 0)
-                for (int k = 0; k < 4; ++k) a.part[(size_t)c * 4 + k] = pk[k];
+            block_sum4(acc, a.part + (size_t)c * 4);
         }
         team_arrive(a.bar);
         if (!(ok = team_wait(a.bar, ++seq * (unsigned)T, a.err, a.wait_ns))) break;
@@ -542,17 +567,22 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                 const int l = tid >> 5;
                 if (s_act[l]) {
                     Scalars sc = s_sc[l];
-                    const double g = s_red[l] * invMd;
-                    const double dl = s_red[2 + l] * invMd;
-                    const double ib = rcp_d(sc.bnorm);
+                    const double ib2 = s_ib2[l];
+                    const double g = s_red[l] * invMd;          // gamma = (r, r)
+                    const double dl = s_red[2 + l] * invMd;     // delta = (A r, r)
+                    // the decisions and steps in FP32 on quantities normalised by
+                    // ||b||^2 (O(1), no FP32 under- or overflow), a few FP64 products
+                    const float gn = (float)(g * ib2);
+                    const float dn = (float)(dl * ib2);
+                    const float gn_old = (float)(sc.rr * ib2);
                     if (sc.iters > 0) {
-                        const double rel = sqrt_d(g) * ib;
+                        const float rel = sqrtf(gn);
                         sc.relres = rel;
                         // Moulinec-Suquet stops on the step just taken, x_i - x_{i-1} =
                         // r_{i-1} / lambda (the tolerance was rescaled at the right-hand side)
-                        const double crit = sc.fixed_alpha > 0.0 ? sqrt_d(sc.rr) * ib : rel;
+                        const float crit = sc.fixed_alpha > 0.0 ? sqrtf(gn_old) : rel;
                         if (!isfinite(g)) sc.status = ST_BREAKDOWN;
-                        else if (crit <= sc.tol) sc.status = ST_CONVERGED;
+                        else if ((double)crit <= sc.tol) sc.status = ST_CONVERGED;
                         else if (sc.iters >= sc.max_iter) sc.status = ST_MAXITER;
                         if (sc.stall_max > 0 && sc.status == ST_ACTIVE) {
                             if (g < 0.25 * sc.best_rr) {
@@ -564,27 +594,27 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_cg_resident(ResArgs a) {
                         }
                     }
                     if (sc.status == ST_ACTIVE) {
-                        double beta = 0.0, alpha = 0.0, den = dl;
+                        float beta = 0.f, alpha = 0.f, den = dn;
                         if (sc.fixed_alpha > 0.0) {
-                            alpha = sc.fixed_alpha;
+                            alpha = (float)sc.fixed_alpha;
                             if (g == 0.0) sc.status = ST_CONVERGED;   // the fixed point, exactly
                         } else {
                             if (sc.iters > 0) {
-                                beta = g * rcp_d(sc.rr);
-                                den = dl - beta * g * rcp_d(sc.alpha);
+                                beta = gn / gn_old;
+                                den = dn - beta * gn / sc.alpha_f;
                             }
-                            if (!(den > 0.0) || !isfinite(den)) sc.status = ST_BREAKDOWN;
-                            else alpha = g * rcp_d(den);
+                            if (!(den > 0.f) || !isfinite(den)) sc.status = ST_BREAKDOWN;
+                            else alpha = gn / den;
                         }
                         if (sc.status == ST_ACTIVE) {
                             sc.iters += 1;
                             sc.total_iters += 1;
                         }
-                        sc.pt = den;
+                        sc.pt = ib2 > 0.0 ? (double)den / ib2 : 0.0;
                         sc.beta = beta;
-                        sc.alpha = alpha;
-                        sc.beta_f = (float)beta;
-                        sc.alpha_f = (float)alpha;
+                        sc.alpha = sc.fixed_alpha > 0.0 ? sc.fixed_alpha : (double)alpha;
+                        sc.beta_f = beta;
+                        sc.alpha_f = alpha;
                     }
                     sc.rr = g;
                     s_alpha[l] = sc.alpha_f;
