@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <deque>
 #include <vector>
 
 using namespace hgk;
@@ -598,16 +599,22 @@ bool same_shape(const hg_grid* a, const hg_grid* b) {
 // Rolling batch: cross-request batching for the request scheduler
 // ---------------------------------------------------------------------------
 // Admitted requests of one precision (standard CG, primal, A0 = I) form one
-// rolling batch.  Every tick steps all of them by check_every CG iterations:
-// per grid shape each pass is ONE launch for all its requests (the batched
-// pass kernels, grid z = request).  Between ticks the scheduler admits new
-// requests (their right-hand sides are enqueued at once and they join the
-// next tick) and retires finished ones; mixed-precision requests whose inner
-// FP32 solve has stopped get their FP64 refinement step batched per shape.
-// A shape's row tile is fixed when the shape first appears (the batch tile
-// for a nominal 64 requests), never taken from the current mix, and a
-// batched launch computes every request's tiles and reductions as it would
-// alone: a request's result does not depend on which others share its ticks.
+// rolling batch.  A chunk steps all of them by check_every CG iterations: per
+// grid shape each pass is ONE launch for all its requests (the batched pass
+// kernels, grid z = request), then every request's scalars are gathered into
+// pinned host memory.  Two chunks are in flight: a tick enqueues the next
+// chunk, then reads the scalars of the previous one while the GPU runs the
+// new one, and enqueues behind it what they call for: the FP64 refinement
+// steps (batched per shape) and next inner solves of requests whose inner
+// FP32 solve has stopped, the A_H of requests that have finished.  A request
+// with host work enqueued sits out (its passes find no active system) until a
+// chunk gathered after that work; a finished request's result is returned
+// once its A_H has been copied.  New requests join and finished ones leave
+// between ticks.  A shape's row tile is fixed when the shape first appears
+// (the batch tile for a nominal 64 requests), never taken from the current
+// mix, and a batched launch computes every request's tiles and reductions as
+// it would alone: a request's result depends neither on which others share
+// its chunks nor on when the host reads them.
 namespace hgrt {
 
 struct RollShape {
@@ -616,7 +623,8 @@ struct RollShape {
     BatchItems cg, ref[3];        // CG iteration and refinement items, capacity cap
     std::vector<void*> blocks;    // their device arrays
     int cap = 0;
-    hg_grid* key = nullptr;       // a grid of this shape (shape comparison only)
+    cudaStream_t s = nullptr;     // the shape's branch of a chunk
+    cudaEvent_t join = nullptr;
     int d = 0, N[3] = {0, 0, 0};
     double Y[3] = {0, 0, 0};
 };
@@ -627,10 +635,41 @@ struct RollMember {
     hg_solve_opts o{};
     int shape = -1;
     bool checked = false;         // mixed: the FP32 right-hand side's zero test has been read
-    bool refining = false;        // refinement enqueued: the next inner solve starts next tick
-    long long ticks = 0;
+    long long valid_from = 0;     // first chunk whose scalars follow the host work enqueued for it
+    long long ticks = 0;          // chunks read for it
     double t0 = 0.0;
     long long launches0 = 0;
+};
+
+// A chunk whose scalars the host has not read yet.
+struct RollGather {
+    long long id = -1;
+    std::vector<uint64_t> tags;   // its members, in gather order
+    Scalars* h = nullptr;         // pinned: outer scalars of every member, then inner
+    int cap = 0;                  // members h holds
+    cudaEvent_t ev = nullptr;     // recorded after the copy into h
+};
+
+// Finished members whose A_H (and FP64 true residual) are being copied.
+struct RollRetired {
+    RollMember m;
+    Scalars outer[MAXL];
+};
+struct RollRetire {
+    std::vector<RollRetired> items;
+    cudaEvent_t ev = nullptr;
+};
+
+// Pinned staging of the host-to-device uploads of one tick (launch items,
+// gather pointers), one per stream that copies (the batch's and the
+// refinement stream); a buffer is reused three ticks later, after the copies
+// from it have run.
+constexpr int ROLL_STAGES = 3;
+struct RollStage {
+    char* h = nullptr;
+    size_t cap = 0, used = 0;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;
 };
 
 struct Rolling {
@@ -640,11 +679,90 @@ struct Rolling {
     std::vector<RollMember> mem;
     std::vector<RollShape> shapes;
     bool dirty = true;
-    int gcap = 0;
+    int gcap = 0;                      // members d_src and d_gather hold
     const Scalars** d_src = nullptr;
     Scalars* d_gather = nullptr;
-    Scalars* h_gather = nullptr;
+    long long seq = 0;                 // chunks enqueued
+    long long nticks = 0;
+    RollGather gat[2];                 // chunk id parity
+    std::deque<RollGather*> unread;    // enqueue order, at most two
+    std::deque<RollRetire> retiring;
+    std::vector<cudaEvent_t> ev_pool;
+    RollStage stage[2][ROLL_STAGES];   // [0] batch stream, [1] refinement stream
+    cudaEvent_t fork = nullptr;
+    // FP64 refinement steps run on their own stream, beside the next chunk;
+    // the refined members' next inner solves start on the batch's stream
+    // before the chunk after that
+    cudaStream_t side = nullptr;
+    cudaEvent_t refined = nullptr;
+    std::vector<uint64_t> restart;
 };
+
+static RollStage& roll_stage(Rolling* R, int k) { return R->stage[k][R->nticks % ROLL_STAGES]; }
+static cudaStream_t stage_stream(Rolling* R, int k) { return k ? R->side : R->s; }
+
+static int stage_begin(Rolling* R) {
+    for (int k = 0; k < 2; ++k) {
+        RollStage& st = roll_stage(R, k);
+        if (st.pending) {
+            HG_CU(cudaEventSynchronize(st.ev));
+            st.pending = false;
+        }
+        st.used = 0;
+    }
+    return HG_OK;
+}
+
+// bytes from host src to device dst on stream k (0 the batch's, 1 the
+// refinement stream), through the tick's pinned stage (the copy runs in
+// stream order; src may go out of scope)
+static int stage_copy(Rolling* R, int k, void* dst, const void* src, size_t bytes) {
+    RollStage& st = roll_stage(R, k);
+    cudaStream_t s = stage_stream(R, k);
+    size_t off = (st.used + 15) & ~size_t(15);
+    if (off + bytes > st.cap) {
+        // growing: the copies enqueued from this buffer run first
+        HG_CU(cudaStreamSynchronize(s));
+        const size_t cap = std::max(off + bytes, 2 * st.cap) + ((size_t)64 << 10);
+        char* h = nullptr;
+        HG_CU(cudaMallocHost((void**)&h, cap));
+        if (st.h) cudaFreeHost(st.h);
+        st.h = h;
+        st.cap = cap;
+        off = 0;
+    }
+    if (!st.ev) HG_CU(cudaEventCreateWithFlags(&st.ev, cudaEventDisableTiming));
+    memcpy(st.h + off, src, bytes);
+    HG_CU(cudaMemcpyAsync(dst, st.h + off, bytes, cudaMemcpyHostToDevice, s));
+    st.used = off + bytes;
+    st.pending = true;
+    return HG_OK;
+}
+
+static int stage_end(Rolling* R) {
+    for (int k = 0; k < 2; ++k) {
+        RollStage& st = roll_stage(R, k);
+        if (st.pending) HG_CU(cudaEventRecord(st.ev, stage_stream(R, k)));
+    }
+    return HG_OK;
+}
+
+static int roll_copy_items(Rolling* R, int k, const std::vector<PassArgs>& pas, BatchItems* it) {
+    const size_t P = pas.size();
+    std::vector<RowFwdArgs> fa(P);
+    std::vector<RowInvArgs> ia(P);
+    std::vector<StrArgs> sa(P);
+    for (size_t p = 0; p < P; ++p) { fa[p] = pas[p].fa; ia[p] = pas[p].ia; }
+    int st;
+    if ((st = stage_copy(R, k, it->fa, fa.data(), P * sizeof(RowFwdArgs)))) return st;
+    if ((st = stage_copy(R, k, it->ia, ia.data(), P * sizeof(RowInvArgs)))) return st;
+    for (int j = 0; j < pas[0].nstr; ++j) {
+        for (size_t p = 0; p < P; ++p) sa[p] = pas[p].sa[j];
+        if ((st = stage_copy(R, k, it->sa[j], sa.data(), P * sizeof(StrArgs)))) return st;
+    }
+    it->first = pas[0];
+    return HG_OK;
+}
 
 static void roll_free_shape(Rolling* R, RollShape& sh) {
     for (void* b : sh.blocks) dev_free(R->ctx, b);
@@ -655,6 +773,10 @@ static void roll_free_shape(Rolling* R, RollShape& sh) {
 static int roll_items_alloc(Rolling* R, RollShape& sh, int need) {
     if (need <= sh.cap) return HG_OK;
     const int cap = std::max(need, std::max(8, 2 * sh.cap));
+    if (sh.cap) {   // chunks and refinement steps in flight read the old arrays
+        HG_CU(cudaStreamSynchronize(R->s));
+        HG_CU(cudaStreamSynchronize(R->side));
+    }
     roll_free_shape(R, sh);
     BatchItems* all[4] = {&sh.cg, &sh.ref[0], &sh.ref[1], &sh.ref[2]};
     for (BatchItems* it : all) {
@@ -686,22 +808,49 @@ Rolling* rolling_create(hg_ctx* ctx, int prec, int chunk) {
         delete R;
         return nullptr;
     }
+    if (cudaStreamCreateWithFlags(&R->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&R->refined, cudaEventDisableTiming) != cudaSuccess) {
+        if (R->side) cudaStreamDestroy(R->side);
+        cudaStreamDestroy(R->s);
+        delete R;
+        return nullptr;
+    }
     return R;
 }
 
 void rolling_destroy(Rolling* R) {
     if (!R) return;
+    cudaStreamSynchronize(R->side);
     cudaStreamSynchronize(R->s);
-    for (RollShape& sh : R->shapes) roll_free_shape(R, sh);
+    for (RollShape& sh : R->shapes) {
+        roll_free_shape(R, sh);
+        if (sh.s) cudaStreamDestroy(sh.s);
+        if (sh.join) cudaEventDestroy(sh.join);
+    }
+    if (R->fork) cudaEventDestroy(R->fork);
     dev_free(R->ctx, (void*)R->d_src);
     dev_free(R->ctx, R->d_gather);
-    if (R->h_gather) cudaFreeHost(R->h_gather);
+    for (RollGather& G : R->gat) {
+        if (G.h) cudaFreeHost(G.h);
+        if (G.ev) cudaEventDestroy(G.ev);
+    }
+    for (auto& ring : R->stage)
+        for (RollStage& st : ring) {
+            if (st.h) cudaFreeHost(st.h);
+            if (st.ev) cudaEventDestroy(st.ev);
+        }
+    for (RollRetire& rt : R->retiring) R->ev_pool.push_back(rt.ev);
+    for (cudaEvent_t e : R->ev_pool) cudaEventDestroy(e);
+    cudaEventDestroy(R->refined);
+    cudaStreamDestroy(R->side);
     cudaStreamDestroy(R->s);
     delete R;
 }
 
 int rolling_chunk(const Rolling* R) { return R->chunk; }
-int rolling_size(const Rolling* R) { return (int)R->mem.size(); }
+int rolling_size(const Rolling* R) {
+    return (int)(R->mem.size() + R->unread.size() + R->retiring.size());
+}
 
 static bool roll_same_shape(const RollShape& sh, const hg_grid* g) {
     if (sh.d != g->gd.d) return false;
@@ -740,7 +889,8 @@ int rolling_add(Rolling* R, hg_grid* g, const hg_solve_opts& o, uint64_t tag) {
     if (R->prec == 1 && (st = grid_alloc_work(g, 1))) return st;
     g->form = 0;
     g->has_ref = 0;
-    // the right-hand side (as a single solve computes it), on the batch's stream
+    // the right-hand side (as a single solve computes it), on the batch's
+    // stream behind the chunks already enqueued
     int init_st[MAXL];
     roll_load_status(o, L, init_st);
     HG_CU(launch_init_scalars(g->work[0].sc, L, init_st, o.tol, R->prec ? o.max_outer : o.max_iter, 0.0, 1.0, R->s));
@@ -762,6 +912,7 @@ int rolling_add(Rolling* R, hg_grid* g, const hg_solve_opts& o, uint64_t tag) {
     m.o = o;
     m.shape = roll_shape_of(R, g);
     m.checked = R->prec == 0;
+    m.valid_from = R->seq;
     m.t0 = wall_ms();
     m.launches0 = g->ctx->launches.load();
     R->mem.push_back(m);
@@ -770,16 +921,24 @@ int rolling_add(Rolling* R, hg_grid* g, const hg_solve_opts& o, uint64_t tag) {
 }
 
 void rolling_remove(Rolling* R, uint64_t tag) {
+    cudaStreamSynchronize(R->side);
     cudaStreamSynchronize(R->s);
     for (size_t i = 0; i < R->mem.size(); ++i)
         if (R->mem[i].tag == tag) {
             R->mem.erase(R->mem.begin() + (long)i);
             R->dirty = true;
-            return;
+            break;
         }
+    for (RollRetire& rt : R->retiring)
+        for (size_t i = 0; i < rt.items.size(); ++i)
+            if (rt.items[i].m.tag == tag) {
+                rt.items.erase(rt.items.begin() + (long)i);
+                break;
+            }
 }
 
-// Member lists per shape, CG items and gather pointers of the current members.
+// Member lists per shape, CG items and gather pointers of the current members
+// (uploaded in stream order, behind the chunks in flight).
 static int roll_rebuild(Rolling* R) {
     for (RollShape& sh : R->shapes) sh.members.clear();
     for (size_t i = 0; i < R->mem.size(); ++i) R->shapes[R->mem[i].shape].members.push_back((int)i);
@@ -792,19 +951,17 @@ static int roll_rebuild(Rolling* R) {
             hg_grid* g = R->mem[sh.members[i]].g;
             cg_iteration_args(g, R->prec, g->gd.d, &pas[i]);
         }
-        if ((st = copy_items(pas, R->s, &sh.cg))) return st;
+        if ((st = roll_copy_items(R, 0, pas, &sh.cg))) return st;
     }
     const int P = (int)R->mem.size();
-    if (2 * P > R->gcap) {
-        const int cap = std::max(2 * P, std::max(64, 2 * R->gcap));
-        cudaStreamSynchronize(R->s);
+    if (P > R->gcap) {
+        const int cap = std::max(P, std::max(64, 2 * R->gcap));
+        HG_CU(cudaStreamSynchronize(R->s));   // the chunk in flight gathers through them
         dev_free(R->ctx, (void*)R->d_src);
         dev_free(R->ctx, R->d_gather);
-        if (R->h_gather) cudaFreeHost(R->h_gather);
-        R->d_src = nullptr; R->d_gather = nullptr; R->h_gather = nullptr; R->gcap = 0;
-        if ((st = dev_alloc(R->ctx, (void**)&R->d_src, cap * sizeof(Scalars*)))) return st;
-        if ((st = dev_alloc(R->ctx, (void**)&R->d_gather, (size_t)cap * MAXL * sizeof(Scalars)))) return st;
-        HG_CU(cudaMallocHost((void**)&R->h_gather, (size_t)cap * MAXL * sizeof(Scalars)));
+        R->d_src = nullptr; R->d_gather = nullptr; R->gcap = 0;
+        if ((st = dev_alloc(R->ctx, (void**)&R->d_src, 2 * (size_t)cap * sizeof(Scalars*)))) return st;
+        if ((st = dev_alloc(R->ctx, (void**)&R->d_gather, 2 * (size_t)cap * MAXL * sizeof(Scalars)))) return st;
         R->gcap = cap;
     }
     std::vector<const Scalars*> src(2 * P);
@@ -812,8 +969,7 @@ static int roll_rebuild(Rolling* R) {
         src[p] = R->mem[p].g->work[0].sc;
         src[P + p] = R->mem[p].g->work[R->prec].sc;
     }
-    HG_CU(cudaMemcpyAsync(R->d_src, src.data(), 2 * P * sizeof(Scalars*), cudaMemcpyHostToDevice, R->s));
-    HG_CU(cudaStreamSynchronize(R->s));   // src is pageable and goes out of scope
+    if ((st = stage_copy(R, 0, (void*)R->d_src, src.data(), 2 * P * sizeof(Scalars*)))) return st;
     R->dirty = false;
     return HG_OK;
 }
@@ -824,31 +980,112 @@ static bool roll_any(const Scalars* h, int L, int status) {
     return false;
 }
 
-int rolling_tick(Rolling* R, std::vector<RollDone>* done) {
-    if (R->mem.empty()) return HG_OK;
+// check_every iterations of every member, then the gather of their scalars.
+// Each shape's iterations run on a stream of their own, so that the launches
+// of different shapes overlap on the device (a shape of small grids does not
+// fill the GPU alone); the batch's stream waits for all of them.
+static int roll_enqueue_chunk(Rolling* R) {
     int st;
-    if (R->dirty && (st = roll_rebuild(R))) return st;
-    const bool mixed = R->prec == 1;
+    if (!R->fork) HG_CU(cudaEventCreateWithFlags(&R->fork, cudaEventDisableTiming));
+    HG_CU(cudaEventRecord(R->fork, R->s));
+    for (RollShape& sh : R->shapes) {
+        if (sh.members.empty()) continue;
+        if (!sh.s) HG_CU(cudaStreamCreateWithFlags(&sh.s, cudaStreamNonBlocking));
+        if (!sh.join) HG_CU(cudaEventCreateWithFlags(&sh.join, cudaEventDisableTiming));
+        HG_CU(cudaStreamWaitEvent(sh.s, R->fork, 0));
+        hg_grid* g0 = R->mem[sh.members[0]].g;   // plans and twiddles of the shape
+        for (int i = 0; i < R->chunk; ++i)
+            if ((st = launch_batch(g0, sh.rc[R->prec], R->prec, sh.cg, (int)sh.members.size(), sh.s))) return st;
+        HG_CU(cudaEventRecord(sh.join, sh.s));
+        HG_CU(cudaStreamWaitEvent(R->s, sh.join, 0));
+    }
+    RollGather& G = R->gat[R->seq & 1];
+    for (const RollGather* u : R->unread)
+        if (u == &G) return HG_ERR_ARG;   // (a tick leaves at most the newest chunk unread)
     const int P = (int)R->mem.size();
-    // check_every iterations of every member: per shape one launch per pass
-    for (int i = 0; i < R->chunk; ++i)
-        for (RollShape& sh : R->shapes) {
-            if (sh.members.empty()) continue;
-            hg_grid* g0 = R->mem[sh.members[0]].g;   // plans and twiddles of the shape
-            if ((st = launch_batch(g0, sh.rc[R->prec], R->prec, sh.cg, (int)sh.members.size(), R->s))) return st;
-        }
-    const int n = mixed ? 2 * P : P;
+    if (G.cap < P) {
+        // (its previous chunk has been read: nothing copies into h)
+        const int cap = std::max(P, std::max(64, 2 * G.cap));
+        if (G.h) cudaFreeHost(G.h);
+        G.h = nullptr;
+        G.cap = 0;
+        HG_CU(cudaMallocHost((void**)&G.h, 2 * (size_t)cap * MAXL * sizeof(Scalars)));
+        G.cap = cap;
+    }
+    if (!G.ev) HG_CU(cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming));
+    const int n = R->prec == 1 ? 2 * P : P;
     HG_CU(launch_gather_scalars(R->d_src, R->d_gather, n, R->s));
-    HG_CU(cudaMemcpyAsync(R->h_gather, R->d_gather, sizeof(Scalars) * MAXL * n, cudaMemcpyDeviceToHost, R->s));
-    HG_CU(cudaStreamSynchronize(R->s));
+    HG_CU(cudaMemcpyAsync(G.h, R->d_gather, sizeof(Scalars) * MAXL * n, cudaMemcpyDeviceToHost, R->s));
+    HG_CU(cudaEventRecord(G.ev, R->s));
+    G.id = R->seq++;
+    G.tags.resize(P);
+    for (int p = 0; p < P; ++p) G.tags[p] = R->mem[p].tag;
+    R->unread.push_back(&G);
+    return HG_OK;
+}
+
+// A_H and the scalars of a finished member as a result.
+static RollDone roll_result(const Rolling* R, const RollRetired& it) {
+    const bool mixed = R->prec == 1;
+    const RollMember& m = it.m;
+    hg_grid* g = m.g;
+    const GridDev& gd = g->gd;
+    RollDone dn;
+    memset(&dn, 0, sizeof(dn));
+    dn.tag = m.tag;
+    hg_result& r = dn.res;
+    r.d = gd.d;
+    for (int i = 0; i < gd.d * gd.d; ++i) { r.AH[i] = g->h_AH[i]; r.AH_flux[i] = g->h_AH[gd.d * gd.d + i]; }
+    int res = HG_OK;
+    for (int l = 0; l < gd.d; ++l) {
+        const Scalars& sc = it.outer[l];
+        const int ms = map_status(sc.status);
+        if (mixed) {
+            r.iters[l] = sc.total_iters;
+            r.outer[l] = sc.iters;
+        } else {
+            r.iters[l] = sc.iters;
+        }
+        if (ms != HG_OK && res == HG_OK) res = ms;
+        r.rel_res[l] = sc.relres;
+        const bool solved = sc.status != ST_IDLE && sc.status != ST_ZERO_RHS && sc.bnorm > 0.0;
+        r.true_rel_res[l] = !solved ? 0.0 : (mixed ? sc.relres : g->h_sc[MAXL + l].relres);
+    }
+    r.status = res;
+    r.wall_ms = wall_ms() - m.t0;
+    r.launches = g->ctx->launches.load() - m.launches0;
+    g->last_prec = R->prec;
+    dn.status = res;
+    return dn;
+}
+
+// Reads the scalars of chunk G and enqueues the host work they call for.
+static int roll_read(Rolling* R, RollGather& G) {
+    HG_CU(cudaEventSynchronize(G.ev));
+    const bool mixed = R->prec == 1;
+    const int PG = (int)G.tags.size();
+    const int P = (int)R->mem.size();
+    std::vector<int> at(P, -1);   // gather position of each current member
+    {
+        std::vector<std::pair<uint64_t, int>> tj(PG);
+        for (int j = 0; j < PG; ++j) tj[j] = {G.tags[j], j};
+        std::sort(tj.begin(), tj.end());
+        for (int p = 0; p < P; ++p) {
+            auto f = std::lower_bound(tj.begin(), tj.end(), std::make_pair(R->mem[p].tag, -1));
+            if (f != tj.end() && f->first == R->mem[p].tag) at[p] = f->second;
+        }
+    }
     std::vector<char> due(P, 0), fin(P, 0);
     bool any_due = false, any_fin = false;
+    int st;
     for (int p = 0; p < P; ++p) {
         RollMember& m = R->mem[p];
+        const int j = at[p];
+        if (j < 0 || G.id < m.valid_from) continue;
         hg_grid* g = m.g;
         const int L = g->gd.d;
-        const Scalars* ho = R->h_gather + (size_t)p * MAXL;
-        const Scalars* hi = R->h_gather + (size_t)(P + p) * MAXL;
+        const Scalars* ho = G.h + (size_t)j * MAXL;
+        const Scalars* hi = G.h + (size_t)(PG + j) * MAXL;
         m.ticks++;
         if (!m.checked) {
             m.checked = true;
@@ -866,6 +1103,7 @@ int rolling_tick(Rolling* R, std::vector<RollDone>* done) {
                                         m.o.inner_tol, m.o.max_iter, 64, grid_weight(g), g->partial,
                                         g->counters + 4, R->s));
                 g->ctx->launches++;
+                m.valid_from = R->seq;
                 continue;
             }
         }
@@ -876,18 +1114,9 @@ int rolling_tick(Rolling* R, std::vector<RollDone>* done) {
             any_fin = true;
             continue;
         }
-        if (!mixed) continue;
-        if (m.refining) {
-            // the refinement step enqueued last tick has run: next inner solve
-            HG_CU(launch_inner_init(g->gd, L, (const double*)g->work[0].r, (float*)g->work[1].r,
-                                    (float*)g->work[1].p, (float*)g->work[1].x, g->work[0].sc, g->work[1].sc,
-                                    m.o.inner_tol, m.o.max_iter, 64, grid_weight(g), g->partial, g->counters + 4,
-                                    R->s));
-            g->ctx->launches++;
-            m.refining = false;
-            continue;
-        }
-        if (roll_any(hi, L, ST_ACTIVE)) continue;
+        if (!mixed || roll_any(hi, L, ST_ACTIVE)) continue;
+        // inner solve stopped: refine, unless the refinement steps are spent
+        // (the outer scalars count them)
         int steps = 0;
         for (int l = 0; l < L; ++l)
             if (ho[l].status == ST_ACTIVE) steps = std::max(steps, ho[l].iters);
@@ -901,12 +1130,17 @@ int rolling_tick(Rolling* R, std::vector<RollDone>* done) {
     }
     // FP64 refinement steps of the due members, batched per shape (the steps of
     // a single solve: delta <- Gamma delta, x64 += delta, [x64 <- Gamma x64],
-    // r = -G A (E + x64))
+    // r = -G A (E + x64)), on the refinement stream beside the chunk now
+    // running (whose passes find no active inner system of theirs, so touch
+    // none of their buffers); their next inner solves (which start only where
+    // the outer residual is still above the tolerance) are launched on the
+    // batch's stream before the next chunk
     if (any_due) {
+        cudaStream_t sd = R->side;
         for (RollShape& sh : R->shapes) {
             std::vector<int> sub;
             for (int i : sh.members)
-                if (due[i]) sub.push_back(i);
+                if (i < P && due[i]) sub.push_back(i);
             if (sub.empty()) continue;
             const int ns = (int)sub.size();
             hg_grid* g0 = R->mem[sub[0]].g;
@@ -917,29 +1151,26 @@ int rolling_tick(Rolling* R, std::vector<RollDone>* done) {
                 matvec_args(g, 1, L, g->work[1].x, false, false, nullptr, nullptr, INV_PROJ, nullptr, 1,
                             g->work[0].sc, &pas[i]);
             }
-            if ((st = copy_items(pas, R->s, &sh.ref[0])) || (st = launch_batch(g0, sh.rc[1], 1, sh.ref[0], ns, R->s)))
+            if ((st = roll_copy_items(R, 1, pas, &sh.ref[0])) || (st = launch_batch(g0, sh.rc[1], 1, sh.ref[0], ns, sd)))
                 return st;
             for (int i : sub) {
                 hg_grid* g = R->mem[i].g;
                 HG_CU(launch_outer_update(g->gd, L, (double*)g->work[0].x, (const float*)g->work[1].x,
-                                          g->work[0].sc, g->work[1].sc, R->s));
+                                          g->work[0].sc, g->work[1].sc, sd));
                 g->ctx->launches++;
             }
-            bool tight = false;
-            for (int i : sub) tight |= R->mem[i].o.tol < 1e-8;
-            if (tight) {
-                std::vector<PassArgs> pt;
-                std::vector<int> tsub;
-                for (int i : sub)
-                    if (R->mem[i].o.tol < 1e-8) tsub.push_back(i);
-                pt.resize(tsub.size());
+            std::vector<int> tsub;
+            for (int i : sub)
+                if (R->mem[i].o.tol < 1e-8) tsub.push_back(i);
+            if (!tsub.empty()) {
+                std::vector<PassArgs> pt(tsub.size());
                 for (size_t i = 0; i < tsub.size(); ++i) {
                     hg_grid* g = R->mem[tsub[i]].g;
                     matvec_args(g, 0, L, g->work[0].x, false, false, nullptr, nullptr, INV_PROJ, nullptr, 1, nullptr,
                                 &pt[i]);
                 }
-                if ((st = copy_items(pt, R->s, &sh.ref[1])) ||
-                    (st = launch_batch(g0, sh.rc[0], 0, sh.ref[1], (int)tsub.size(), R->s)))
+                if ((st = roll_copy_items(R, 1, pt, &sh.ref[1])) ||
+                    (st = launch_batch(g0, sh.rc[0], 0, sh.ref[1], (int)tsub.size(), sd)))
                     return st;
             }
             for (int i = 0; i < ns; ++i) {
@@ -947,31 +1178,20 @@ int rolling_tick(Rolling* R, std::vector<RollDone>* done) {
                 matvec_args(g, 0, L, g->work[0].x, true, true, nullptr, nullptr, INV_RESID, nullptr, 1, nullptr,
                             &pas[i]);
             }
-            if ((st = copy_items(pas, R->s, &sh.ref[2])) || (st = launch_batch(g0, sh.rc[0], 0, sh.ref[2], ns, R->s)))
+            if ((st = roll_copy_items(R, 1, pas, &sh.ref[2])) || (st = launch_batch(g0, sh.rc[0], 0, sh.ref[2], ns, sd)))
                 return st;
-            for (int i : sub) R->mem[i].refining = true;
+            for (int i : sub) {
+                RollMember& m = R->mem[i];
+                R->restart.push_back(m.tag);
+                m.valid_from = R->seq;   // the next chunk follows its inner start
+            }
         }
+        HG_CU(cudaEventRecord(R->refined, sd));
     }
     if (!any_fin) return HG_OK;
-    // finished members: FP64 true residual (FP64 path), A_H, then the results
-    for (int p = 0; p < P; ++p) {
-        if (!fin[p]) continue;
-        hg_grid* g = R->mem[p].g;
-        const GridDev& gd = g->gd;
-        if (!mixed) {
-            HG_CU(cudaMemcpyAsync(g->d_sc_aux, g->work[0].sc, sizeof(Scalars) * MAXL, cudaMemcpyDeviceToDevice, R->s));
-            if ((st = enqueue_matvec(g, 0, gd.d, g->work[0].x, true, true, nullptr, nullptr, INV_RESID, nullptr, 0,
-                                     R->s, g->d_sc_aux)))
-                return st;
-            HG_CU(cudaMemcpyAsync(g->h_sc + MAXL, g->d_sc_aux, sizeof(Scalars) * MAXL, cudaMemcpyDeviceToHost, R->s));
-        }
-        HG_CU(launch_energy(gd, gd.d, coeffs_for(g, 0, true), (const double*)g->work[0].x,
-                            R->mem[p].o.loads_mask & ((1u << gd.d) - 1u), g->partial, g->counters + 5, g->d_AH,
-                            R->s));
-        g->ctx->launches++;
-        HG_CU(cudaMemcpyAsync(g->h_AH, g->d_AH, sizeof(double) * 2 * gd.d * gd.d, cudaMemcpyDeviceToHost, R->s));
-    }
-    HG_CU(cudaStreamSynchronize(R->s));
+    // finished members: FP64 true residual (FP64 path), A_H; they leave the
+    // batch now and their results follow the copies
+    RollRetire rt;
     std::vector<RollMember> keep;
     for (int p = 0; p < P; ++p) {
         RollMember& m = R->mem[p];
@@ -981,38 +1201,94 @@ int rolling_tick(Rolling* R, std::vector<RollDone>* done) {
         }
         hg_grid* g = m.g;
         const GridDev& gd = g->gd;
-        RollDone dn;
-        memset(&dn, 0, sizeof(dn));
-        dn.tag = m.tag;
-        hg_result& r = dn.res;
-        r.d = gd.d;
-        for (int i = 0; i < gd.d * gd.d; ++i) { r.AH[i] = g->h_AH[i]; r.AH_flux[i] = g->h_AH[gd.d * gd.d + i]; }
-        int res = HG_OK;
-        const Scalars* ho = R->h_gather + (size_t)p * MAXL;
-        for (int l = 0; l < gd.d; ++l) {
-            const Scalars& sc = ho[l];
-            const int ms = map_status(sc.status);
-            if (mixed) {
-                r.iters[l] = sc.total_iters;
-                r.outer[l] = sc.iters;
-            } else {
-                r.iters[l] = sc.iters;
-            }
-            if (ms != HG_OK && res == HG_OK) res = ms;
-            r.rel_res[l] = sc.relres;
-            const bool solved = sc.status != ST_IDLE && sc.status != ST_ZERO_RHS && sc.bnorm > 0.0;
-            r.true_rel_res[l] = !solved ? 0.0 : (mixed ? sc.relres : g->h_sc[MAXL + l].relres);
+        if (!mixed) {
+            HG_CU(cudaMemcpyAsync(g->d_sc_aux, g->work[0].sc, sizeof(Scalars) * MAXL, cudaMemcpyDeviceToDevice, R->s));
+            if ((st = enqueue_matvec(g, 0, gd.d, g->work[0].x, true, true, nullptr, nullptr, INV_RESID, nullptr, 0,
+                                     R->s, g->d_sc_aux)))
+                return st;
+            HG_CU(cudaMemcpyAsync(g->h_sc + MAXL, g->d_sc_aux, sizeof(Scalars) * MAXL, cudaMemcpyDeviceToHost, R->s));
         }
-        r.status = res;
-        r.wall_ms = wall_ms() - m.t0;
-        r.launches = g->ctx->launches.load() - m.launches0;
-        g->last_prec = R->prec;
-        dn.status = res;
-        done->push_back(dn);
+        HG_CU(launch_energy(gd, gd.d, coeffs_for(g, 0, true), (const double*)g->work[0].x,
+                            m.o.loads_mask & ((1u << gd.d) - 1u), g->partial, g->counters + 5, g->d_AH, R->s));
+        g->ctx->launches++;
+        HG_CU(cudaMemcpyAsync(g->h_AH, g->d_AH, sizeof(double) * 2 * gd.d * gd.d, cudaMemcpyDeviceToHost, R->s));
+        RollRetired it;
+        it.m = m;
+        memcpy(it.outer, G.h + (size_t)at[p] * MAXL, sizeof(it.outer));
+        rt.items.push_back(it);
     }
+    if (R->ev_pool.empty()) {
+        cudaEvent_t e;
+        HG_CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        R->ev_pool.push_back(e);
+    }
+    rt.ev = R->ev_pool.back();
+    R->ev_pool.pop_back();
+    HG_CU(cudaEventRecord(rt.ev, R->s));
+    R->retiring.push_back(rt);
     R->mem.swap(keep);
     R->dirty = true;
     return HG_OK;
+}
+
+// Results of retired members whose copies have completed (all of them, waiting,
+// when `block`).
+static int roll_collect(Rolling* R, std::vector<RollDone>* done, bool block) {
+    while (!R->retiring.empty()) {
+        RollRetire& rt = R->retiring.front();
+        if (block) {
+            HG_CU(cudaEventSynchronize(rt.ev));
+        } else {
+            const cudaError_t q = cudaEventQuery(rt.ev);
+            if (q == cudaErrorNotReady) break;
+            HG_CU(q);
+        }
+        for (const RollRetired& it : rt.items) done->push_back(roll_result(R, it));
+        R->ev_pool.push_back(rt.ev);
+        R->retiring.pop_front();
+    }
+    return HG_OK;
+}
+
+// The next inner solves of the members refined in the last tick, behind their
+// refinement steps, on the batch's stream.
+static int roll_restart(Rolling* R) {
+    if (R->restart.empty()) return HG_OK;
+    HG_CU(cudaStreamWaitEvent(R->s, R->refined, 0));
+    for (uint64_t tag : R->restart)
+        for (RollMember& m : R->mem) {
+            if (m.tag != tag) continue;
+            hg_grid* g = m.g;
+            HG_CU(launch_inner_init(g->gd, g->gd.d, (const double*)g->work[0].r, (float*)g->work[1].r,
+                                    (float*)g->work[1].p, (float*)g->work[1].x, g->work[0].sc, g->work[1].sc,
+                                    m.o.inner_tol, m.o.max_iter, 64, grid_weight(g), g->partial, g->counters + 4,
+                                    R->s));
+            g->ctx->launches++;
+            break;
+        }
+    R->restart.clear();
+    return HG_OK;
+}
+
+int rolling_tick(Rolling* R, std::vector<RollDone>* done) {
+    int st;
+    if ((st = stage_begin(R))) return st;
+    if ((st = roll_restart(R))) return st;
+    // the next chunk of the current members (the previous one may still run)
+    if (!R->mem.empty()) {
+        if (R->dirty && (st = roll_rebuild(R))) return st;
+        if ((st = roll_enqueue_chunk(R))) return st;
+    }
+    // the oldest chunk not read yet, unless it is the only one in flight
+    // while members remain (the next tick reads it behind a new chunk)
+    if (R->unread.size() >= 2 || (R->mem.empty() && !R->unread.empty())) {
+        RollGather* G = R->unread.front();
+        R->unread.pop_front();
+        if ((st = roll_read(R, *G))) return st;
+    }
+    if ((st = stage_end(R))) return st;
+    R->nticks++;
+    return roll_collect(R, done, R->mem.empty() && R->unread.empty());
 }
 
 }  // namespace hgrt

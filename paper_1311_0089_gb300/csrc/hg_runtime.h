@@ -205,7 +205,7 @@ int grid_ensure_partial(hg_grid* g, long long nbx);
 
 // Rolling batch (hg_batch.cpp): the scheduler's cross-request batching.
 // Requests of one precision step together, check_every CG iterations per
-// tick, one batched launch per pass and grid shape for all of them; members
+// chunk, one batched launch per pass and grid shape for all of them; members
 // join and leave between ticks.
 struct Rolling;
 struct RollDone {
@@ -216,6 +216,7 @@ struct RollDone {
 Rolling* rolling_create(hg_ctx* ctx, int prec, int chunk);
 void rolling_destroy(Rolling* R);
 int rolling_chunk(const Rolling* R);
+// Members plus chunks not read yet and results not returned yet (0: idle).
 int rolling_size(const Rolling* R);
 // Row-pass CTAs of the shape's batched launches (reduction slots a member needs).
 long long rolling_nbx(Rolling* R, const hg_grid* g);
@@ -223,10 +224,12 @@ long long rolling_nbx(Rolling* R, const hg_grid* g);
 // state and enqueues its right-hand side.  HG_ERR_NO_MEMORY leaves nothing
 // allocated beyond what the grid already held.
 int rolling_add(Rolling* R, hg_grid* g, const hg_solve_opts& o, uint64_t tag);
-// One tick: check_every iterations of every member, then refinement steps
-// and the results of the members that have finished (appended to *done).
+// One tick: enqueues the next chunk (check_every iterations of every member),
+// reads the scalars of the chunk before it and enqueues the refinement steps
+// and A_H they call for; appends to *done the results whose copies have
+// completed (waits for them once no member is left).
 int rolling_tick(Rolling* R, std::vector<RollDone>* done);
-// Drops a member (cancellation); waits for the batch's stream first.
+// Drops a member (cancellation); waits for the batch's streams first.
 void rolling_remove(Rolling* R, uint64_t tag);
 
 // scheduler (hg_sched.cpp)

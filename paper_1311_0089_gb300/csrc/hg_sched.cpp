@@ -2,10 +2,12 @@
 //
 // Continuous batching across requests.  Requests for the standard CG on
 // Eq. final_system (primal, A0 = I) join the rolling batch of their precision
-// (hg_batch.cpp): every tick steps ALL of them by check_every iterations, with
+// (hg_batch.cpp): every chunk steps ALL of them by check_every iterations, with
 // one batched launch per pass and grid shape for every request of that shape,
-// and their FP64 refinement steps batched per shape; new requests join and
-// finished ones leave between ticks.  Other requests (Moulinec-Suquet, the
+// and their FP64 refinement steps batched per shape beside the next chunk; a
+// tick enqueues one chunk and reads the one before, so the device always has
+// the next chunk queued; new requests join and finished ones leave between
+// ticks.  Other requests (Moulinec-Suquet, the
 // dual formulation, a general reference medium) run as resumable per-request
 // jobs on their own streams, overlapping the batch on the device.  Every
 // admitted request keeps its CG state resident on the device.  Admission
