@@ -14,8 +14,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhg.so")
 SOURCES = ["hg_kernels_f64.cu", "hg_kernels_f32.cu", "hg_kernels.cu", "hg_api.cpp", "hg_capi.cpp",
            "hg_sched.cpp", "hg_noalloc.cu", "hg_batch.cpp",
-           "hg_ga.cu", "hg_tune.cpp", "hg_resident.cu"]
-HEADERS = ["fft_device.cuh", "hg_kernels.cuh", "hg_internal.h", "hg_runtime.h"]
+           "hg_ga.cu", "hg_tune.cpp", "hg_resident.cu", "hg_plane.cu"]
+HEADERS = ["fft_device.cuh", "hg_kernels.cuh", "hg_pencil.cuh", "hg_internal.h", "hg_runtime.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

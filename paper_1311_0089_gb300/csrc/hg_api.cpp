@@ -437,6 +437,14 @@ static void strided_sequence(const hg_grid* g, StrArgs base, int gamma_mode, Pas
     }
 }
 
+// Whether g's FP32 CG iterations run as the plane passes: N0 x N x N grids of
+// the compiled plane lengths, the plain scalar product (A0 = I), and
+// reduction slots for one CTA per (plane, component).
+bool plane_path(const hg_grid* g, int prec) {
+    return prec == 1 && g->use_plane && !g->has_ref && plane_supported(g->gd) &&
+           plane_units(g->gd) * MAXL <= g->partial_slots;
+}
+
 void cg_iteration_args(hg_grid* g, int prec, int L, PassArgs* pa) {
     const GridDev& gd = g->gd;
     Work& w = g->work[prec];
@@ -456,7 +464,16 @@ void cg_iteration_args(hg_grid* g, int prec, int L, PassArgs* pa) {
         sa.has_A0 = 1;
         for (int i = 0; i < d * d; ++i) sa.A0[i] = g->ref[i];
     }
-    strided_sequence(g, sa, STR_GAMMA, pa);
+    pa->plane = plane_path(g, prec) ? 1 : 0;
+    if (pa->plane) {
+        // axis 0 only: the plane passes take axes 1 and 2
+        StrArgs a = sa;
+        a.mode = STR_GAMMA; a.axis = 0; a.outer = 1; a.n = gd.N[0]; a.inner = gd.Ms / gd.N[0];
+        pa->sa[0] = a;
+        pa->nstr = 1;
+    } else {
+        strided_sequence(g, sa, STR_GAMMA, pa);
+    }
     RowInvArgs& ia = pa->ia;
     memset(&ia, 0, sizeof(ia));
     ia.early_stage = 1;
@@ -511,6 +528,22 @@ static int launch_passes(hg_grid* g, int prec, const PassArgs& pa, cudaStream_t 
     const GridDev& gd = g->gd;
     const int last = gd.d - 1;
     int pass = 0;
+    if (pa.plane) {
+        const float2* tw = static_cast<const float2*>(g->tw[1]) + g->plan[last].tw_off;
+        HG_CU(mark(true, pass));
+        HG_CU(launch_plane_fwd(gd, tw, pa.fa, s));
+        HG_CU(mark(false, pass));
+        ++pass;
+        HG_CU(mark(true, pass));
+        HG_CU(launch_strided(prec, gd, g->plan[0], g->tw[prec], g->strcfg[prec][0], pa.sa[0], s));
+        HG_CU(mark(false, pass));
+        ++pass;
+        HG_CU(mark(true, pass));
+        HG_CU(launch_plane_inv(gd, tw, pa.ia, s));
+        HG_CU(mark(false, pass));
+        g->ctx->launches += 3;
+        return HG_OK;
+    }
     HG_CU(mark(true, pass));
     HG_CU(launch_row_fwd(prec, gd, g->plan[last], g->tw[prec], g->rowcfg[prec], pa.fa, s));
     HG_CU(mark(false, pass));
@@ -558,7 +591,8 @@ int enqueue_matvec(hg_grid* g, int prec, int L, const void* u, bool unit_loads, 
 // A CUDA graph of `chunk` CG iterations, cached per precision.
 int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nkern, int prof_pass) {
     GraphCache& gc = g->graphs[prec];
-    if (gc.exec && gc.chunk == chunk && gc.prof_pass == prof_pass && gc.form == g->form &&
+    const int plane = plane_path(g, prec) ? 1 : 0;
+    if (gc.exec && gc.chunk == chunk && gc.prof_pass == prof_pass && gc.form == g->form && gc.plane == plane &&
         gc.has_ref == g->has_ref && (!g->has_ref || memcmp(gc.ref, g->ref, sizeof(gc.ref)) == 0)) {
         *out = gc.exec;
         *nkern = gc.nkern;
@@ -595,6 +629,7 @@ int get_cg_graph(hg_grid* g, int prec, int chunk, cudaGraphExec_t* out, int* nke
     gc.chunk = chunk;
     gc.prof_pass = prof_pass;
     gc.form = g->form;
+    gc.plane = plane;
     gc.has_ref = g->has_ref;
     memcpy(gc.ref, g->ref, sizeof(gc.ref));
     gc.nkern = (int)nk;
@@ -945,6 +980,7 @@ int job_begin(Job& j) {
     if (j.prec == 1 && (st = grid_alloc_work(g, 1))) return st;
     g->form = j.o.formulation == HG_DUAL ? 1 : 0;
     g->has_ref = j.o.A0[0] != 0.0 ? 1 : 0;
+    g->use_plane = j.o.resident != 0 && j.o.time_pass < 0;
     j.zscale = 1.0;
     for (int i = 0; i < 9; ++i) g->ref[i] = g->has_ref && i < gd.d * gd.d ? j.o.A0[i] : 0.0;
     if (g->has_ref) {

@@ -109,6 +109,16 @@ int launch_batch(hg_grid* g0, const RowCfg& rc, int prec, const BatchItems& it, 
     const GridDev& gd = g0->gd;
     const int last = gd.d - 1;
     const int L = it.first.fa.L;
+    if (it.first.plane) {
+        const float2* tw = static_cast<const float2*>(g0->tw[1]) + g0->plan[last].tw_off;
+        const StrArgs& a = it.first.sa[0];
+        HG_CU(launch_plane_fwd_batch(gd, tw, it.fa, P, L, s));
+        HG_CU(launch_strided_batch(prec, gd, g0->plan[0], g0->tw[prec], g0->strcfg[prec][0], it.sa[0], P, L, a.n,
+                                   a.inner, a.outer, s));
+        HG_CU(launch_plane_inv_batch(gd, tw, it.ia, P, L, s));
+        g0->ctx->launches += 3;
+        return HG_OK;
+    }
     HG_CU(launch_row_fwd_batch(prec, gd, g0->plan[last], g0->tw[prec], rc, it.fa, P, L, s));
     g0->ctx->launches++;
     for (int k = 0; k < it.first.nstr; ++k) {
@@ -516,6 +526,7 @@ int solve_batch(Batch& b, hg_result* results) {
             if (b.prec == 1 && (st = grid_alloc_work(g, 1))) return st;
             g->form = 0;
             g->has_ref = 0;
+            g->use_plane = b.o.resident != 0;
         }
         HG_CU(cudaStreamCreateWithFlags(&gr.side, cudaStreamNonBlocking));
         HG_CU(cudaEventCreateWithFlags(&gr.join, cudaEventDisableTiming));
@@ -627,6 +638,7 @@ struct RollShape {
     cudaEvent_t join = nullptr;
     int d = 0, N[3] = {0, 0, 0};
     double Y[3] = {0, 0, 0};
+    bool plane = true;            // its members' use_plane (members of a shape agree)
 };
 
 struct RollMember {
@@ -853,7 +865,7 @@ int rolling_size(const Rolling* R) {
 }
 
 static bool roll_same_shape(const RollShape& sh, const hg_grid* g) {
-    if (sh.d != g->gd.d) return false;
+    if (sh.d != g->gd.d || sh.plane != g->use_plane) return false;
     for (int k = 0; k < 3; ++k)
         if (sh.N[k] != g->gd.N[k] || sh.Y[k] != g->gd.Y[k]) return false;
     return true;
@@ -864,6 +876,7 @@ static int roll_shape_of(Rolling* R, const hg_grid* g) {
         if (roll_same_shape(R->shapes[k], g)) return (int)k;
     RollShape sh;
     sh.d = g->gd.d;
+    sh.plane = g->use_plane;
     for (int k = 0; k < 3; ++k) { sh.N[k] = g->gd.N[k]; sh.Y[k] = g->gd.Y[k]; }
     for (int p = 0; p < 2; ++p) sh.rc[p] = batch_row_cfg(g, p, 64, R->sms);
     R->shapes.push_back(sh);
@@ -881,6 +894,7 @@ static void roll_load_status(const hg_solve_opts& o, int L, int* init_st) {
 
 int rolling_add(Rolling* R, hg_grid* g, const hg_solve_opts& o, uint64_t tag) {
     const int L = g->gd.d;
+    g->use_plane = o.resident != 0;   // (part of the shape key)
     const long long nbx = rolling_nbx(R, g);
     int st;
     if ((st = grid_alloc_common(g))) return st;

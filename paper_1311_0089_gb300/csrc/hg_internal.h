@@ -189,6 +189,19 @@ bool resident_cfg(int n, int L, int T, int nsm, int max_smem, ResCfg& cfg);
 cudaError_t launch_resident(int n, const ResArgs& a, const ResCfg& cfg, cudaStream_t s);
 cudaError_t configure_resident(int max_smem, const double* ctw);
 
+// Plane passes of the FP32 CG iteration on N0 x N x N grids (hg_plane.cu):
+// one CTA per (load, axis-0 plane, component), the axis-1 and axis-2
+// transforms in shared memory; the spectrum in the pass kernels' layout.
+bool plane_supported(const GridDev& g);
+long long plane_units(const GridDev& g);        // CTAs per load (reduction slots)
+cudaError_t launch_plane_fwd(const GridDev& g, const void* tw, const RowFwdArgs& a, cudaStream_t s);
+cudaError_t launch_plane_inv(const GridDev& g, const void* tw, const RowInvArgs& a, cudaStream_t s);
+cudaError_t launch_plane_fwd_batch(const GridDev& g, const void* tw, const RowFwdArgs* items, int P, int L,
+                                   cudaStream_t s);
+cudaError_t launch_plane_inv_batch(const GridDev& g, const void* tw, const RowInvArgs* items, int P, int L,
+                                   cudaStream_t s);
+cudaError_t configure_plane(const double* ctw);
+
 // Launchers (prec: 0 = double, 1 = float).  Return cudaGetLastError().
 cudaError_t launch_row_fwd(int prec, const GridDev& g, const AxisPlanH& pl, const void* tw,
                            const RowCfg& cfg, const RowFwdArgs& a, cudaStream_t s);

@@ -320,7 +320,8 @@ cudaError_t configure_kernels(int max_smem) {
     cudaError_t e = configure_f64(max_smem, ctw);
     cudaError_t e2 = configure_f32(max_smem, ctw);
     cudaError_t e3 = configure_resident(max_smem, ctw);
-    return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3);
+    cudaError_t e4 = configure_plane(ctw);
+    return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e4));
 }
 
 cudaError_t launch_row_fwd(int prec, const GridDev& g, const AxisPlanH& pl, const void* tw,

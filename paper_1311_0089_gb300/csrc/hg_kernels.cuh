@@ -310,6 +310,53 @@ constexpr int MAX_REAL_ROWS = 64;
 // 2D, 4 in 3D (ct_max_lanes in hg_internal.h, shared with the host's choice).
 static_assert(CT_THREADS == CT_THREADS_HOST, "host launch geometry and device tiling disagree");
 
+// The step of a CG iteration from val = (p, A p) (the last CTA of the forward
+// pass, thread 0): alpha = (r, r) / (p, A p) (Sec. 5.3, Eq. CG_identity);
+// Moulinec-Suquet takes the fixed step 1 / lambda.
+__device__ __forceinline__ void fwd_cg_scalars(Scalars& s, double val) {
+    s.pt = val;
+    if (s.fixed_alpha > 0.0 && s.rr == 0.0) {
+        // Moulinec-Suquet reached the fixed point exactly: the step from r = 0
+        // is zero
+        s.status = ST_CONVERGED;
+        s.alpha = 0.0;
+    } else if (!(val > 0.0) || !isfinite(val)) {
+        s.status = ST_BREAKDOWN;
+        s.alpha = 0.0;
+    } else {
+        s.alpha = s.fixed_alpha > 0.0 ? s.fixed_alpha : s.rr / val;
+    }
+    s.alpha_f = (float)s.alpha;
+}
+
+// The end of a CG iteration from rr = (r, r) of the updated residual (the last
+// CTA of the inverse pass, thread 0): iteration count, relative residual,
+// stopping tests, beta = (r, r) / (r, r)_old.
+__device__ __forceinline__ void inv_cg_scalars(Scalars& s, double rr) {
+    s.iters += 1;
+    s.total_iters += 1;
+    const double rel = sqrt(rr) / s.bnorm;
+    s.relres = rel;
+    // Moulinec-Suquet stops on the step just taken, x_{i+1} - x_i = r_i /
+    // lambda, i.e. on the residual before this update (the tolerance was
+    // rescaled by lambda / ||b|| at the right-hand side)
+    const double crit = s.fixed_alpha > 0.0 ? sqrt(s.rr) / s.bnorm : rel;
+    if (!isfinite(rr)) s.status = ST_BREAKDOWN;
+    else if (crit <= s.tol) s.status = ST_CONVERGED;
+    else if (s.iters >= s.max_iter) s.status = ST_MAXITER;
+    if (s.stall_max > 0 && s.status == ST_ACTIVE) {
+        if (rr < 0.25 * s.best_rr) {
+            s.best_rr = rr;
+            s.stall = 0;
+        } else if (++s.stall >= s.stall_max) {
+            s.status = ST_STAGNATED;
+        }
+    }
+    s.beta = s.fixed_alpha > 0.0 ? 0.0 : rr / s.rr;   // MS: p = r
+    s.beta_f = (float)s.beta;
+    s.rr = rr;
+}
+
 // Offset of the half-spectrum row of real row rr (-1: none) for a row tile:
 // real row rr = (rowi * nl + li) * D + al holds component al of load l0 + li
 // on spatial row row0 + rowi.
@@ -521,21 +568,7 @@ __device__ __forceinline__ void row_fwd_body(GridDev g, AxisPlanH pl, const Cx<T
             const double val = tot[l] * g.invM;
             if (a.mode == FWD_CG) {
                 if (a.check_status && s.status != ST_ACTIVE) continue;
-                s.pt = val;
-                if (s.fixed_alpha > 0.0 && s.rr == 0.0) {
-                    // Moulinec-Suquet reached the fixed point exactly: the step
-                    // from r = 0 is zero
-                    s.status = ST_CONVERGED;
-                    s.alpha = 0.0;
-                } else if (!(val > 0.0) || !isfinite(val)) {
-                    s.status = ST_BREAKDOWN;
-                    s.alpha = 0.0;
-                } else {
-                    // CG: alpha = (r, r) / (p, A p); Moulinec-Suquet: the step
-                    // of the reference medium, 1 / lambda
-                    s.alpha = s.fixed_alpha > 0.0 ? s.fixed_alpha : s.rr / val;
-                }
-                s.alpha_f = (float)s.alpha;
+                fwd_cg_scalars(s, val);
             } else {
                 s.aen = sqrt(val);
             }
@@ -933,28 +966,7 @@ __device__ __forceinline__ void row_inv_body(GridDev g, AxisPlanH pl, const Cx<T
             if (a.check_status && s.status != ST_ACTIVE) continue;
             const double rr = tot[l] * g.invM;
             if (a.mode == INV_CG) {
-                s.iters += 1;
-                s.total_iters += 1;
-                const double rel = sqrt(rr) / s.bnorm;
-                s.relres = rel;
-                // Moulinec-Suquet stops on the step just taken, x_{i+1} - x_i =
-                // r_i / lambda, i.e. on the residual before this update (the
-                // tolerance was rescaled by lambda / ||b|| at the right-hand side)
-                const double crit = s.fixed_alpha > 0.0 ? sqrt(s.rr) / s.bnorm : rel;
-                if (!isfinite(rr)) s.status = ST_BREAKDOWN;
-                else if (crit <= s.tol) s.status = ST_CONVERGED;
-                else if (s.iters >= s.max_iter) s.status = ST_MAXITER;
-                if (s.stall_max > 0 && s.status == ST_ACTIVE) {
-                    if (rr < 0.25 * s.best_rr) {
-                        s.best_rr = rr;
-                        s.stall = 0;
-                    } else if (++s.stall >= s.stall_max) {
-                        s.status = ST_STAGNATED;
-                    }
-                }
-                s.beta = s.fixed_alpha > 0.0 ? 0.0 : rr / s.rr;   // MS: p = r
-                s.beta_f = (float)s.beta;
-                s.rr = rr;
+                inv_cg_scalars(s, rr);
             } else if (a.mode == INV_RHS) {
                 s.rr = rr;
                 s.bnorm = sqrt(rr);

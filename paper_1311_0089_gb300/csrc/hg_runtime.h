@@ -56,6 +56,7 @@ struct GraphCache {
     int nkern = 0;
     int prof_pass = -1;   // pass bracketed by event records (-1: none)
     int form = 0;         // formulation captured (coefficients and projection)
+    int plane = 0;        // 3D plane passes captured
     int has_ref = 0;      // general reference medium captured, and its value
     double ref[9] = {0};
 };
@@ -86,6 +87,9 @@ struct hg_grid {
     // formulation the next enqueued work uses: 0 primal, 1 dual (coefficients
     // A^-1 and the projection onto J_N); set by every entry point that enqueues
     int form = 0;
+    // the FP32 CG iterations of the next enqueued work may run as the 3D plane
+    // passes (hg_plane.cu) where the grid allows them; set like `form`
+    bool use_plane = true;
     // general reference medium A0 of the next enqueued CG work (0: A0 = I); set
     // like `form`
     int has_ref = 0;
@@ -147,6 +151,7 @@ struct PassArgs {
     hgk::StrArgs sa[3];
     int nstr = 0;
     hgk::RowInvArgs ia;
+    int plane = 0;      // 1: fa / ia run as the 3D plane passes, sa[0] is the axis-0 pass
 };
 void cg_iteration_args(hg_grid* g, int prec, int L, PassArgs* pa);
 void matvec_args(hg_grid* g, int prec, int L, const void* u, bool unit_loads, bool withA,

@@ -143,6 +143,7 @@ static void worker(Scheduler* S) {
             size_t need;
             {
                 std::lock_guard<std::recursive_mutex> lk(S->ctx->mu);
+                if (R) t->g->use_plane = o.resident != 0;   // its shape in the batch
                 need = solve_bytes_needed(t->g, prec, R ? rolling_nbx(R, t->g) : 0);
             }
             int st = HG_ERR_NO_MEMORY;
