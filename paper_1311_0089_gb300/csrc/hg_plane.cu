@@ -37,7 +37,7 @@
 namespace hgk {
 
 constexpr int PLANE_D = 3;
-constexpr int PLANE_THREADS = 256;
+constexpr int PLANE_THREADS = 512;
 constexpr int PLANE_ALT_BYTES = 36000;   // group buffer budget
 
 template <typename Lst> struct Plan2;
@@ -163,7 +163,7 @@ __device__ __forceinline__ void plane_fwd_body(const GridDev& g, const float2* _
         // the global loads of UV voxels (6 UV floats and the phase bytes or
         // field entries) are all issued before any of them is used; the table
         // lookups follow
-        constexpr int UV = 8;
+        constexpr int UV = 4;
         const int mode = co.mode;
         const float* fld = static_cast<const float*>(co.field);
         const int code = al == 0 ? 0x430 : (al == 1 ? 0x513 : 0x254);   // packed 11,22,33,12,13,23
@@ -318,7 +318,7 @@ __device__ __forceinline__ void plane_inv_body(const GridDev& g, const float2* _
     if (act) {
         // the plane's spectrum [k1][k2] -> U[k1 H + k2]
         const float2* Sp = static_cast<const float2*>(a.S) + ((long long)(l * PLANE_D + al) * g.N[0] + i0) * NP;
-        constexpr int KB = 12;
+        constexpr int KB = 6;
         for (int i0s = tid; i0s < NP; i0s += KB * PLANE_THREADS) {
             float2 v[KB];
 #pragma unroll
@@ -369,7 +369,7 @@ __device__ __forceinline__ void plane_inv_body(const GridDev& g, const float2* _
         float* X = static_cast<float*>(a.x) + base;
         float* R = static_cast<float*>(a.r) + base;
         float* P = static_cast<float*>(a.p) + base;
-        constexpr int UV = 12;
+        constexpr int UV = 6;
         for (int e0 = tid; e0 < NN2; e0 += UV * PLANE_THREADS) {
             float xv[UV], rv[UV], pv[UV];
 #pragma unroll
