@@ -116,10 +116,11 @@ typedef struct {
     int max_outer;       /* HG_MIXED: refinement steps (default 30)            */
     int time_pass;       /* >= 0: time this pass with CUDA events inside the
                             captured graphs, in the first iteration of every
-                            chunk of check_every iterations (0 = first-axis
-                            forward pass, last = last-axis inverse pass, as in
-                            hg_time_pass); results in hg_result.pass_*.
-                            -1 (default): no timing.  check_every <= 64.      */
+                            chunk of check_every iterations (0 = the forward
+                            pass, last = the inverse pass (update), in launch
+                            order; hg_num_iter_passes passes); results in
+                            hg_result.pass_*.  -1 (default): no timing.
+                            check_every <= 64.                                 */
     int method;          /* hg_method (default HG_CG).  HG_MS needs the bounds
                             c_A, C_A: the first HG_MS solve after new
                             coefficients computes them on the device and
@@ -153,18 +154,24 @@ typedef struct {
                             75, 81, 135, 243, 375 or 729: run each inner FP32
                             solve as
                             ONE cooperative launch whose CTAs (one per SM) keep
-                            the residual and the search direction of their grid
-                            rows in shared memory for all its iterations, with
-                            bounded grid-wide barriers between the row, column
-                            and row phases of an iteration.  -1 (default): when
-                            the state fits on chip; 0: never (the pass kernels,
-                            check_every iterations per CUDA graph); > 0: with at
+                            the residual, the search direction and the iterate
+                            of their grid rows in tensor memory for all its
+                            iterations, with bounded grid-wide barriers between
+                            the row, column and row phases of an iteration
+                            (hg_solve_AH only; hg_submit and hg_solve_batch run
+                            the pass kernels there).  On N0 x N x N grids with
+                            N in {15, 27, 45, 81, 135} and A0 = I, each FP32
+                            iteration is the three plane passes (axes 1 and 2
+                            transformed in shared memory, one CTA per plane and
+                            component), in every entry point.  -1 (default):
+                            where they apply and the state fits; 0: never (the
+                            pass kernels, check_every iterations per CUDA
+                            graph); > 0: as -1, the resident launch with at
                             most that many CTAs.  The iterates equal those of
                             the pass kernels up to the rounding of the partial
-                            sums.  time_pass >= 0 then times that launch (one
-                            per inner solve).  hg_solve_AH only: hg_submit and
-                            hg_solve_batch run the pass kernels.  A barrier wait
-                            that gives up returns HG_ERR_DEVICE_TIMEOUT.       */
+                            sums.  time_pass >= 0 times the resident launch
+                            (one per inner solve) or a plane pass.  A barrier
+                            wait that gives up returns HG_ERR_DEVICE_TIMEOUT. */
 } hg_solve_opts;
 
 typedef struct {
@@ -410,6 +417,11 @@ long long hg_launch_count(hg_ctx* ctx);
 int hg_time_pass(hg_grid* grid, int prec, int pass, int reps, double* ms_out,
                  char* name_out);
 int hg_num_passes(hg_grid* grid);
+/* Launches of one CG iteration of a solve of `grid` with `opts` (null: the
+ * defaults): the valid range of opts->time_pass.  3 where the FP32 iteration
+ * runs as the plane passes (see hg_solve_opts.resident), else the pass
+ * kernels' d + 1.  Negative status on a null grid. */
+int hg_num_iter_passes(hg_grid* grid, const hg_solve_opts* opts);
 
 const char* hg_strerror(int status);
 

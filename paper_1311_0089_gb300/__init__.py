@@ -133,6 +133,7 @@ SIGNATURES = [
     ("hg_launch_count", ctypes.c_longlong, [_VP]),
     ("hg_time_pass", _I, [_VP, _I, _I, _I, ctypes.POINTER(_D), ctypes.c_char_p]),
     ("hg_num_passes", _I, [_VP]),
+    ("hg_num_iter_passes", _I, [_VP, ctypes.POINTER(SolveOpts)]),
     ("hg_solve_batch", _I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(SolveOpts), ctypes.POINTER(Result)]),
     ("hg_get_launch_cfg", _I, [_VP, _I, ctypes.POINTER(LaunchCfg)]),
     ("hg_set_launch_cfg", _I, [_VP, _I, ctypes.POINTER(LaunchCfg)]),
@@ -417,6 +418,13 @@ class Grid:
 
     def num_passes(self) -> int:
         return int(load().hg_num_passes(self.h))
+
+    def num_iter_passes(self, opts: Optional["SolveOpts"] = None) -> int:
+        o = opts if opts is not None else default_opts()
+        n = int(load().hg_num_iter_passes(self.h, ctypes.byref(o)))
+        if n < 0:
+            raise HGError(n, "hg_num_iter_passes")
+        return n
 
     def time_pass(self, pass_idx: int, prec: int = HG_FP64, reps: int = 20):
         ms = ctypes.c_double()

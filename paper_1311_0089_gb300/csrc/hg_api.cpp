@@ -980,7 +980,7 @@ int job_begin(Job& j) {
     if (j.prec == 1 && (st = grid_alloc_work(g, 1))) return st;
     g->form = j.o.formulation == HG_DUAL ? 1 : 0;
     g->has_ref = j.o.A0[0] != 0.0 ? 1 : 0;
-    g->use_plane = j.o.resident != 0 && j.o.time_pass < 0;
+    g->use_plane = j.o.resident != 0;
     j.zscale = 1.0;
     for (int i = 0; i < 9; ++i) g->ref[i] = g->has_ref && i < gd.d * gd.d ? j.o.A0[i] : 0.0;
     if (g->has_ref) {

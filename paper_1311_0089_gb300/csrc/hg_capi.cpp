@@ -553,7 +553,7 @@ int hg_solve_AH(hg_grid* g, const hg_solve_opts* opts, double* AH_out, hg_result
     if (opts) o = *opts; else hg_default_opts(&o);
     const int vst = validate_solve_opts(g, &o);
     if (vst) return vst;
-    if (o.time_pass >= hg_num_passes(g) || (o.time_pass >= 0 && o.check_every > hgrt::MAX_PROF_CHUNK))
+    if (o.time_pass >= hg_num_iter_passes(g, &o) || (o.time_pass >= 0 && o.check_every > hgrt::MAX_PROF_CHUNK))
         return HG_ERR_ARG;
     if (g->borrowed.load() > 0) return HG_ERR_BUSY;
     hg_ctx* c = g->ctx;
@@ -666,6 +666,16 @@ int hg_spectrum(hg_grid* g, const double* u, double* S_out, int prec, int on_dev
 }
 
 int hg_num_passes(hg_grid* g) { return g ? (g->gd.d == 2 ? 3 : 5) : -1; }
+
+int hg_num_iter_passes(hg_grid* g, const hg_solve_opts* opts) {
+    if (!g) return HG_ERR_ARG;
+    hg_solve_opts o;
+    if (opts) o = *opts; else hg_default_opts(&o);
+    // the conditions of plane_path() that a solve's options decide (the
+    // reduction slots always hold a plane launch's CTAs)
+    const bool plane = o.prec == HG_MIXED && o.resident != 0 && o.A0[0] == 0.0 && plane_supported(g->gd);
+    return plane ? 3 : hg_num_passes(g);
+}
 
 int hg_time_pass(hg_grid* g, int prec, int pass, int reps, double* ms_out, char* name_out) {
     if (!g || !ms_out || reps < 1 || (prec != HG_FP64 && prec != HG_MIXED)) return HG_ERR_ARG;

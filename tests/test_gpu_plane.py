@@ -148,3 +148,25 @@ def test_plane_scheduler_alone_and_in_a_mix(hg, ctx):
     assert rel_max(alone[0]["AH"], ref["AH"]) < 1e-6
     for g in grids:
         g.close()
+
+
+def test_plane_time_pass_and_pass_count(hg, ctx):
+    """hg_num_iter_passes gives the schedule's launches per iteration (3 for
+    the plane passes, the pass kernels' 5 otherwise), and time_pass brackets
+    each of the three plane launches without changing the result."""
+    N = (27, 27, 27)
+    ms = _balls(N, seed=11)
+    g = ctx.grid(N)
+    g.set_coeffs_phase(ms.phase, ms.table)
+    o = hg.default_opts(tol=1e-8, prec=hg.HG_MIXED)
+    assert g.num_iter_passes(o) == 3
+    assert g.num_iter_passes(hg.default_opts(tol=1e-8, prec=hg.HG_MIXED, resident=0)) == 5
+    assert g.num_iter_passes(hg.default_opts(tol=1e-8, prec=hg.HG_FP64)) == 5
+    base = g.solve(o)
+    for p in range(3):
+        r = g.solve(hg.default_opts(tol=1e-8, prec=hg.HG_MIXED, time_pass=p))
+        assert r["status"] == 0 and r["pass_launches"] > 0 and r["pass_ms_total"] > 0.0
+        assert np.array_equal(r["AH"], base["AH"])
+    with pytest.raises(hg.HGError):
+        g.solve(hg.default_opts(tol=1e-8, prec=hg.HG_MIXED, time_pass=3))
+    g.close()
