@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--batch-once", action="store_true",
                     help="batched workload: tune, one warm-up and one timed hg_solve_batch call only, "
                          "printing the kernel launches made before the timed call (an ncu -s value)")
+    ap.add_argument("--solves-once", type=int, default=0,
+                    help="c2 / c3: only this many mixed solves of the workload at the bench's settings "
+                         "(default launch geometry, no timing): the command ncu captures are taken on")
     ap.add_argument("--passes-once", action="store_true",
                     help="launch every CG pass twice (FP32 then FP64) on the workload and exit "
                          "(a short command for ncu captures)")
@@ -798,6 +801,24 @@ def sub_batched(hg, torch, dev, args):
     return out
 
 
+def run_solves_once(args):
+    """args.solves_once mixed solves of the c2 or c3 workload, nothing else."""
+    import paper_1311_0089_gb300 as hg
+    hg.load()
+    ms, _ = workload(args.workload if args.workload in ("c2", "c3") else "c2")
+    ctx = hg.Context(0)
+    g = ctx.grid(ms.N)
+    g.set_coeffs_phase(ms.phase, ms.table)
+    o = hg.default_opts(tol=args.tol, prec=hg.HG_MIXED, inner_tol=max(0.5 * args.tol, 1e-6))
+    for _ in range(args.solves_once):
+        r = g.solve(o)
+    print(json.dumps({"iters": list(r["iters"]), "device_ms": r["device_ms"],
+                      "resident_ctas": r["resident_ctas"]}))
+    g.close()
+    ctx.close()
+    return 0
+
+
 def run_passes_once(args):
     import torch
     import paper_1311_0089_gb300 as hg
@@ -1304,6 +1325,8 @@ def run_batch_once(args):
 
 def main():
     args = parse()
+    if args.solves_once > 0:
+        return run_solves_once(args)
     if args.passes_once:
         return run_passes_once(args)
     if args.batch_once:
