@@ -38,7 +38,7 @@ namespace hgk {
 
 constexpr int PLANE_D = 3;
 constexpr int PLANE_THREADS = 512;
-constexpr int PLANE_ALT_BYTES = 36000;   // group buffer budget
+constexpr int PLANE_ALT_BYTES = 36720;   // group buffer budget (two groups of 34 pencils at N = 135)
 
 template <typename Lst> struct Plan2;
 template <int R1> struct Plan2<RadixList<R1>> { static constexpr int r1 = R1, r2 = 1, nst = 1; };
