@@ -31,8 +31,7 @@
 // X_i1(k2) at U[i1 H + k2]), and a group buffer of G pencils: each transform
 // runs its out-of-place stages group by group through it and ends in U.
 // About 112 KB for N = 135 (two groups of 34 pencils), so that two CTAs share
-// an SM and the loads of one
-// overlap the transforms of the other.
+// an SM and the loads of one overlap the transforms of the other.
 #include "hg_pencil.cuh"
 
 namespace hgk {
