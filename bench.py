@@ -254,10 +254,26 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_source_hash():
+# the source files each profiled kernel is compiled from (traffic figures stay
+# valid while these are unchanged)
+KERNEL_SOURCES = {
+    "resident": ("hg_resident.cu", "hg_pencil.cuh", "hg_kernels.cuh", "fft_device.cuh"),
+    "plane": ("hg_plane.cu", "hg_pencil.cuh", "hg_kernels.cuh", "fft_device.cuh"),
+    "passes": ("hg_kernels.cuh", "hg_kernels.cu", "fft_device.cuh"),
+}
+
+
+def kernel_family(kernel_key):
+    if "resident" in kernel_key:
+        return "resident"
+    if "plane" in kernel_key:
+        return "plane"
+    return "passes"
+
+
+def kernel_source_hash(family="passes"):
     h = hashlib.sha256()
-    for f in ("hg_kernels.cuh", "hg_kernels.cu", "fft_device.cuh", "hg_resident.cu", "hg_pencil.cuh",
-              "hg_plane.cu"):
+    for f in KERNEL_SOURCES[family]:
         with open(os.path.join(ROOT, "paper_1311_0089_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -270,7 +286,7 @@ def profiled_traffic(kernel_key, geometry=None):
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         ent = t.get(kernel_key)
-        if ent and ent.get("kernel_source_sha") == kernel_source_hash():
+        if ent and ent.get("kernel_source_sha") == kernel_source_hash(kernel_family(kernel_key)):
             if geometry is not None and ent.get("launch_geometry") not in (None, geometry):
                 return None
             return ent["dram_bytes_per_launch"]
