@@ -661,6 +661,7 @@ def run_ours(args):
         # beside the headline (each with its own clocks and plain-FP64 comparison)
         line["c3"] = sub_c3(hg, torch, dev, args)
         line["batched"] = sub_batched(hg, torch, dev, args)
+        line["serving"] = sub_serving(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     g.close()
@@ -992,7 +993,7 @@ def run_batched(args):
 # ----------------------------------------------------------------------------
 # serving: Poisson arrivals, admission by memory, continuous batching
 # ----------------------------------------------------------------------------
-def run_serving(args):
+def serving_line(args, rate_offered, duration, rate_search):
     """Poisson request stream through hg_submit / hg_poll (cross-request batched
     ticks).  The offered rate (default 200/s) for the full window, then, with
     --rate-search, shorter windows at lower rates down to the highest rate the
@@ -1080,7 +1081,7 @@ def run_serving(args):
                            "max": float(lat.max()), "p99_first_third": p99_first, "p99_last_third": p99_last},
             "p99_flat": flat, "clocks": clocks}
 
-    reqs, done, main = serve(args.rate, args.duration)
+    reqs, done, main = serve(rate_offered, duration)
     # same result alone and in the mix: the same requests again, one at a time
     diffs = []
     rng = np.random.default_rng(3)
@@ -1091,9 +1092,9 @@ def run_serving(args):
         alone = ctx.poll(ctx.submit(g, o_mixed), timeout_us=-1)["AH"]
         diffs.append(float(np.max(np.abs(alone - out["AH"])) / np.max(np.abs(alone))))
     search = []
-    if args.rate_search:
+    if rate_search:
         for k, rate in enumerate((150.0, 100.0, 75.0, 60.0, 50.0, 40.0, 30.0, 20.0)):
-            if rate >= args.rate:
+            if rate >= rate_offered:
                 continue
             _, _, row = serve(rate, 15.0, seed_off=k + 1)
             search.append(row)
@@ -1123,7 +1124,7 @@ def run_serving(args):
                                "{81^2,243^2,729^2,27^3,45^3,81^3,135^3}, balls to vf 0.2, contrast "
                                "log-uniform [10,1e3], rel. residual %g; %d grids per size as slots; "
                                "memory budget %g GiB; cross-request batched ticks"
-                               % (args.rate, args.duration, args.tol, POOL, args.budget_gib)},
+                               % (rate_offered, duration, args.tol, POOL, args.budget_gib)},
         "offered": main,
         "sustained": sustained,
         "rate_search": search,
@@ -1133,12 +1134,28 @@ def run_serving(args):
         "alone_vs_mix_max_rel_diff": max(diffs) if diffs else None,
         "clocks": main["clocks"],
     }
-    print(json.dumps(line), flush=True)
     for gs in free.values():
         for g in gs:
             g.close()
     ctx.close()
+    return line
+
+
+def run_serving(args):
+    print(json.dumps(serving_line(args, args.rate, args.duration, args.rate_search)), flush=True)
     return 0
+
+
+def sub_serving(args):
+    """A 15 s Poisson window at 60 requests/s (the highest offered rate whose p99
+    latency stays flat in the full serving run) through the scheduler."""
+    line = serving_line(args, 60.0, 15.0, False)
+    main = line["offered"]
+    return {"config": line["config"], "solves_per_s": main["solves_per_s"], "offered_rate": main["offered_rate"],
+            "requests": main["requests"], "ok": main["ok"], "latency_ms": main["latency_ms"],
+            "p99_flat": main["p99_flat"], "plain_fp64_per_request": line["plain_fp64_per_request"],
+            "speedup_vs_plain_fp64": line["speedup_vs_plain_fp64"],
+            "alone_vs_mix_max_rel_diff": line["alone_vs_mix_max_rel_diff"], "clocks": main["clocks"]}
 
 
 # ----------------------------------------------------------------------------
