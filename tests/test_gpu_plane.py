@@ -37,9 +37,10 @@ def _launches_per_iter(r):
     return r["launches"] / max(1, max(r["iters"]))
 
 
-# cubic and N0 != N1 = N2 grids of every plane length (N odd, H odd and even)
+# cubic and N0 != N1 = N2 grids of every plane length (N odd, H odd and even);
+# N0 = 21 and 35 take the run-time FFT plan in the axis-0 pass
 @pytest.mark.parametrize("N", [(15, 15, 15), (27, 27, 27), (45, 45, 45), (81, 27, 27), (27, 45, 45),
-                               (45, 81, 81), (15, 135, 135)])
+                               (45, 81, 81), (15, 135, 135), (21, 27, 27), (35, 45, 45)])
 def test_plane_matches_oracle_and_pass_kernels(hg, ctx, N):
     ms = _balls(N, seed=sum(N))
     ref = O.solve_AH(ms.full_field(), ms.N, tol=1e-12)
