@@ -37,7 +37,13 @@
 namespace hgk {
 
 constexpr int PLANE_D = 3;
-constexpr int PLANE_THREADS = 512;
+// Threads and CTAs per SM of a plane launch (measured per length): N >= 81
+// two CTAs of 512 threads; smaller planes four CTAs of 256 (64 registers
+// either way)
+template <int N> struct PlaneCfg {
+    static constexpr int threads = N >= 81 ? 512 : 256;
+    static constexpr int blocks = N >= 81 ? 2 : 4;
+};
 constexpr int PLANE_ALT_BYTES = 36720;   // group buffer budget (two groups of 34 pencils at N = 135)
 
 template <typename Lst> struct Plan2;
@@ -59,13 +65,13 @@ template <int N> struct PlaneGeo {
 // pencil p at src[p sps + m ses] -> dst[p dps + m des] (the stage's output
 // order).  PEN_FAST: consecutive threads take consecutive pencils (strided
 // pencils); else consecutive butterflies of one pencil.  tw: [r-1][k], k < NS.
-template <int N, int R, int NS, bool PEN_FAST>
+template <int N, int R, int NS, bool PEN_FAST, int TH = PlaneCfg<N>::threads>
 __device__ __forceinline__ void pstage(const float2* __restrict__ src, int sps, int ses, float2* __restrict__ dst,
                                        int dps, int des, int npen, const float2* __restrict__ tw) {
     constexpr int NB = N / R;
     const int total = npen * NB;
 #pragma unroll 1
-    for (int idx = threadIdx.x; idx < total; idx += PLANE_THREADS) {
+    for (int idx = threadIdx.x; idx < total; idx += TH) {
         int pen, j;
         if (PEN_FAST) { j = idx / npen; pen = idx - j * npen; }
         else { pen = idx / NB; j = idx - pen * NB; }
@@ -100,7 +106,7 @@ __device__ __noinline__ void plane_ifft(float2* U, int ps, int es, int npen, flo
         if constexpr (Q::P::nst == 2) {
             pstage<N, Q::P::r2, Q::P::r1, PEN_FAST>(alt, N, 1, Ug, ps, es, ng, tws);
         } else {
-            for (int i = threadIdx.x; i < ng * N; i += PLANE_THREADS) {
+            for (int i = threadIdx.x; i < ng * N; i += PlaneCfg<N>::threads) {
                 const int pn = i / N, m = i - pn * N;
                 Ug[pn * ps + m * es] = alt[i];
             }
@@ -120,7 +126,7 @@ template <int N, typename Args>
 __device__ __forceinline__ void plane_fwd_body(const GridDev& g, const float2* __restrict__ tw_nat, Args a,
                                                TileIdx ti) {
     typedef PlaneGeo<N> Q;
-    constexpr int H = Q::H, W = Q::W, NP = Q::NP, NN2 = N * N;
+    constexpr int H = Q::H, W = Q::W, NP = Q::NP, NN2 = N * N, PT = PlaneCfg<N>::threads;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* U = reinterpret_cast<float2*>(smem_raw);
     float2* alt = U + Q::UCX;
@@ -170,12 +176,12 @@ __device__ __forceinline__ void plane_fwd_body(const GridDev& g, const float2* _
         const long long o0 = (long long)(code & 15) * M, o1 = (long long)((code >> 4) & 15) * M,
                         o2 = (long long)((code >> 8) & 15) * M;
         const int nph1 = co.n_phases - 1;
-        for (int e0 = tid; e0 < NN2; e0 += UV * PLANE_THREADS) {
+        for (int e0 = tid; e0 < NN2; e0 += UV * PT) {
             float rv[UV][PLANE_D], pv[UV][PLANE_D], fv[UV][PLANE_D];
             int ph[UV];
 #pragma unroll
             for (int u = 0; u < UV; ++u) {
-                const int e = min(e0 + u * PLANE_THREADS, NN2 - 1);   // (a clamped index is loaded, not used)
+                const int e = min(e0 + u * PT, NN2 - 1);   // (a clamped index is loaded, not used)
                 ph[u] = 0;
                 fv[u][0] = fv[u][1] = fv[u][2] = 0.f;
                 if (mode == 0) {
@@ -193,7 +199,7 @@ __device__ __forceinline__ void plane_fwd_body(const GridDev& g, const float2* _
             }
 #pragma unroll
             for (int u = 0; u < UV; ++u) {
-                const int e = e0 + u * PLANE_THREADS;
+                const int e = e0 + u * PT;
                 if (e >= NN2) break;
                 float ar[PLANE_D];
                 if (mode == 0) {
@@ -217,7 +223,7 @@ __device__ __forceinline__ void plane_fwd_body(const GridDev& g, const float2* _
             }
         }
         // N is odd: the last packed row holds one grid row
-        for (int i2 = tid; i2 < N; i2 += PLANE_THREADS) U[(H - 1) * W + i2].y = 0.f;
+        for (int i2 = tid; i2 < N; i2 += PT) U[(H - 1) * W + i2].y = 0.f;
     }
     __syncthreads();
     if (act) {
@@ -225,13 +231,13 @@ __device__ __forceinline__ void plane_fwd_body(const GridDev& g, const float2* _
         plane_ifft<N, false>(U, W, 1, H, alt, tws);
         // split each pair in place: row j becomes conj X_2j(k2), k2 < H, then
         // conj X_2j+1(k2), i.e. conj X_i1(k2) at U[i1 H + k2]
-        constexpr int RCH = (4 * PLANE_THREADS) / H > 0 ? (4 * PLANE_THREADS) / H : 1;
+        constexpr int RCH = (4 * PT) / H > 0 ? (4 * PT) / H : 1;
         for (int j0 = 0; j0 < H; j0 += RCH) {
             const int nit = min(RCH, H - j0) * H;
             float2 xe[4], xo[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int it = tid + q * PLANE_THREADS;
+                const int it = tid + q * PT;
                 if (it < nit) {
                     const int j = j0 + it / H, k = it % H;
                     const float2 y1 = U[j * W + k];
@@ -243,7 +249,7 @@ __device__ __forceinline__ void plane_fwd_body(const GridDev& g, const float2* _
             __syncthreads();
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int it = tid + q * PLANE_THREADS;
+                const int it = tid + q * PT;
                 if (it < nit) {
                     const int j = j0 + it / H, k = it % H;
                     U[j * W + k] = xe[q];
@@ -257,7 +263,7 @@ __device__ __forceinline__ void plane_fwd_body(const GridDev& g, const float2* _
         plane_ifft<N, true>(U, 1, H, H, alt, tws);
         grid_dep_launch();
         float2* Sp = static_cast<float2*>(a.S) + ((long long)(l * PLANE_D + al) * g.N[0] + i0) * NP;
-        for (int i = tid; i < NP; i += PLANE_THREADS) {
+        for (int i = tid; i < NP; i += PT) {
             const float2 q = U[i];
             Sp[i] = make_float2(q.x, -q.y);
         }
@@ -289,7 +295,7 @@ template <int N, typename Args>
 __device__ __forceinline__ void plane_inv_body(const GridDev& g, const float2* __restrict__ tw_nat, Args a,
                                                TileIdx ti) {
     typedef PlaneGeo<N> Q;
-    constexpr int H = Q::H, W = Q::W, NP = Q::NP, NN2 = N * N;
+    constexpr int H = Q::H, W = Q::W, NP = Q::NP, NN2 = N * N, PT = PlaneCfg<N>::threads;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* U = reinterpret_cast<float2*>(smem_raw);
     float2* alt = U + Q::UCX;
@@ -319,13 +325,13 @@ __device__ __forceinline__ void plane_inv_body(const GridDev& g, const float2* _
         // the plane's spectrum [k1][k2] -> U[k1 H + k2]
         const float2* Sp = static_cast<const float2*>(a.S) + ((long long)(l * PLANE_D + al) * g.N[0] + i0) * NP;
         constexpr int KB = 6;
-        for (int i0s = tid; i0s < NP; i0s += KB * PLANE_THREADS) {
+        for (int i0s = tid; i0s < NP; i0s += KB * PT) {
             float2 v[KB];
 #pragma unroll
-            for (int u = 0; u < KB; ++u) v[u] = __ldcg(Sp + min(i0s + u * PLANE_THREADS, NP - 1));
+            for (int u = 0; u < KB; ++u) v[u] = __ldcg(Sp + min(i0s + u * PT, NP - 1));
 #pragma unroll
             for (int u = 0; u < KB; ++u) {
-                const int i = i0s + u * PLANE_THREADS;
+                const int i = i0s + u * PT;
                 if (i < NP) U[i] = v[u];
             }
         }
@@ -335,13 +341,13 @@ __device__ __forceinline__ void plane_inv_body(const GridDev& g, const float2* _
         // rows 2j, 2j + 1 as one complex row Z = X_2j + i X_2j+1 over all k2
         // (X(k2) = conj X(N - k2) for k2 >= H), in place: row j of U (stride W)
         // holds X_2j then X_2j+1, and receives Z_j
-        constexpr int RCH = (4 * PLANE_THREADS) / H > 0 ? (4 * PLANE_THREADS) / H : 1;
+        constexpr int RCH = (4 * PT) / H > 0 ? (4 * PT) / H : 1;
         for (int j0 = 0; j0 < H; j0 += RCH) {
             const int nit = min(RCH, H - j0) * H;
             float2 xe[4], xo[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int it = tid + q * PLANE_THREADS;
+                const int it = tid + q * PT;
                 if (it < nit) {
                     const int j = j0 + it / H, k = it % H;
                     xe[q] = U[j * W + k];
@@ -351,7 +357,7 @@ __device__ __forceinline__ void plane_inv_body(const GridDev& g, const float2* _
             __syncthreads();
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int it = tid + q * PLANE_THREADS;
+                const int it = tid + q * PT;
                 if (it < nit) {
                     const int j = j0 + it / H, k = it % H;
                     // Z(k) = Xe + i Xo;  Z(N - k) = conj(Xe) + i conj(Xo)
@@ -370,18 +376,18 @@ __device__ __forceinline__ void plane_inv_body(const GridDev& g, const float2* _
         float* R = static_cast<float*>(a.r) + base;
         float* P = static_cast<float*>(a.p) + base;
         constexpr int UV = 6;
-        for (int e0 = tid; e0 < NN2; e0 += UV * PLANE_THREADS) {
+        for (int e0 = tid; e0 < NN2; e0 += UV * PT) {
             float xv[UV], rv[UV], pv[UV];
 #pragma unroll
             for (int u = 0; u < UV; ++u) {
-                const int e = min(e0 + u * PLANE_THREADS, NN2 - 1);   // (a clamped index is loaded, not used)
+                const int e = min(e0 + u * PT, NN2 - 1);   // (a clamped index is loaded, not used)
                 xv[u] = __ldcg(X + e);
                 rv[u] = __ldcg(R + e);
                 pv[u] = __ldcg(P + e);
             }
 #pragma unroll
             for (int u = 0; u < UV; ++u) {
-                const int e = e0 + u * PLANE_THREADS;
+                const int e = e0 + u * PT;
                 if (e >= NN2) break;
                 const int i1 = e / N, i2 = e - i1 * N;
                 const float2 qz = U[(i1 >> 1) * W + i2];
@@ -415,23 +421,23 @@ __device__ __forceinline__ void plane_inv_body(const GridDev& g, const float2* _
 }
 
 template <int N>
-__global__ void __launch_bounds__(PLANE_THREADS, 2) k_plane_fwd(GridDev g, const float2* __restrict__ tw,
+__global__ void __launch_bounds__(PlaneCfg<N>::threads, PlaneCfg<N>::blocks) k_plane_fwd(GridDev g, const float2* __restrict__ tw,
                                                                 RowFwdArgs a) {
     plane_fwd_body<N>(g, tw, a, TileIdx::of_block());
 }
 template <int N>
-__global__ void __launch_bounds__(PLANE_THREADS, 2) k_plane_inv(GridDev g, const float2* __restrict__ tw,
+__global__ void __launch_bounds__(PlaneCfg<N>::threads, PlaneCfg<N>::blocks) k_plane_inv(GridDev g, const float2* __restrict__ tw,
                                                                 RowInvArgs a) {
     plane_inv_body<N>(g, tw, a, TileIdx::of_block());
 }
 // batched: grid z = problem (the arguments of problem z from items)
 template <int N>
-__global__ void __launch_bounds__(PLANE_THREADS, 2) k_plane_fwd_b(GridDev g, const float2* __restrict__ tw,
+__global__ void __launch_bounds__(PlaneCfg<N>::threads, PlaneCfg<N>::blocks) k_plane_fwd_b(GridDev g, const float2* __restrict__ tw,
                                                                   const RowFwdArgs* __restrict__ items) {
     plane_fwd_body<N, const RowFwdArgs&>(g, tw, stage_item(items, blockIdx.z), TileIdx::of_block());
 }
 template <int N>
-__global__ void __launch_bounds__(PLANE_THREADS, 2) k_plane_inv_b(GridDev g, const float2* __restrict__ tw,
+__global__ void __launch_bounds__(PlaneCfg<N>::threads, PlaneCfg<N>::blocks) k_plane_inv_b(GridDev g, const float2* __restrict__ tw,
                                                                   const RowInvArgs* __restrict__ items) {
     plane_inv_body<N, const RowInvArgs&>(g, tw, stage_item(items, blockIdx.z), TileIdx::of_block());
 }
@@ -452,13 +458,13 @@ bool plane_supported(const GridDev& g) {
 // Reduction slots a plane launch needs per load.
 long long plane_units(const GridDev& g) { return (long long)g.N[0] * PLANE_D; }
 
-// Plane launches: grid (N0 d, L[, P]), PLANE_THREADS threads, two CTAs per SM.
+// Plane launches: grid (N0 d, L[, P]), PlaneCfg threads.
 cudaError_t launch_plane_fwd(const GridDev& g, const void* tw, const RowFwdArgs& a, cudaStream_t s) {
     const dim3 grid((unsigned)plane_units(g), (unsigned)a.L);
     const float2* twp = static_cast<const float2*>(tw);
     cudaError_t le = cudaErrorInvalidConfiguration;
     switch (g.N[2]) {
-#define HG_PC(NV) case NV: le = launch_pdl(k_plane_fwd<NV>, grid, PLANE_THREADS, PlaneGeo<NV>::bytes, s, g, twp, a); break;
+#define HG_PC(NV) case NV: le = launch_pdl(k_plane_fwd<NV>, grid, PlaneCfg<NV>::threads, PlaneGeo<NV>::bytes, s, g, twp, a); break;
         HG_PLANE_SIZES(HG_PC)
 #undef HG_PC
         default: break;
@@ -471,7 +477,7 @@ cudaError_t launch_plane_inv(const GridDev& g, const void* tw, const RowInvArgs&
     const float2* twp = static_cast<const float2*>(tw);
     cudaError_t le = cudaErrorInvalidConfiguration;
     switch (g.N[2]) {
-#define HG_PC(NV) case NV: le = launch_pdl(k_plane_inv<NV>, grid, PLANE_THREADS, PlaneGeo<NV>::bytes, s, g, twp, a); break;
+#define HG_PC(NV) case NV: le = launch_pdl(k_plane_inv<NV>, grid, PlaneCfg<NV>::threads, PlaneGeo<NV>::bytes, s, g, twp, a); break;
         HG_PLANE_SIZES(HG_PC)
 #undef HG_PC
         default: break;
@@ -485,7 +491,7 @@ cudaError_t launch_plane_fwd_batch(const GridDev& g, const void* tw, const RowFw
     const float2* twp = static_cast<const float2*>(tw);
     cudaError_t le = cudaErrorInvalidConfiguration;
     switch (g.N[2]) {
-#define HG_PC(NV) case NV: le = launch_pdl(k_plane_fwd_b<NV>, grid, PLANE_THREADS, PlaneGeo<NV>::bytes, s, g, twp, items); break;
+#define HG_PC(NV) case NV: le = launch_pdl(k_plane_fwd_b<NV>, grid, PlaneCfg<NV>::threads, PlaneGeo<NV>::bytes, s, g, twp, items); break;
         HG_PLANE_SIZES(HG_PC)
 #undef HG_PC
         default: break;
@@ -499,7 +505,7 @@ cudaError_t launch_plane_inv_batch(const GridDev& g, const void* tw, const RowIn
     const float2* twp = static_cast<const float2*>(tw);
     cudaError_t le = cudaErrorInvalidConfiguration;
     switch (g.N[2]) {
-#define HG_PC(NV) case NV: le = launch_pdl(k_plane_inv_b<NV>, grid, PLANE_THREADS, PlaneGeo<NV>::bytes, s, g, twp, items); break;
+#define HG_PC(NV) case NV: le = launch_pdl(k_plane_inv_b<NV>, grid, PlaneCfg<NV>::threads, PlaneGeo<NV>::bytes, s, g, twp, items); break;
         HG_PLANE_SIZES(HG_PC)
 #undef HG_PC
         default: break;
