@@ -375,30 +375,58 @@ __device__ __forceinline__ void plane_inv_body(const GridDev& g, const float2* _
         float* X = static_cast<float*>(a.x) + base;
         float* R = static_cast<float*>(a.r) + base;
         float* P = static_cast<float*>(a.p) + base;
-        constexpr int UV = 6;
-        for (int e0 = tid; e0 < NN2; e0 += UV * PT) {
-            float xv[UV], rv[UV], pv[UV];
+        // one voxel: x += alpha v, r -= alpha q, p = v (v = r + beta p)
+        auto upd = [&](int e, float& xv, float& rv, float& pv) {
+            const int i1 = e / N, i2 = e - i1 * N;
+            const float2 qz = U[(i1 >> 1) * W + i2];
+            const float q = (i1 & 1) ? qz.y : qz.x;
+            const float v = rv + beta * pv;
+            xv = xv + alpha * v;
+            rv = rv - alpha * q;
+            pv = v;
+            tacc += rv * rv;
+        };
+        // x, r and p of the plane start at the same offset from their (aligned)
+        // buffers: the voxels up to a 16-byte boundary one by one, then groups
+        // of four as float4, then the rest one by one
+        const int head = (int)((4 - (base & 3)) & 3);
+        if (tid < head && tid < NN2) {
+            float xv = X[tid], rv = R[tid], pv = P[tid];
+            upd(tid, xv, rv, pv);
+            X[tid] = xv; R[tid] = rv; P[tid] = pv;
+        }
+        const int n4 = (NN2 - head) >> 2;
+        float4* X4 = reinterpret_cast<float4*>(X + head);
+        float4* R4 = reinterpret_cast<float4*>(R + head);
+        float4* P4 = reinterpret_cast<float4*>(P + head);
+        constexpr int UV4 = 2;
+        for (int g0 = tid; g0 < n4; g0 += UV4 * PT) {
+            float4 xv[UV4], rv[UV4], pv[UV4];
 #pragma unroll
-            for (int u = 0; u < UV; ++u) {
-                const int e = min(e0 + u * PT, NN2 - 1);   // (a clamped index is loaded, not used)
-                xv[u] = __ldcg(X + e);
-                rv[u] = __ldcg(R + e);
-                pv[u] = __ldcg(P + e);
+            for (int u = 0; u < UV4; ++u) {
+                const int gq = min(g0 + u * PT, n4 - 1);   // (a clamped index is loaded, not used)
+                xv[u] = __ldcg(X4 + gq);
+                rv[u] = __ldcg(R4 + gq);
+                pv[u] = __ldcg(P4 + gq);
             }
 #pragma unroll
-            for (int u = 0; u < UV; ++u) {
-                const int e = e0 + u * PT;
-                if (e >= NN2) break;
-                const int i1 = e / N, i2 = e - i1 * N;
-                const float2 qz = U[(i1 >> 1) * W + i2];
-                const float q = (i1 & 1) ? qz.y : qz.x;
-                const float v = rv[u] + beta * pv[u];
-                const float rn = rv[u] - alpha * q;
-                X[e] = xv[u] + alpha * v;
-                R[e] = rn;
-                P[e] = v;
-                tacc += rn * rn;
+            for (int u = 0; u < UV4; ++u) {
+                const int gq = g0 + u * PT;
+                if (gq >= n4) break;
+                const int e = head + 4 * gq;
+                upd(e, xv[u].x, rv[u].x, pv[u].x);
+                upd(e + 1, xv[u].y, rv[u].y, pv[u].y);
+                upd(e + 2, xv[u].z, rv[u].z, pv[u].z);
+                upd(e + 3, xv[u].w, rv[u].w, pv[u].w);
+                X4[gq] = xv[u];
+                R4[gq] = rv[u];
+                P4[gq] = pv[u];
             }
+        }
+        for (int e = head + 4 * n4 + tid; e < NN2; e += PT) {
+            float xv = X[e], rv = R[e], pv = P[e];
+            upd(e, xv, rv, pv);
+            X[e] = xv; R[e] = rv; P[e] = pv;
         }
     }
 
