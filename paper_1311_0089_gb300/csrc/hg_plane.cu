@@ -263,9 +263,19 @@ __device__ __forceinline__ void plane_fwd_body(const GridDev& g, const float2* _
         plane_ifft<N, true>(U, 1, H, H, alt, tws);
         grid_dep_launch();
         float2* Sp = static_cast<float2*>(a.S) + ((long long)(l * PLANE_D + al) * g.N[0] + i0) * NP;
-        for (int i = tid; i < NP; i += PT) {
-            const float2 q = U[i];
-            Sp[i] = make_float2(q.x, -q.y);
+        if constexpr (NP % 2 == 0) {
+            // an even plane size keeps every plane 16-byte aligned: two entries at a time
+            const float4* U4 = reinterpret_cast<const float4*>(U);
+            float4* S4 = reinterpret_cast<float4*>(Sp);
+            for (int i = tid; i < NP / 2; i += PT) {
+                const float4 q = U4[i];
+                S4[i] = make_float4(q.x, -q.y, q.z, -q.w);
+            }
+        } else {
+            for (int i = tid; i < NP; i += PT) {
+                const float2 q = U[i];
+                Sp[i] = make_float2(q.x, -q.y);
+            }
         }
     }
 
@@ -324,15 +334,32 @@ __device__ __forceinline__ void plane_inv_body(const GridDev& g, const float2* _
     if (act) {
         // the plane's spectrum [k1][k2] -> U[k1 H + k2]
         const float2* Sp = static_cast<const float2*>(a.S) + ((long long)(l * PLANE_D + al) * g.N[0] + i0) * NP;
-        constexpr int KB = 6;
-        for (int i0s = tid; i0s < NP; i0s += KB * PT) {
-            float2 v[KB];
+        if constexpr (NP % 2 == 0) {
+            // an even plane size keeps every plane 16-byte aligned: two entries at a time
+            constexpr int KB = 3, NP2 = NP / 2;
+            const float4* S4 = reinterpret_cast<const float4*>(Sp);
+            float4* U4 = reinterpret_cast<float4*>(U);
+            for (int i0s = tid; i0s < NP2; i0s += KB * PT) {
+                float4 v[KB];
 #pragma unroll
-            for (int u = 0; u < KB; ++u) v[u] = __ldcg(Sp + min(i0s + u * PT, NP - 1));
+                for (int u = 0; u < KB; ++u) v[u] = __ldcg(S4 + min(i0s + u * PT, NP2 - 1));
 #pragma unroll
-            for (int u = 0; u < KB; ++u) {
-                const int i = i0s + u * PT;
-                if (i < NP) U[i] = v[u];
+                for (int u = 0; u < KB; ++u) {
+                    const int i = i0s + u * PT;
+                    if (i < NP2) U4[i] = v[u];
+                }
+            }
+        } else {
+            constexpr int KB = 6;
+            for (int i0s = tid; i0s < NP; i0s += KB * PT) {
+                float2 v[KB];
+#pragma unroll
+                for (int u = 0; u < KB; ++u) v[u] = __ldcg(Sp + min(i0s + u * PT, NP - 1));
+#pragma unroll
+                for (int u = 0; u < KB; ++u) {
+                    const int i = i0s + u * PT;
+                    if (i < NP) U[i] = v[u];
+                }
             }
         }
         __syncthreads();
