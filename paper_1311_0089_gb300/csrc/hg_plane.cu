@@ -182,7 +182,9 @@ __device__ __forceinline__ void plane_fwd_body(const GridDev& g, const float2* _
         if (co.mode == 1) co.field = static_cast<const float*>(a.co.field) + pl0;
         // the plane's r and p (shared by the three CTAs of the plane: a third
         // each) and its coefficients into L2 ahead of the batched loads below
-        // (135^3 solve 85.7 -> 84.7 ms; at N <= 81 the hints cost 0.5-1.5%)
+        // (135^3: plane_fwd 169 -> 164 us; at N <= 81 the hints cost 0.5-1.5%
+        // of the solve.  The same hints for x, r, p at the start of plane_inv
+        // were evicted before its update: DRAM reads 355 -> 439 MB, slower)
         if constexpr (N >= 135) {
             for (int be = 0; be < PLANE_D; ++be) {
                 l2_prefetch(R0 + be * M, NN2 * 4, al, PLANE_D);
@@ -356,14 +358,6 @@ __device__ __forceinline__ void plane_inv_body(const GridDev& g, const float2* _
     const bool act = s_act;
     float tacc = 0.f;
     if (act) {
-        // x, r and p of the plane into L2 while the transforms run (the
-        // update at the end reads them); N >= 135 as in plane_fwd
-        if constexpr (N >= 135) {
-            const long long pbase = ((long long)(l * PLANE_D + al)) * M + (long long)i0 * NN2;
-            l2_prefetch(static_cast<const float*>(a.x) + pbase, NN2 * 4, 0, 1);
-            l2_prefetch(static_cast<const float*>(a.r) + pbase, NN2 * 4, 0, 1);
-            l2_prefetch(static_cast<const float*>(a.p) + pbase, NN2 * 4, 0, 1);
-        }
         // the plane's spectrum [k1][k2] -> U[k1 H + k2]
         const float2* Sp = static_cast<const float2*>(a.S) + ((long long)(l * PLANE_D + al) * g.N[0] + i0) * NP;
         if constexpr (NP % 2 == 0) {
