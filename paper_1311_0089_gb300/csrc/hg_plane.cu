@@ -183,8 +183,7 @@ __device__ __forceinline__ void plane_fwd_body(const GridDev& g, const float2* _
         // the plane's r and p (shared by the three CTAs of the plane: a third
         // each) and its coefficients into L2 ahead of the batched loads below
         // (135^3: plane_fwd 169 -> 164 us; at N <= 81 the hints cost 0.5-1.5%
-        // of the solve.  The same hints for x, r, p at the start of plane_inv
-        // were evicted before its update: DRAM reads 355 -> 439 MB, slower)
+        // of the solve)
         if constexpr (N >= 135) {
             for (int be = 0; be < PLANE_D; ++be) {
                 l2_prefetch(R0 + be * M, NN2 * 4, al, PLANE_D);
@@ -360,6 +359,7 @@ __device__ __forceinline__ void plane_inv_body(const GridDev& g, const float2* _
     if (act) {
         // the plane's spectrum [k1][k2] -> U[k1 H + k2]
         const float2* Sp = static_cast<const float2*>(a.S) + ((long long)(l * PLANE_D + al) * g.N[0] + i0) * NP;
+        if constexpr (N >= 135) l2_prefetch(Sp, NP * 8, 0, 1);
         if constexpr (NP % 2 == 0) {
             // an even plane size keeps every plane 16-byte aligned: two entries at a time
             constexpr int KB = 3, NP2 = NP / 2;
@@ -391,6 +391,16 @@ __device__ __forceinline__ void plane_inv_body(const GridDev& g, const float2* _
         __syncthreads();
         // axis 1: U[i1 H + k2] = X_i1(k2), the half spectra of the grid rows
         plane_ifft<N, true>(U, 1, H, H, alt, tws);
+        // x, r and p of the plane into L2 for the update (after the first
+        // transform: hints issued at the start of the kernel were evicted
+        // before use, DRAM reads 355 -> 439 MB; here plane_inv 166 -> 146 us
+        // at the same DRAM traffic, with the spectrum plane's hints above)
+        if constexpr (N >= 135) {
+            const long long pbase = ((long long)(l * PLANE_D + al)) * M + (long long)i0 * NN2;
+            l2_prefetch(static_cast<const float*>(a.x) + pbase, NN2 * 4, 0, 1);
+            l2_prefetch(static_cast<const float*>(a.r) + pbase, NN2 * 4, 0, 1);
+            l2_prefetch(static_cast<const float*>(a.p) + pbase, NN2 * 4, 0, 1);
+        }
         // rows 2j, 2j + 1 as one complex row Z = X_2j + i X_2j+1 over all k2
         // (X(k2) = conj X(N - k2) for k2 >= H), in place: row j of U (stride W)
         // holds X_2j then X_2j+1, and receives Z_j
