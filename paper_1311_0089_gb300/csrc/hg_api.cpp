@@ -985,7 +985,7 @@ int job_begin(Job& j) {
     for (int i = 0; i < 9; ++i) g->ref[i] = g->has_ref && i < gd.d * gd.d ? j.o.A0[i] : 0.0;
     if (g->has_ref) {
         // ||b||_A0 <= sqrt(lmax(A0)) / lmin(A0) ||A E|| (reading of the zero test)
-        double ev[3];
+        double ev[3] = {0.0, 0.0, 0.0};
         sym_eig_host(g->ref, gd.d, ev);
         const double lmin = *std::min_element(ev, ev + gd.d), lmax = *std::max_element(ev, ev + gd.d);
         j.zscale = std::sqrt(lmax) / lmin;
