@@ -223,6 +223,18 @@ def plane_pass_bytes(N, L, prec_bytes=4, n_phases_bytes=1):
     return [2 * vec + M * n_phases_bytes + spec, 2 * spec, spec + 6 * vec]
 
 
+def per_pass_roofline(keys, pass_bytes_list, pass_ms, peak_gbs):
+    """Each pass of an iteration against the HBM peak: its algorithmic bytes
+    per launch over its mean in-solve launch duration (None where no launch
+    was timed)."""
+    out = []
+    for k, b, ms in zip(keys, pass_bytes_list, pass_ms):
+        gbs = b / (ms * 1e-3) / 1e9 if ms and ms > 0 else None
+        out.append({"pass": k, "ms_in_solve": ms, "bytes": int(b), "achieved_gbs": gbs,
+                    "frac": gbs / peak_gbs if gbs is not None else None})
+    return out
+
+
 def resident_bytes(N, iters, prec_bytes=4):
     """Algorithmic bytes (the fused pass schedule's count) of the iterations a
     resident launch ran: per load and iteration the three passes' vector and
@@ -748,6 +760,7 @@ def sub_c3(hg, torch, dev, args):
                      "bytes_per_launch": pb[dom_pass], "ms_per_launch": dom_avg, "launches_timed": dom_n,
                      "traffic": profiled_traffic("fp32_" + keys[dom_pass] + "_3d", g.launch_cfg(hg.HG_MIXED)),
                      "pass_ms_in_solve": dict(zip(keys, pass_avg)),
+                     "per_pass": per_pass_roofline(keys, pb, pass_avg, peaks["hbm_gbs"]),
                      "iteration_ms": float(sum(pass_avg)),
                      "iteration_bytes": int(sum(pb)),
                      "iteration_frac": sum(pb) / (sum(pass_avg) * 1e-3) / 1e9 / peaks["hbm_gbs"],
